@@ -1,0 +1,259 @@
+"""FP64 CPU oracle of the MOND particle-mesh method (Visser, Eijt & de Nijs 2023).
+
+TEST INFRASTRUCTURE ONLY. The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers. The oracle shares no code
+with the CUDA library under ``paper_2312_02968_gb300/``; neither imports the
+other. All arithmetic lives in ``mond_oracle.c``; this module only marshals
+numpy arrays into it.
+
+What pins each function (tests in ``tests/test_oracle_*.py``):
+  ball            251 taps for sigma = 1 (Sect. 3.1, Fig. 1); brute-force counts.
+  axis_lut        Poisson-summation normalisation of the sampled Gaussian.
+  deposit_fixed   vs the direct FP64 Eq. smooth (error bound of the rule);
+                  Fourier transform of one particle = exp(-sigma^2 k^2/2)
+                  (App. Fourier); mass conservation; order independence.
+  fft1/fft3       vs the plain DFT; round trip; Parseval; numpy.fft.
+  mu/nu           mu(x) x = y <=> nu(y) y = x for every kind (Sect. 2.1).
+  solve           transform count 42 for K = 4 and 2 for Newton (Sect. 5.2,
+                  Sect. 6); the Newtonian closed form; the spectral Poisson
+                  solve of a point mass; curl/div invariants; deep-MOND
+                  point-mass field sqrt(G M a0)/r (Sect. 2); two-body force
+                  (Eq. twobodyforce); ring force (Eq. ringforce); isothermal
+                  field (Eq. g); residual of the discretised AQUAL equation at
+                  the converged fixed point; convergence rate (Sect. 2.1).
+  gather          particle at a node sees the node-smoothed field; constant
+                  field reproduces the ball weight sum; two-body force.
+  push            Eq. motion on hand-checked numbers; circular orbit period.
+  particle_diag   two-body constants of motion on hand-made states.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mond_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libmondoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no FMA contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            L.ora_mu.restype = f64
+            L.ora_mu.argtypes = [i32, f64]
+            L.ora_nu.restype = f64
+            L.ora_nu.argtypes = [i32, f64]
+            L.ora_ball_reach.restype = i32
+            L.ora_ball_reach.argtypes = [f64]
+            L.ora_ball.restype = i32
+            L.ora_ball.argtypes = [f64, P, i32]
+            L.ora_axis_lut.argtypes = [f64, P]
+            L.ora_kacc.restype = i32
+            L.ora_kacc.argtypes = [i64, P]
+            L.ora_deposit_fixed.restype = i64
+            L.ora_deposit_fixed.argtypes = [i32, f64, i64, P, P, P, i32, P]
+            L.ora_acc_to_rho.argtypes = [i32, P, i32, f64, P, P]
+            L.ora_deposit_exact.argtypes = [i32, f64, f64, i64, P, P, P, P]
+            L.ora_dft1.argtypes = [i32, P, P, i32]
+            L.ora_fft1.argtypes = [i32, P, i32]
+            L.ora_fft3_raw.argtypes = [i32, P, i32]
+            L.ora_solve.restype = i32
+            L.ora_solve.argtypes = [i32, f64, f64, f64, i32, i32, P, P, i32, P, P, P, P, P]
+            L.ora_gather.argtypes = [i32, f64, P, i64, P, P, P]
+            L.ora_push.argtypes = [i32, f64, f64, i64, P, P, P, P, i32]
+            L.ora_particle_diag.argtypes = [i32, f64, i64, P, P, P, P, P]
+            L.ora_transform_count.restype = ctypes.c_longlong
+            L.ora_num_threads.restype = i32
+            _lib = L
+        return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return lib().ora_num_threads()
+
+
+def mu(kind: int, x: float) -> float:
+    return lib().ora_mu(kind, float(x))
+
+
+def nu(kind: int, y: float) -> float:
+    return lib().ora_nu(kind, float(y))
+
+
+def ball_reach(sigma: float) -> int:
+    return lib().ora_ball_reach(float(sigma))
+
+
+def ball(sigma: float) -> np.ndarray:
+    n = lib().ora_ball(float(sigma), None, 0)
+    d = np.zeros((n, 3), np.int32)
+    lib().ora_ball(float(sigma), _p(d), n)
+    return d
+
+
+def axis_lut(sigma: float) -> np.ndarray:
+    r = ball_reach(sigma)
+    t = np.zeros((65537, 2 * r + 1), np.uint32)
+    lib().ora_axis_lut(float(sigma), _p(t))
+    return t
+
+
+def kacc(mass) -> int:
+    m = _c(mass, np.float32)
+    return lib().ora_kacc(m.size, _p(m))
+
+
+def deposit_fixed(n: int, sigma: float, cell, off, mass, kacc_val: int | None = None):
+    """Fixed-point deposit. Returns (acc uint64 [n,n,n] in z,y,x order, kacc, skipped)."""
+    cell = _c(cell, np.int32).reshape(-1, 3)
+    off = _c(off, np.float32).reshape(-1, 3)
+    mass = _c(mass, np.float32).reshape(-1)
+    if kacc_val is None:
+        kacc_val = kacc(mass)
+    acc = np.zeros((n, n, n), np.uint64)
+    sk = lib().ora_deposit_fixed(n, float(sigma), mass.size, _p(cell), _p(off), _p(mass), int(kacc_val), _p(acc))
+    return acc, int(kacc_val), int(sk)
+
+
+def acc_to_rho(acc, kacc_val: int, s: float):
+    acc = _c(acc, np.uint64)
+    n = acc.shape[0]
+    r32 = np.zeros(acc.shape, np.float32)
+    r64 = np.zeros(acc.shape, np.float64)
+    lib().ora_acc_to_rho(n, _p(acc), int(kacc_val), float(s), _p(r32), _p(r64))
+    return r32, r64
+
+
+def deposit_exact(n: int, sigma: float, s: float, cell, off, mass):
+    cell = _c(cell, np.int32).reshape(-1, 3)
+    off = _c(off, np.float32).reshape(-1, 3)
+    mass = _c(mass, np.float32).reshape(-1)
+    rho = np.zeros((n, n, n), np.float64)
+    lib().ora_deposit_exact(n, float(sigma), float(s), mass.size, _p(cell), _p(off), _p(mass), _p(rho))
+    return rho
+
+
+def dft1(x, sign: int = -1):
+    x = _c(x, np.complex128)
+    X = np.zeros_like(x)
+    lib().ora_dft1(x.size, _p(x), _p(X), int(sign))
+    return X
+
+
+def fft1(x, sign: int = -1):
+    x = _c(x, np.complex128).copy()
+    lib().ora_fft1(x.size, _p(x), int(sign))
+    return x
+
+
+def fft3_raw(a, sign: int = -1):
+    a = _c(a, np.complex128).copy()
+    lib().ora_fft3_raw(a.shape[0], _p(a), int(sign))
+    return a
+
+
+def transform_count() -> int:
+    return int(lib().ora_transform_count())
+
+
+def reset_transform_count() -> None:
+    lib().ora_reset_transform_count()
+
+
+def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None,
+          finish_h: bool = False, want=("gN", "H", "phi", "acc", "dH")):
+    """Field solve (App. Flow steps 3-9). rho: [n,n,n] float64 (z,y,x).
+    Returns a dict of the requested outputs (vector fields as [3,n,n,n])."""
+    rho = _c(rho, np.float64)
+    n = rho.shape[0]
+    out = {}
+    gN = np.zeros((3, n, n, n)) if "gN" in want else None
+    H = np.zeros((3, n, n, n)) if "H" in want else None
+    phi = np.zeros((n, n, n)) if "phi" in want else None
+    acc = np.zeros((3, n, n, n)) if "acc" in want else None
+    dH = np.zeros(max(n_iter, 1)) if "dH" in want else None
+    H0a = None if H0 is None else _c(H0, np.float64)
+    rc = lib().ora_solve(n, float(s), float(G), float(a0), int(mu_kind), int(n_iter), _p(rho), _p(H0a),
+                         int(bool(finish_h)), _p(gN), _p(H), _p(phi), _p(acc), _p(dH))
+    if rc != 0:
+        raise RuntimeError(f"oracle solve failed: {rc}")
+    for k, v in (("gN", gN), ("H", H), ("phi", phi), ("acc", acc), ("dH", dH)):
+        if v is not None:
+            out[k] = v
+    return out
+
+
+def gather(sigma: float, acc, cell, off):
+    acc = _c(acc, np.float64)
+    n = acc.shape[1]
+    cell = _c(cell, np.int32).reshape(-1, 3)
+    off = _c(off, np.float32).reshape(-1, 3)
+    g = np.zeros((cell.shape[0], 3))
+    lib().ora_gather(n, float(sigma), _p(acc), cell.shape[0], _p(cell), _p(off), _p(g))
+    return g
+
+
+def push(n: int, s: float, dt: float, g, cell, off, vel, drift: bool = True):
+    """Kick (and drift). Returns new (cell int32, offset float64, vel float64)."""
+    g = _c(g, np.float64).reshape(-1, 3)
+    cell = _c(cell, np.int32).reshape(-1, 3).copy()
+    off = _c(off, np.float64).reshape(-1, 3).copy()
+    vel = _c(vel, np.float64).reshape(-1, 3).copy()
+    lib().ora_push(n, float(s), float(dt), cell.shape[0], _p(g), _p(cell), _p(off), _p(vel), int(bool(drift)))
+    return cell, off, vel
+
+
+def particle_diag(n: int, s: float, cell, off, vel, mass):
+    cell = _c(cell, np.int32).reshape(-1, 3)
+    off = _c(off, np.float64).reshape(-1, 3)
+    vel = _c(vel, np.float64).reshape(-1, 3)
+    mass = _c(mass, np.float32).reshape(-1)
+    out = np.zeros(11)
+    lib().ora_particle_diag(n, float(s), mass.size, _p(cell), _p(off), _p(vel), _p(mass), _p(out))
+    return {"mass": out[0], "P": out[1:4].copy(), "R": out[4:7].copy(), "L": out[7:10].copy(), "Ekin": out[10]}
+
+
+def step(n: int, s: float, G: float, a0: float, mu_kind: int, sigma: float, n_iter: int, dt: float,
+         cell, off, vel, mass, H0=None, finish_h: bool = False):
+    """One time step in the order deposit -> solve -> gather -> kick -> drift.
+    Returns (cell, off float64, vel float64, g, fields dict, kacc)."""
+    acc, ka, _ = deposit_fixed(n, sigma, cell, off, mass)
+    _, rho64 = acc_to_rho(acc, ka, s)
+    f = solve(rho64, s, G, a0, mu_kind, n_iter, H0=H0, finish_h=finish_h)
+    g = gather(sigma, f["acc"], cell, off)
+    c2, o2, v2 = push(n, s, dt, g, cell, np.asarray(off, np.float64), vel)
+    return c2, o2, v2, g, f, ka
