@@ -1,0 +1,209 @@
+/*
+ * mond_pm.h -- C ABI of the GB300 (sm_103a) MOND particle-mesh force pipeline.
+ *
+ * Method: Visser, Eijt & de Nijs, "Fast particle-mesh code for Milgromian
+ * dynamics" (A&A 2023, arXiv:2312.02968). One time step is
+ *   deposit (Eq. smooth) -> field solve (Sect. 2.1 iteration, App. Flow steps
+ *   3-9) -> gather (Eq. gi) -> leapfrog kick and drift (Eq. motion).
+ *
+ * Conventions shared by every call:
+ *  - Mesh: the FFT domain is n_f^3 pixels of width s = box / n, with
+ *    n_f = n (pad = 1) or n_f = 2n (pad = 2: the physical n^3 sits in the
+ *    centre of a zero-padded periodic domain). The whole iteration is periodic
+ *    on n_f^3 (Sect. 3: periodic lattice with empty margin).
+ *  - Scalar mesh fields are float32 [z][y][x] (x fastest), n_f^3 values;
+ *    vector fields are three such planes, component x first.
+ *  - Particles are borrowed device arrays in [N][3] layout: int32 cell (the
+ *    FFT-domain pixel of the nearest pixel centre, 0..n_f-1 on each axis),
+ *    float32 offset from that centre in pixels, in [-1/2, 1/2], float32
+ *    velocity (length per time), and float32 mass [N]. Physical position is
+ *    (cell - n_f/2 + offset) * s.
+ *  - Every call enqueues work on the handle's CUDA stream and returns without
+ *    synchronising, unless its comment says it synchronises.
+ *  - Every call returns MOND_OK (0) or a negative error code. Errors found on
+ *    the device (a particle outside the domain, a non-finite field) are
+ *    latched in a device status word and returned by the next call that
+ *    synchronises (mond_pm_sync, mond_pm_diagnostics, mond_pm_get_field).
+ *    mond_pm_last_error() describes the most recent error.
+ *
+ * Ownership: the caller allocates all device memory. The handle only carves
+ * the caller's workspace (mond_pm_workspace_bytes) and borrows the particle
+ * arrays; it frees neither. The library calls no cudaMalloc.
+ */
+#ifndef MOND_PM_H
+#define MOND_PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mond_pm* mond_pm_t;
+
+typedef struct {
+  int32_t n;   /* physical mesh side; n_f = n * pad must be 2^a 3^b, 16 <= n_f <= 512 */
+  int32_t pad; /* 1 or 2 */
+} mond_pm_grid;
+
+/* Interpolation function mu (Eq. mu and Sect. 4): deep mu(x) = x; simple
+ * mu(x) = x/(1+x); standard mu(x) = x/sqrt(1+x^2); Newton mu = 1. */
+enum { MOND_MU_DEEP = 0, MOND_MU_SIMPLE = 1, MOND_MU_STANDARD = 2, MOND_MU_NEWTON = 3 };
+
+/* Initial H of the iteration: zero (App. Flow step 7), the H of the previous
+ * solve (Sect. 5.2 item iv), or a caller-supplied guess. */
+enum { MOND_WARM_NONE = 0, MOND_WARM_PREV = 1, MOND_WARM_GUESS = 2 };
+
+/* Mesh fields readable with mond_pm_get_field. */
+enum {
+  MOND_FIELD_RHO = 0,    /* density from the last deposit, 1 plane */
+  MOND_FIELD_GN = 1,     /* Newtonian field g_N of the last solve, 3 planes */
+  MOND_FIELD_H = 2,      /* H state: the last H formed by a solve (warm-start state), 3 planes */
+  MOND_FIELD_PHI = 3,    /* MOND potential phi of the last solve, 1 plane (needs MOND_OPT_KEEP_PHI) */
+  MOND_FIELD_ACC = 4,    /* acceleration mesh a = -grad_FD phi of the last solve, 3 planes */
+  MOND_FIELD_SMOOTH = 5  /* node-smoothed acceleration of the last mond_pm_smooth, 3 planes */
+};
+
+/* Error codes. */
+enum {
+  MOND_OK = 0,
+  MOND_EINVAL = -1,    /* bad argument (size, kind, width, pointer, alignment) */
+  MOND_ENOMEM = -2,    /* workspace too small */
+  MOND_ECUDA = -3,     /* a CUDA runtime call failed */
+  MOND_EOVERFLOW = -4, /* fixed-point bound violated (cannot happen for N < 2^31) */
+  MOND_EDOMAIN = -5,   /* a particle's cell or offset is outside the domain; it was skipped */
+  MOND_ENAN = -6,      /* a non-finite value appeared in a field or a particle */
+  MOND_ETIMEOUT = -7,  /* a bounded device wait gave up (kernel returned early) */
+  MOND_ESTATE = -8     /* call out of order (no particles bound, no solve yet, ...) */
+};
+
+/* Options for mond_pm_set_option. */
+enum {
+  MOND_OPT_KEEP_PHI = 1,  /* value 1: also form the potential phi in the final pass */
+  MOND_OPT_TRACK_DH = 2,  /* value 1: record ||H_j - H_{j-1}|| / ||g_N|| per iteration (costs one reduction) */
+  MOND_OPT_USE_GRAPH = 3  /* value 1: replay mond_pm_step as a captured CUDA graph (default 0) */
+};
+
+typedef struct {
+  double mass;          /* sum of m_i */
+  double momentum[3];   /* sum m_i v_i */
+  double com[3];        /* centre of mass (physical coordinates) */
+  double ang_mom[3];    /* sum m_i (x_i - com) x v_i */
+  double e_kin;         /* sum m_i |v_i|^2 / 2 */
+  double e_pot;         /* s^3 sum rho phi (needs MOND_OPT_KEEP_PHI and a solve), else NaN */
+  double rho_mass;      /* s^3 sum rho of the last deposit */
+  int32_t n_iter_done;  /* iterations run by the last solve */
+  int32_t pad_;
+  double dH[64];        /* ||H_j - H_{j-1}|| / ||g_N|| per iteration (MOND_OPT_TRACK_DH), NaN otherwise */
+} mond_pm_diag;
+
+/* Bytes of device workspace a handle with this grid and kernel width needs
+ * for up to max_particles particles. Returns MOND_EINVAL for an unsupported
+ * grid or width. */
+int mond_pm_workspace_bytes(mond_pm_grid grid, double kernel_width, int64_t max_particles, size_t* bytes);
+
+/* Create a handle. box: physical side of the n^3 mesh (s = box/n); a0:
+ * Milgrom's constant; G: Newton's constant; mu_kind: MOND_MU_*;
+ * kernel_width: sigma of the Gaussian of Eq. smooth in pixels (0.75..2; the
+ * paper uses 1; the ball of taps is |d| < 4 sigma, Sect. 3.1); cuda_stream: a
+ * cudaStream_t (NULL = default stream); workspace: device memory of at least
+ * mond_pm_workspace_bytes (256-byte aligned), owned by the caller and kept
+ * alive until mond_pm_destroy. Builds the lookup table of Sect. 3.1 on the
+ * host and uploads it (synchronises once). */
+int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_kind, double kernel_width,
+                   void* cuda_stream, void* workspace, size_t workspace_bytes, int64_t max_particles,
+                   mond_pm_t* out);
+
+/* Release the handle (not the workspace, not the particles). Synchronises. */
+int mond_pm_destroy(mond_pm_t h);
+
+/* Set an option (MOND_OPT_*). */
+int mond_pm_set_option(mond_pm_t h, int option, int64_t value);
+
+/* Borrow particle arrays (device pointers, layout above), N <= max_particles.
+ * Scans the masses for the fixed-point scale (synchronises once). The arrays
+ * cell, offset and vel are updated in place by gather_push / half_kick. */
+int mond_pm_bind_particles(mond_pm_t h, int64_t N, int32_t* cell, float* offset, float* vel, const float* mass);
+
+/* Mass deposit, Eq. smooth restricted to the ball around each particle's
+ * cell (Sect. 3.1; App. Flow main loop steps 1-2) in a fixed-point rule that
+ * makes the result independent of order and bit-identical to the CPU oracle:
+ * per-axis weights round(2^24 g1) from a table indexed by the offset rounded
+ * to 2^-16 px, combined in integers, accumulated in int64 units of
+ * 2^-Kacc mass; rho = float(double(acc) * 2^-Kacc / s^3). Also bins the
+ * particles by 8^3 mesh tile for the gather. */
+int mond_pm_deposit(mond_pm_t h);
+
+/* Field solve (Sect. 2.1 iteration; App. Flow steps 3-9) on the last
+ * deposit: Newtonian field, then n_iter iterations of
+ * F = g_N + H, g_M = nu(|F|/a0) F, curl-free projection, F = mu(|g_M|/a0) g_M,
+ * H = F - g_N, divergence-free projection; the last iteration stops after the
+ * curl-free projection and the acceleration mesh a = -grad_FD phi is formed.
+ * n_iter = 0 gives the Newtonian solve (a = g_N). warm: MOND_WARM_NONE
+ * (H = 0), MOND_WARM_PREV (H of the previous solve) or MOND_WARM_GUESS
+ * (H_guess: device float32, 3 planes; it is projected onto its
+ * divergence-free part first). With PREV or GUESS the last iteration also
+ * completes the H update so the next solve can start from it. 0 <= n_iter <= 64. */
+int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess);
+
+/* Node-smoothed acceleration: the periodic discrete convolution of the
+ * acceleration mesh with the ball-truncated Gaussian of Eq. gi, i.e. the force
+ * Eq. gi gives a particle sitting exactly on each pixel centre. Written to
+ * accel_mesh_out (device float32, 3 planes) when non-NULL and kept for
+ * mond_pm_get_field(MOND_FIELD_SMOOTH). */
+int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out);
+
+/* Force at the particles from the acceleration mesh of the last solve
+ * (Eq. gi, same ball and Gaussian as the deposit, FP32 weights), then the
+ * leapfrog step of Eq. motion: v += g dt; r += v dt; the cell becomes the
+ * nearest pixel centre and wraps periodically. Uses the binning of the last
+ * deposit, so the particles must not have moved since. */
+int mond_pm_gather_push(mond_pm_t h, double dt);
+
+/* As gather_push but velocity only (v += g dt): the initial or final half
+ * step of Sect. 3. */
+int mond_pm_half_kick(mond_pm_t h, double dt);
+
+/* Force at the particles only (Eq. gi) into g_out (device float32 [N][3]). */
+int mond_pm_gather(mond_pm_t h, float* g_out);
+
+/* One time step: deposit, solve_field(n_iter, warm, NULL), gather_push(dt). */
+int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm);
+
+/* One time step through host memory: copies cell/offset/vel of the N bound
+ * particles from the host arrays (pinned memory recommended) to the bound
+ * device arrays, runs mond_pm_step, copies cell/offset/vel back and
+ * synchronises. Masses are not copied: they are constant and were scanned at
+ * bind time. Returns any latched device error. */
+int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cell_host, float* offset_host,
+                      float* vel_host);
+
+/* Diagnostics in FP64 (the monitored quantities of Sects. 4.1 and 4.3) into a
+ * host struct. Synchronises and returns any latched device error. */
+int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out);
+
+/* Copy a mesh field (MOND_FIELD_*) into dst (device float32, compact n_f^3
+ * per plane). Synchronises and returns any latched device error. */
+int mond_pm_get_field(mond_pm_t h, int which, float* dst);
+
+/* Copy the raw int64 deposit accumulator of the last deposit (n_f^3 words)
+ * into dst (device) and report Kacc (units are 2^-Kacc mass). Synchronises. */
+int mond_pm_get_deposit_acc(mond_pm_t h, uint64_t* dst, int32_t* kacc);
+
+/* Synchronise the stream and return (and clear) any latched device error. */
+int mond_pm_sync(mond_pm_t h);
+
+/* Text of the last error on this handle (or of the last failed create when
+ * h is NULL). Valid until the next call on the handle. */
+const char* mond_pm_last_error(mond_pm_t h);
+
+/* Number of kernels this handle has launched since creation (each graph
+ * replay counts its kernels). */
+int64_t mond_pm_kernel_launches(mond_pm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOND_PM_H */

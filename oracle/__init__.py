@@ -90,6 +90,7 @@ def lib():
             L.ora_particle_diag.argtypes = [i32, f64, i64, P, P, P, P, P]
             L.ora_transform_count.restype = ctypes.c_longlong
             L.ora_num_threads.restype = i32
+            L.ora_project_div.argtypes = [i32, f64, P, P]
             _lib = L
         return _lib
 
@@ -214,6 +215,14 @@ def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None
     for k, v in (("gN", gN), ("H", H), ("phi", phi), ("acc", acc), ("dH", dH)):
         if v is not None:
             out[k] = v
+    return out
+
+
+def project_div(field, s: float):
+    """Divergence-free part of a vector field [3, n, n, n] (Eq. divH)."""
+    f = _c(field, np.float64)
+    out = np.zeros_like(f)
+    lib().ora_project_div(f.shape[1], float(s), _p(f), _p(out))
     return out
 
 

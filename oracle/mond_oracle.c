@@ -676,3 +676,24 @@ void ora_particle_diag(int n, double s, int64_t N, const int32_t* cell, const do
   }
   out[10] = E;
 }
+
+/* Divergence-free part of a vector field (Eq. divH): H^ -> H^ - k A k.H^,
+ * k = 0 kept; the real part of the inverse transform is kept. */
+void ora_project_div(int n, double s, const double* in, double* out) {
+  int64_t tot = (int64_t)n * n * n;
+  cplx* cv = (cplx*)malloc(sizeof(cplx) * 3 * tot);
+  for (int64_t j = 0; j < 3 * tot; j++) cv[j] = in[j];
+  for (int a = 0; a < 3; a++) fwd3(n, s, cv + a * tot);
+  for (int l = 0; l < n; l++)
+    for (int jy = 0; jy < n; jy++)
+      for (int i = 0; i < n; i++) {
+        double k[3];
+        kvec(n, s, i, jy, l, k);
+        int64_t j = idx3(n, i, jy, l);
+        double A = invlap(k);
+        cplx kh = k[0] * cv[j] + k[1] * cv[tot + j] + k[2] * cv[2 * tot + j];
+        for (int a = 0; a < 3; a++) cv[a * tot + j] -= k[a] * A * kh;
+      }
+  for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, out + a * tot);
+  free(cv);
+}

@@ -1,0 +1,215 @@
+"""ctypes binding of the C ABI in include/mond_pm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libmondpm.so``. PyTorch provides device memory (the workspace and the
+particle tensors) and the CUDA stream. ``lib()`` raises if the library has not
+been built; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmondpm.so")
+
+MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
+WARM_NONE, WARM_PREV, WARM_GUESS = 0, 1, 2
+FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
+OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH = 1, 2, 3
+ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
+          -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
+
+# every function the header declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("mass", _D), ("momentum", _D * 3), ("com", _D * 3), ("ang_mom", _D * 3), ("e_kin", _D),
+                ("e_pot", _D), ("rho_mass", _D), ("n_iter_done", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("dH", _D * 64)]
+
+
+SIGNATURES = {
+    "mond_pm_workspace_bytes": (_I, [Grid, _D, _I64, ctypes.POINTER(ctypes.c_size_t)]),
+    "mond_pm_create": (_I, [Grid, _D, _D, _D, _I, _D, _P, _P, ctypes.c_size_t, _I64, ctypes.POINTER(_P)]),
+    "mond_pm_destroy": (_I, [_P]),
+    "mond_pm_set_option": (_I, [_P, _I, _I64]),
+    "mond_pm_bind_particles": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "mond_pm_deposit": (_I, [_P]),
+    "mond_pm_solve_field": (_I, [_P, _I, _I, _P]),
+    "mond_pm_smooth": (_I, [_P, _P]),
+    "mond_pm_gather_push": (_I, [_P, _D]),
+    "mond_pm_half_kick": (_I, [_P, _D]),
+    "mond_pm_gather": (_I, [_P, _P]),
+    "mond_pm_step": (_I, [_P, _D, _I, _I]),
+    "mond_pm_step_host": (_I, [_P, _D, _I, _I, _P, _P, _P]),
+    "mond_pm_diagnostics": (_I, [_P, ctypes.POINTER(Diag)]),
+    "mond_pm_get_field": (_I, [_P, _I, _P]),
+    "mond_pm_get_deposit_acc": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "mond_pm_sync": (_I, [_P]),
+    "mond_pm_last_error": (ctypes.c_char_p, [_P]),
+    "mond_pm_kernel_launches": (_I64, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libmondpm.so (raises if it was not built: run __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class MondError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def workspace_bytes(n: int, pad: int, kernel_width: float, max_particles: int) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().mond_pm_workspace_bytes(Grid(n, pad), float(kernel_width), int(max_particles), ctypes.byref(out))
+    if rc != 0:
+        raise MondError(rc, "unsupported grid or kernel width")
+    return int(out.value)
+
+
+class MondPM:
+    """One simulation handle: mesh n^3 (FFT domain (n pad)^3), box side, a0, G,
+    interpolation function, Gaussian width in pixels. Workspace is a torch
+    uint8 tensor on the current CUDA device; the handle runs on ``stream``
+    (default: torch's current stream)."""
+
+    def __init__(self, n: int, pad: int, box: float, a0: float, G: float, mu_kind: int, kernel_width: float,
+                 max_particles: int, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.n, self.pad, self.nf = n, pad, n * pad
+        self.box, self.s = box, box / n
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = workspace_bytes(n, pad, kernel_width, max_particles)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = ctypes.c_void_p()
+        rc = lib().mond_pm_create(Grid(n, pad), float(box), float(a0), float(G), int(mu_kind), float(kernel_width),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(aligned),
+                                  nbytes, int(max_particles), ctypes.byref(h))
+        if rc != 0:
+            raise MondError(rc, lib().mond_pm_last_error(None).decode())
+        self.h = h
+        self.particles = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise MondError(rc, lib().mond_pm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mond_pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI, one method per entry point ------------------------------------
+    def set_option(self, option: int, value: int):
+        self._check(lib().mond_pm_set_option(self.h, int(option), int(value)))
+
+    def bind_particles(self, cell, offset, vel, mass):
+        """Borrow device tensors: cell int32 [N,3], offset float32 [N,3],
+        vel float32 [N,3], mass float32 [N] (all contiguous)."""
+        torch = self.torch
+        for t, dt in ((cell, torch.int32), (offset, torch.float32), (vel, torch.float32), (mass, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or t.device != self.device:
+                raise ValueError("particle tensors must be contiguous device tensors of the documented dtypes")
+        self.particles = (cell, offset, vel, mass)
+        self._check(lib().mond_pm_bind_particles(self.h, int(mass.numel()), _ptr(cell), _ptr(offset), _ptr(vel),
+                                                 _ptr(mass)))
+
+    def deposit(self):
+        self._check(lib().mond_pm_deposit(self.h))
+
+    def solve_field(self, n_iter: int = 4, warm: int = WARM_NONE, H_guess=None):
+        self._check(lib().mond_pm_solve_field(self.h, int(n_iter), int(warm), _ptr(H_guess)))
+
+    def smooth(self, out=None):
+        self._check(lib().mond_pm_smooth(self.h, _ptr(out)))
+
+    def gather_push(self, dt: float):
+        self._check(lib().mond_pm_gather_push(self.h, float(dt)))
+
+    def half_kick(self, dt: float):
+        self._check(lib().mond_pm_half_kick(self.h, float(dt)))
+
+    def gather(self, out=None):
+        torch = self.torch
+        N = self.particles[3].numel()
+        if out is None:
+            out = torch.empty((N, 3), dtype=torch.float32, device=self.device)
+        self._check(lib().mond_pm_gather(self.h, _ptr(out)))
+        return out
+
+    def step(self, dt: float, n_iter: int = 4, warm: int = WARM_NONE):
+        self._check(lib().mond_pm_step(self.h, float(dt), int(n_iter), int(warm)))
+
+    def step_host(self, dt: float, n_iter: int, warm: int, cell_host, offset_host, vel_host):
+        """Host tensors (pinned, contiguous) in and out; synchronises."""
+        self._check(lib().mond_pm_step_host(self.h, float(dt), int(n_iter), int(warm), _ptr(cell_host),
+                                            _ptr(offset_host), _ptr(vel_host)))
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        self._check(lib().mond_pm_diagnostics(self.h, ctypes.byref(d)))
+        return {"mass": d.mass, "momentum": list(d.momentum), "com": list(d.com), "ang_mom": list(d.ang_mom),
+                "e_kin": d.e_kin, "e_pot": d.e_pot, "rho_mass": d.rho_mass, "n_iter_done": d.n_iter_done,
+                "dH": list(d.dH)}
+
+    def get_field(self, which: int, out=None):
+        torch = self.torch
+        planes = 3 if which in (FIELD_GN, FIELD_H, FIELD_ACC, FIELD_SMOOTH) else 1
+        shape = (planes, self.nf, self.nf, self.nf) if planes == 3 else (self.nf, self.nf, self.nf)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        self._check(lib().mond_pm_get_field(self.h, int(which), _ptr(out)))
+        return out
+
+    def get_deposit_acc(self):
+        torch = self.torch
+        out = torch.empty((self.nf, self.nf, self.nf), dtype=torch.int64, device=self.device)
+        k = ctypes.c_int32(0)
+        self._check(lib().mond_pm_get_deposit_acc(self.h, _ptr(out), ctypes.byref(k)))
+        return out, int(k.value)
+
+    def sync(self):
+        self._check(lib().mond_pm_sync(self.h))
+
+    def kernel_launches(self) -> int:
+        return int(lib().mond_pm_kernel_launches(self.h))

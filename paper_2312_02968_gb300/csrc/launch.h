@@ -1,0 +1,14 @@
+// launch.h -- declarations of the per-size pass launchers (one translation
+// unit per supported FFT-domain side) and the supported-size list.
+#pragma once
+#include <cuda_runtime.h>
+#include "passes.cuh"
+
+#define MOND_SIZES(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+#define MOND_DECL_LAUNCHERS(n)                                                          \
+  cudaError_t mond_xpass_##n(int mode, const passes::XArgs& a, cudaStream_t st);        \
+  cudaError_t mond_ypass_##n(int dir, const passes::YArgs& a, int ncomp, cudaStream_t st); \
+  cudaError_t mond_zpass_##n(int mode, const passes::ZArgs& a, cudaStream_t st);
+MOND_SIZES(MOND_DECL_LAUNCHERS)
+#undef MOND_DECL_LAUNCHERS

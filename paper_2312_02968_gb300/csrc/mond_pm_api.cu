@@ -1,0 +1,804 @@
+// mond_pm_api.cu -- the C ABI of include/mond_pm.h: handle, workspace
+// carve-up, host-built tables, and the pass sequence of a time step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mond_pm.h"
+#include "launch.h"
+#include "particles.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Workspace {
+  uint32_t* status;
+  double* red;       // 256 doubles: [0..10] particle diag, [16..17] plane sums, [32..] dH pairs
+  unsigned long long* isum;  // integer sum slot
+  int* emax;
+  int* counters;     // work counters (deposit, gather)
+  float2* tw;
+  float* kv;
+  float* kp;
+  uint32_t* lut;
+  uint32_t* ball;
+  uint64_t* dep;
+  float2* W;         // 3 spectral planes
+  float2* A;         // 4 spectral planes
+  float* gN;         // 3 real planes
+  float* Hs;         // 3 real planes
+  float* acc;        // 4 real planes: acceleration (3) then phi (1)
+  float* smooth;     // 3 real planes
+  float* rho;        // 1 real plane
+  float* khat;       // N * N * (N/2 + 1)
+  uint32_t* key;
+  uint32_t* perm;
+  int* count;
+  int* fill;
+  int* tile_start;
+  int* chunk_start;
+};
+
+bool size_supported(int n) {
+  switch (n) {
+#define MOND_CASE(k) case k:
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+    return true;
+    default: return false;
+  }
+}
+
+int ball_reach(double sigma) {
+  double lim = 16.0 * sigma * sigma;
+  int r = 0;
+  while ((double)((r + 1) * (r + 1)) < lim) r++;
+  return r;
+}
+
+// Layout of the workspace; when base is null only the size is computed.
+size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  const int64_t n3 = (int64_t)n * n * n;
+  const int64_t plane = (int64_t)n * n * (n / 2 + 2);
+  const int ntx = n / parts::TILE;
+  const int ntile = ntx * ntx * ntx;
+  const int lw = 2 * r + 1;
+  Workspace t{};
+  t.status = (uint32_t*)take(256);
+  t.red = (double*)take(sizeof(double) * 256);
+  t.isum = (unsigned long long*)take(64);
+  t.emax = (int*)take(64);
+  t.counters = (int*)take(256);
+  t.tw = (float2*)take(sizeof(float2) * n);
+  t.kv = (float*)take(sizeof(float) * n);
+  t.kp = (float*)take(sizeof(float) * n);
+  t.lut = (uint32_t*)take(sizeof(uint32_t) * 65537 * lw);
+  t.ball = (uint32_t*)take(sizeof(uint32_t) * nb);
+  t.dep = (uint64_t*)take(sizeof(uint64_t) * n3);
+  t.W = (float2*)take(sizeof(float2) * 3 * plane);
+  t.A = (float2*)take(sizeof(float2) * 4 * plane);
+  t.gN = (float*)take(sizeof(float) * 3 * n3);
+  t.Hs = (float*)take(sizeof(float) * 3 * n3);
+  t.acc = (float*)take(sizeof(float) * 4 * n3);
+  t.smooth = (float*)take(sizeof(float) * 3 * n3);
+  t.rho = (float*)take(sizeof(float) * n3);
+  t.khat = (float*)take(sizeof(float) * (int64_t)n * n * (n / 2 + 1));
+  t.key = (uint32_t*)take(sizeof(uint32_t) * (maxp > 0 ? maxp : 1));
+  t.perm = (uint32_t*)take(sizeof(uint32_t) * (maxp > 0 ? maxp : 1));
+  t.count = (int*)take(sizeof(int) * (ntile + 2));
+  t.fill = (int*)take(sizeof(int) * (ntile + 2));
+  t.tile_start = (int*)take(sizeof(int) * (ntile + 2));
+  t.chunk_start = (int*)take(sizeof(int) * (ntile + 2));
+  if (w) *w = t;
+  return off;
+}
+
+// Gaussian of Eq. smooth along one axis, width sigma pixels.
+double g1(double u, double sigma) { return exp(-(u * u) / (2.0 * sigma * sigma)) / (sigma * sqrt(2.0 * M_PI)); }
+
+// node-smoothing kernel spectrum: K^(k) = sum_{d in ball} w(d) cos(kx dx s) cos(ky dy s) cos(kz dz s)
+__global__ void k_khat(int n, int r, double sigma, float* khat) {
+  int64_t tot = (int64_t)n * n * (n / 2 + 1);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tot) return;
+  int kx = (int)(i % (n / 2 + 1)), ky = (int)((i / (n / 2 + 1)) % n), kz = (int)(i / ((int64_t)(n / 2 + 1) * n));
+  double lim = 16.0 * sigma * sigma;
+  double ax = 2.0 * M_PI * freq_of(kx, n) / n, ay = 2.0 * M_PI * freq_of(ky, n) / n,
+         az = 2.0 * M_PI * freq_of(kz, n) / n;
+  double norm = 1.0 / (sigma * sqrt(2.0 * M_PI));
+  double sum = 0.0;
+  for (int dz = -r; dz <= r; dz++)
+    for (int dy = -r; dy <= r; dy++) {
+      double wyz = exp(-(double)(dy * dy + dz * dz) / (2.0 * sigma * sigma)) * norm * norm * cos(ay * dy) * cos(az * dz);
+      double row = 0.0;
+      for (int dx = -r; dx <= r; dx++)
+        if ((double)(dx * dx + dy * dy + dz * dz) < lim) row += exp(-(double)(dx * dx) / (2.0 * sigma * sigma)) * norm * cos(ax * dx);
+      sum += wyz * row;
+    }
+  khat[i] = (float)sum;
+}
+
+// FP32 density from the accumulator (same rule as the x-pass).
+__global__ void k_dep_to_rho(int64_t n3, const uint64_t* dep, double scale, float* rho) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    rho[i] = __double2float_rn(__dmul_rn(__ll2double_rn((long long)dep[i]), scale));
+}
+
+__global__ void k_dep_sum(int64_t n3, const uint64_t* dep, unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    acc += dep[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+}  // namespace
+
+struct mond_pm {
+  int n, npad, nf;
+  double box, s, a0, G, sigma;
+  int mu_kind, r, nb;
+  int64_t maxp;
+  cudaStream_t st;
+  Workspace w;
+  int64_t plane;
+  int64_t n3;
+  int ntx, ntile;
+  int sms;
+  // particles
+  int64_t N = 0;
+  int32_t* cell = nullptr;
+  float* off = nullptr;
+  float* vel = nullptr;
+  const float* mass = nullptr;
+  int kacc = 0;
+  bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false;
+  int keep_phi = 0, track_dh = 0, use_graph = 0;
+  int last_iters = 0;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(mond_pm* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(h, MOND_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
+  a.tw = h->w.tw;
+  a.status = h->w.status;
+  a.mu_kind = h->mu_kind;
+  a.a0 = (float)h->a0;
+  a.pstride = h->plane;
+  h->launches++;
+  switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_xpass_##k(mode, a, h->st);
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
+  passes::YArgs a{};
+  a.spec = spec;
+  a.pstride = h->plane;
+  a.tw = h->w.tw;
+  h->launches++;
+  switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_ypass_##k(dir, a, ncomp, h->st);
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
+  passes::ZArgs a{};
+  a.in = in;
+  a.out = out;
+  a.pstride = h->plane;
+  a.nout = nout;
+  a.kv = h->w.kv;
+  a.kp = h->w.kp;
+  a.tw = h->w.tw;
+  a.khat = h->w.khat;
+  a.norm = (float)(1.0 / ((double)h->nf * h->nf * h->nf));
+  a.coef = (float)(4.0 * M_PI * h->G);
+  h->launches++;
+  switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_zpass_##k(mode, a, h->st);
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define PK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(h, MOND_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int read_status(mond_pm* h) {
+  uint32_t st = 0;
+  CK(cudaMemcpyAsync(&st, h->w.status, sizeof st, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (st) CK(cudaMemsetAsync(h->w.status, 0, sizeof(uint32_t), h->st));
+  if (st & ST_TIMEOUT) return fail(h, MOND_ETIMEOUT, "a bounded device wait gave up");
+  if (st & ST_NAN) return fail(h, MOND_ENAN, "a non-finite value appeared in a field or a particle");
+  if (st & ST_DOMAIN) return fail(h, MOND_EDOMAIN, "a particle's cell or offset was outside the domain and was skipped");
+  if (st & ST_OVERFLOW) return fail(h, MOND_EOVERFLOW, "fixed-point bound violated");
+  return MOND_OK;
+}
+
+int do_bin(mond_pm* h) {
+  parts::BinArgs b{};
+  b.n = h->nf;
+  b.ntx = h->ntx;
+  b.ntile = h->ntile;
+  b.N = h->N;
+  b.cell = h->cell;
+  b.off = h->off;
+  b.mass = h->mass;
+  b.key = h->w.key;
+  b.count = h->w.count;
+  b.fill = h->w.fill;
+  b.tile_start = h->w.tile_start;
+  b.chunk_start = h->w.chunk_start;
+  b.perm = h->w.perm;
+  b.status = h->w.status;
+  CK(cudaMemsetAsync(h->w.count, 0, sizeof(int) * (h->ntile + 2), h->st));
+  CK(cudaMemsetAsync(h->w.fill, 0, sizeof(int) * (h->ntile + 2), h->st));
+  unsigned nb = (unsigned)((h->N + 255) / 256);
+  if (h->N > 0) {
+    parts::k_bin_count<<<nb, 256, 0, h->st>>>(b);
+    h->launches++;
+  }
+  parts::k_bin_scan<<<1, 1024, 0, h->st>>>(b);
+  h->launches++;
+  if (h->N > 0) {
+    parts::k_bin_scatter<<<nb, 256, 0, h->st>>>(b);
+    h->launches++;
+  }
+  CK(cudaGetLastError());
+  return MOND_OK;
+}
+
+size_t dep_smem(mond_pm* h) {
+  int hw = parts::TILE + 2 * h->r;
+  return sizeof(unsigned long long) * (size_t)hw * hw * hw + sizeof(uint32_t) * h->nb;
+}
+size_t gat_smem(mond_pm* h) {
+  int hw = parts::TILE + 2 * h->r;
+  return sizeof(float) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * h->nb;
+}
+
+int do_deposit(mond_pm* h) {
+  CK(cudaMemsetAsync(h->w.dep, 0, sizeof(uint64_t) * h->n3, h->st));
+  int rc = do_bin(h);
+  if (rc) return rc;
+  parts::DepArgs d{};
+  d.n = h->nf;
+  d.ntx = h->ntx;
+  d.ntile = h->ntile;
+  d.r = h->r;
+  d.nb = h->nb;
+  d.cell = h->cell;
+  d.off = h->off;
+  d.mass = h->mass;
+  d.perm = h->w.perm;
+  d.tile_start = h->w.tile_start;
+  d.chunk_start = h->w.chunk_start;
+  d.lut = h->w.lut;
+  d.ball = h->w.ball;
+  d.dep = h->w.dep;
+  d.kacc = h->kacc;
+  d.work_counter = h->w.counters;
+  CK(cudaMemsetAsync(h->w.counters, 0, sizeof(int), h->st));
+  size_t sm = dep_smem(h);
+  CK(cudaFuncSetAttribute(parts::k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  parts::k_deposit<<<h->sms * 4, parts::DEP_NT, sm, h->st>>>(d);
+  h->launches++;
+  CK(cudaGetLastError());
+  h->have_dep = true;
+  h->have_solve = false;
+  return MOND_OK;
+}
+
+int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
+  parts::GatArgs g{};
+  g.n = h->nf;
+  g.ntx = h->ntx;
+  g.ntile = h->ntile;
+  g.r = h->r;
+  g.nb = h->nb;
+  g.cell = h->cell;
+  g.off = h->off;
+  g.vel = h->vel;
+  g.perm = h->w.perm;
+  g.tile_start = h->w.tile_start;
+  g.chunk_start = h->w.chunk_start;
+  g.acc = h->w.acc;
+  g.ball = h->w.ball;
+  g.g_out = g_out;
+  g.dt = (float)dt;
+  g.dt_over_s = (float)(dt / h->s);
+  g.do_kick = kick;
+  g.do_drift = drift;
+  g.inv2s2 = (float)(1.0 / (2.0 * h->sigma * h->sigma));
+  g.gnorm = (float)(1.0 / (h->sigma * sqrt(2.0 * M_PI)));
+  g.work_counter = h->w.counters + 1;
+  g.status = h->w.status;
+  CK(cudaMemsetAsync(h->w.counters + 1, 0, sizeof(int), h->st));
+  size_t sm = gat_smem(h);
+  CK(cudaFuncSetAttribute(parts::k_gather_push, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  parts::k_gather_push<<<h->sms * 2, parts::GAT_NT, sm, h->st>>>(g);
+  h->launches++;
+  CK(cudaGetLastError());
+  return MOND_OK;
+}
+
+// Field solve: the pass sequence of the iteration (see mond_pm_solve_field).
+int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
+  const int nout = h->keep_phi ? 4 : 3;
+  float2* W = h->w.W;
+  float2* A = h->w.A;
+  passes::XArgs x{};
+  x.ncomp = 1;
+  x.spec = W;
+  x.dep = h->w.dep;
+  x.rho_out = h->w.rho;
+  x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
+  PK(xpass(h, passes::X_RHO, x));
+  PK(ypass(h, -1, W, 1));
+  if (K == 0) {
+    PK(zpass(h, passes::Z_NEWTON, W, A, nout));
+    PK(ypass(h, +1, A, nout));
+    passes::XArgs xi{};
+    xi.ncomp = nout;
+    xi.spec = A;
+    xi.real_out = h->w.acc;
+    PK(xpass(h, passes::X_INV, xi));
+    CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
+    h->last_iters = 0;
+    h->have_solve = true;
+    return MOND_OK;
+  }
+  PK(zpass(h, passes::Z_NEWTON, W, W, 3));
+  PK(ypass(h, +1, W, 3));
+  const float* H0 = nullptr;
+  if (warm == MOND_WARM_GUESS) {
+    // project the guess onto its divergence-free part: H state = P_div(guess)
+    passes::XArgs xf{};
+    xf.ncomp = 3;
+    xf.spec = A;
+    xf.real_in = Hguess;
+    PK(xpass(h, passes::X_FWD, xf));
+    PK(ypass(h, -1, A, 3));
+    PK(zpass(h, passes::Z_DIV, A, A, 3));
+    PK(ypass(h, +1, A, 3));
+    passes::XArgs xi{};
+    xi.ncomp = 3;
+    xi.spec = A;
+    xi.real_out = h->w.Hs;
+    PK(xpass(h, passes::X_INV, xi));
+    H0 = h->w.Hs;
+  } else if (warm == MOND_WARM_PREV) {
+    H0 = h->w.Hs;
+  } else if (K == 1 || h->track_dh) {
+    CK(cudaMemsetAsync(h->w.Hs, 0, sizeof(float) * 3 * h->n3, h->st));
+  }
+  if (h->track_dh) CK(cudaMemsetAsync(h->w.red + 32, 0, sizeof(double) * 2 * 64, h->st));
+  passes::XArgs xn{};
+  xn.ncomp = 3;
+  xn.spec = W;
+  xn.gN_out = h->w.gN;
+  xn.H0 = H0;
+  PK(xpass(h, passes::X_NU_FIRST, xn));
+  for (int j = 1; j <= K; j++) {
+    PK(ypass(h, -1, W, 3));
+    const bool last = (j == K);
+    if (last) {
+      PK(zpass(h, passes::Z_FINAL, W, A, nout));
+      PK(ypass(h, +1, A, nout));
+      passes::XArgs xi{};
+      xi.ncomp = nout;
+      xi.spec = A;
+      xi.real_out = h->w.acc;
+      PK(xpass(h, passes::X_INV, xi));
+      if (warm == MOND_WARM_NONE) break;
+    }
+    PK(zpass(h, passes::Z_CURL, W, W, 3));
+    PK(ypass(h, +1, W, 3));
+    passes::XArgs xm{};
+    xm.ncomp = 3;
+    xm.spec = W;
+    xm.gN = h->w.gN;
+    PK(xpass(h, passes::X_MU, xm));
+    PK(ypass(h, -1, W, 3));
+    PK(zpass(h, passes::Z_DIV, W, W, 3));
+    PK(ypass(h, +1, W, 3));
+    if (last) {
+      // warm start: finish the H update so the next solve can begin from it
+      passes::XArgs xi{};
+      xi.ncomp = 3;
+      xi.spec = W;
+      xi.real_out = h->w.Hs;
+      PK(xpass(h, passes::X_INV, xi));
+      break;
+    }
+    passes::XArgs xv{};
+    xv.ncomp = 3;
+    xv.spec = W;
+    xv.gN = h->w.gN;
+    const bool store = h->track_dh || (j == K - 1);
+    xv.Hs_out = store ? h->w.Hs : nullptr;
+    xv.red = h->track_dh ? h->w.red + 32 + 2 * (j - 1) : nullptr;
+    PK(xpass(h, passes::X_NU, xv));
+  }
+  h->last_iters = K;
+  h->have_solve = true;
+  return MOND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mond_pm_workspace_bytes(mond_pm_grid grid, double kernel_width, int64_t max_particles, size_t* bytes) {
+  if (!bytes) return MOND_EINVAL;
+  int nf = grid.n * grid.pad;
+  if ((grid.pad != 1 && grid.pad != 2) || !size_supported(nf) || !(kernel_width >= 0.75) || kernel_width > 2.0 ||
+      max_particles < 0 || max_particles >= (int64_t)1 << 31)
+    return MOND_EINVAL;
+  int r = ball_reach(kernel_width);
+  int nb = 0;
+  for (int dz = -r; dz <= r; dz++)
+    for (int dy = -r; dy <= r; dy++)
+      for (int dx = -r; dx <= r; dx++)
+        if ((double)(dx * dx + dy * dy + dz * dz) < 16.0 * kernel_width * kernel_width) nb++;
+  *bytes = carve(nf, r, nb, max_particles, nullptr, nullptr);
+  return MOND_OK;
+}
+
+int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_kind, double kernel_width,
+                   void* cuda_stream, void* workspace, size_t workspace_bytes, int64_t max_particles,
+                   mond_pm_t* out) {
+  mond_pm* h = nullptr;
+  if (!out) return fail(h, MOND_EINVAL, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  if (mond_pm_workspace_bytes(grid, kernel_width, max_particles, &need) != MOND_OK)
+    return fail(h, MOND_EINVAL, "unsupported grid (n=%d pad=%d) or kernel width %g", grid.n, grid.pad, kernel_width);
+  if (!(box > 0) || !(a0 > 0) || !(G > 0) || mu_kind < 0 || mu_kind > 3)
+    return fail(h, MOND_EINVAL, "box, a0 and G must be positive and mu_kind in 0..3");
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(h, MOND_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < need) return fail(h, MOND_ENOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, need);
+  h = new mond_pm();
+  h->n = grid.n;
+  h->npad = grid.pad;
+  h->nf = grid.n * grid.pad;
+  h->box = box;
+  h->s = box / grid.n;
+  h->a0 = a0;
+  h->G = G;
+  h->sigma = kernel_width;
+  h->mu_kind = mu_kind;
+  h->r = ball_reach(kernel_width);
+  h->maxp = max_particles;
+  h->st = (cudaStream_t)cuda_stream;
+  const int n = h->nf;
+  h->n3 = (int64_t)n * n * n;
+  h->plane = (int64_t)n * n * (n / 2 + 2);
+  h->ntx = n / parts::TILE;
+  h->ntile = h->ntx * h->ntx * h->ntx;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->sms <= 0) h->sms = 1;
+  // ball of taps |d|^2 < (4 sigma)^2 (Sect. 3.1), packed offsets + r
+  std::vector<uint32_t> ball;
+  const double lim = 16.0 * kernel_width * kernel_width;
+  for (int dz = -h->r; dz <= h->r; dz++)
+    for (int dy = -h->r; dy <= h->r; dy++)
+      for (int dx = -h->r; dx <= h->r; dx++)
+        if ((double)(dx * dx + dy * dy + dz * dz) < lim)
+          ball.push_back((uint32_t)(dx + h->r) | ((uint32_t)(dy + h->r) << 8) | ((uint32_t)(dz + h->r) << 16));
+  h->nb = (int)ball.size();
+  carve(n, h->r, h->nb, max_particles, (char*)workspace, &h->w);
+  // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))
+  const int lw = 2 * h->r + 1;
+  std::vector<uint32_t> lut((size_t)65537 * lw);
+  for (int qi = 0; qi < 65537; qi++) {
+    int q = qi - 32768;
+    for (int j = 0; j < lw; j++) {
+      double u = (double)(j - h->r) - (double)q * (1.0 / 65536.0);
+      lut[(size_t)qi * lw + j] = (uint32_t)nearbyint(g1(u, kernel_width) * 16777216.0);
+    }
+  }
+  // twiddles (cos, sin)(2 pi m / n); wave numbers k and kappa = sin(k s)/s per index
+  std::vector<float2> tw(n);
+  std::vector<float> kv(n), kp(n);
+  for (int m = 0; m < n; m++) {
+    double ang = 2.0 * M_PI * m / n;
+    tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    int f = freq_of(m, n);
+    double k = 2.0 * M_PI * f / (n * h->s);
+    kv[m] = (float)k;
+    kp[m] = (2 * m == n) ? 0.0f : (float)(sin(2.0 * M_PI * f / n) / h->s);
+  }
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemcpyAsync(h->w.lut, lut.data(), sizeof(uint32_t) * lut.size(), cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.ball, ball.data(), sizeof(uint32_t) * ball.size(), cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.kv, kv.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.kp, kp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemsetAsync(h->w.status, 0, 256, h->st);
+  e = e ? e : cudaMemsetAsync(h->w.Hs, 0, sizeof(float) * 3 * h->n3, h->st);
+  e = e ? e : cudaMemsetAsync(h->w.dep, 0, sizeof(uint64_t) * h->n3, h->st);
+  e = e ? e : cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    int rc = fail(nullptr, MOND_ECUDA, "create: %s", cudaGetErrorString(e));
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MOND_OK;
+}
+
+int mond_pm_destroy(mond_pm_t h) {
+  if (!h) return MOND_EINVAL;
+  cudaStreamSynchronize(h->st);
+  delete h;
+  return MOND_OK;
+}
+
+int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
+  if (!h) return MOND_EINVAL;
+  switch (option) {
+    case MOND_OPT_KEEP_PHI: h->keep_phi = value ? 1 : 0; return MOND_OK;
+    case MOND_OPT_TRACK_DH: h->track_dh = value ? 1 : 0; return MOND_OK;
+    case MOND_OPT_USE_GRAPH: h->use_graph = value ? 1 : 0; return MOND_OK;
+  }
+  return fail(h, MOND_EINVAL, "unknown option %d", option);
+}
+
+int mond_pm_bind_particles(mond_pm_t h, int64_t N, int32_t* cell, float* offset, float* vel, const float* mass) {
+  if (!h) return MOND_EINVAL;
+  if (N < 0 || N > h->maxp) return fail(h, MOND_EINVAL, "N=%lld exceeds max_particles=%lld", (long long)N, (long long)h->maxp);
+  if (N > 0 && (!cell || !offset || !vel || !mass)) return fail(h, MOND_EINVAL, "null particle array");
+  h->N = N;
+  h->cell = cell;
+  h->off = offset;
+  h->vel = vel;
+  h->mass = mass;
+  // fixed-point scale: N max|m| 2^Kacc <= 2^62, with max|m| < 2^(emax - 126)
+  int emax = 1;
+  if (N > 0) {
+    CK(cudaMemcpyAsync(h->w.emax, &emax, sizeof(int), cudaMemcpyHostToDevice, h->st));
+    int nb = (int)std::min<int64_t>((N + 255) / 256, (int64_t)h->sms * 8);
+    parts::k_mass_exponent<<<nb, 256, 0, h->st>>>(N, mass, h->w.emax);
+    h->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&emax, h->w.emax, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  int L = 0;
+  while (((int64_t)1 << L) < N) L++;
+  h->kacc = 62 - (emax - 126) - L;
+  h->have_dep = false;
+  h->have_solve = false;
+  return MOND_OK;
+}
+
+int mond_pm_deposit(mond_pm_t h) {
+  if (!h) return MOND_EINVAL;
+  if (!h->cell && h->N > 0) return fail(h, MOND_ESTATE, "no particles bound");
+  return do_deposit(h);
+}
+
+int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess) {
+  if (!h) return MOND_EINVAL;
+  if (!h->have_dep) return fail(h, MOND_ESTATE, "solve_field before deposit");
+  if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
+  if (warm < 0 || warm > 2) return fail(h, MOND_EINVAL, "bad warm mode %d", warm);
+  if (warm == MOND_WARM_GUESS && !H_guess) return fail(h, MOND_EINVAL, "MOND_WARM_GUESS needs H_guess");
+  if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
+  return do_solve(h, n_iter, warm, H_guess);
+}
+
+int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out) {
+  if (!h) return MOND_EINVAL;
+  if (!h->have_solve) return fail(h, MOND_ESTATE, "smooth before solve_field");
+  if (!h->have_khat) {
+    int64_t tot = (int64_t)h->nf * h->nf * (h->nf / 2 + 1);
+    k_khat<<<(unsigned)((tot + 255) / 256), 256, 0, h->st>>>(h->nf, h->r, h->sigma, h->w.khat);
+    h->launches++;
+    CK(cudaGetLastError());
+    h->have_khat = true;
+  }
+  passes::XArgs xf{};
+  xf.ncomp = 3;
+  xf.spec = h->w.A;
+  xf.real_in = h->w.acc;
+  PK(xpass(h, passes::X_FWD, xf));
+  PK(ypass(h, -1, h->w.A, 3));
+  PK(zpass(h, passes::Z_SMOOTH, h->w.A, h->w.A, 3));
+  PK(ypass(h, +1, h->w.A, 3));
+  passes::XArgs xi{};
+  xi.ncomp = 3;
+  xi.spec = h->w.A;
+  xi.real_out = h->w.smooth;
+  xi.real_out2 = accel_mesh_out;
+  PK(xpass(h, passes::X_INV, xi));
+  h->have_smooth = true;
+  return MOND_OK;
+}
+
+int mond_pm_gather_push(mond_pm_t h, double dt) {
+  if (!h) return MOND_EINVAL;
+  if (!h->have_solve) return fail(h, MOND_ESTATE, "gather_push before solve_field");
+  int rc = do_gather(h, nullptr, dt, 1, 1);
+  h->have_dep = false;  // particles moved: the binning is stale
+  h->have_solve = false;
+  return rc;
+}
+
+int mond_pm_half_kick(mond_pm_t h, double dt) {
+  if (!h) return MOND_EINVAL;
+  if (!h->have_solve) return fail(h, MOND_ESTATE, "half_kick before solve_field");
+  return do_gather(h, nullptr, dt, 1, 0);
+}
+
+int mond_pm_gather(mond_pm_t h, float* g_out) {
+  if (!h) return MOND_EINVAL;
+  if (!h->have_solve) return fail(h, MOND_ESTATE, "gather before solve_field");
+  if (!g_out) return fail(h, MOND_EINVAL, "g_out is NULL");
+  return do_gather(h, g_out, 0.0, 0, 0);
+}
+
+int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
+  if (!h) return MOND_EINVAL;
+  int rc = mond_pm_deposit(h);
+  if (rc) return rc;
+  rc = mond_pm_solve_field(h, n_iter, warm, nullptr);
+  if (rc) return rc;
+  return mond_pm_gather_push(h, dt);
+}
+
+int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cell_host, float* offset_host,
+                      float* vel_host) {
+  if (!h) return MOND_EINVAL;
+  if (h->N > 0 && (!cell_host || !offset_host || !vel_host)) return fail(h, MOND_EINVAL, "null host array");
+  const size_t N = (size_t)h->N;
+  CK(cudaMemcpyAsync(h->cell, cell_host, sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->off, offset_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->vel, vel_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->st));
+  int rc = mond_pm_step(h, dt, n_iter, warm);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(cell_host, h->cell, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(offset_host, h->off, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(vel_host, h->vel, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));
+  return read_status(h);
+}
+
+int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out) {
+  if (!h || !out) return MOND_EINVAL;
+  memset(out, 0, sizeof *out);
+  CK(cudaMemsetAsync(h->w.red, 0, sizeof(double) * 32, h->st));
+  CK(cudaMemsetAsync(h->w.isum, 0, sizeof(unsigned long long), h->st));
+  if (h->N > 0) {
+    int nb = (int)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 8);
+    parts::k_particle_diag<<<nb, 256, 0, h->st>>>(h->nf, h->s, h->N, h->cell, h->off, h->vel, h->mass, h->w.red);
+    h->launches++;
+  }
+  k_dep_sum<<<h->sms * 4, 256, 0, h->st>>>(h->n3, h->w.dep, h->w.isum);
+  h->launches++;
+  bool epot = h->have_solve && h->keep_phi;
+  if (epot) {
+    parts::k_plane_sum<<<h->sms * 4, 256, 0, h->st>>>(h->n3, h->w.rho, h->w.acc + 3 * h->n3, h->w.red + 16);
+    h->launches++;
+  }
+  CK(cudaGetLastError());
+  double red[32];
+  double dh[128];
+  unsigned long long isum = 0;
+  CK(cudaMemcpyAsync(red, h->w.red, sizeof red, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(dh, h->w.red + 32, sizeof dh, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&isum, h->w.isum, sizeof isum, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  out->mass = red[0];
+  for (int d = 0; d < 3; d++) {
+    out->momentum[d] = red[1 + d];
+    out->com[d] = red[0] > 0 ? red[4 + d] / red[0] : 0.0;
+  }
+  // L about the centre of mass = L about the origin - R x P
+  const double* R = out->com;
+  const double* P = out->momentum;
+  out->ang_mom[0] = red[7] - (R[1] * P[2] - R[2] * P[1]);
+  out->ang_mom[1] = red[8] - (R[2] * P[0] - R[0] * P[2]);
+  out->ang_mom[2] = red[9] - (R[0] * P[1] - R[1] * P[0]);
+  out->e_kin = red[10];
+  out->rho_mass = (double)(long long)isum * ldexp(1.0, -h->kacc);
+  const double s3 = h->s * h->s * h->s;
+  out->e_pot = epot ? red[16] * s3 : NAN;
+  out->n_iter_done = h->last_iters;
+  for (int j = 0; j < 64; j++)
+    out->dH[j] = (h->track_dh && j < h->last_iters - 1 && dh[2 * j + 1] > 0) ? sqrt(dh[2 * j] / dh[2 * j + 1]) : NAN;
+  return read_status(h);
+}
+
+int mond_pm_get_field(mond_pm_t h, int which, float* dst) {
+  if (!h || !dst) return MOND_EINVAL;
+  const float* src = nullptr;
+  int planes = 1;
+  switch (which) {
+    case MOND_FIELD_RHO:
+      if (!h->have_dep && !h->have_solve) return fail(h, MOND_ESTATE, "no deposit yet");
+      k_dep_to_rho<<<h->sms * 4, 256, 0, h->st>>>(h->n3, h->w.dep, ldexp(1.0, -h->kacc) / (h->s * h->s * h->s), h->w.rho);
+      h->launches++;
+      src = h->w.rho;
+      break;
+    case MOND_FIELD_GN: src = h->w.gN; planes = 3; break;
+    case MOND_FIELD_H: src = h->w.Hs; planes = 3; break;
+    case MOND_FIELD_PHI:
+      if (!h->keep_phi) return fail(h, MOND_ESTATE, "phi needs MOND_OPT_KEEP_PHI before the solve");
+      src = h->w.acc + 3 * h->n3;
+      break;
+    case MOND_FIELD_ACC: src = h->w.acc; planes = 3; break;
+    case MOND_FIELD_SMOOTH:
+      if (!h->have_smooth) return fail(h, MOND_ESTATE, "no smooth() yet");
+      src = h->w.smooth;
+      planes = 3;
+      break;
+    default: return fail(h, MOND_EINVAL, "unknown field %d", which);
+  }
+  CK(cudaMemcpyAsync(dst, src, sizeof(float) * planes * h->n3, cudaMemcpyDeviceToDevice, h->st));
+  return read_status(h);
+}
+
+int mond_pm_get_deposit_acc(mond_pm_t h, uint64_t* dst, int32_t* kacc) {
+  if (!h || !dst) return MOND_EINVAL;
+  CK(cudaMemcpyAsync(dst, h->w.dep, sizeof(uint64_t) * h->n3, cudaMemcpyDeviceToDevice, h->st));
+  if (kacc) *kacc = h->kacc;
+  return read_status(h);
+}
+
+int mond_pm_sync(mond_pm_t h) {
+  if (!h) return MOND_EINVAL;
+  return read_status(h);
+}
+
+const char* mond_pm_last_error(mond_pm_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t mond_pm_kernel_launches(mond_pm_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

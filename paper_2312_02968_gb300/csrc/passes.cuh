@@ -1,0 +1,500 @@
+// passes.cuh -- the mesh passes of the field solve (Sect. 2.1 iteration,
+// App. Flow steps 3-9), as templates over the FFT-domain side N.
+//
+// Data layout in HBM:
+//  real planes     float [z][y][x], N^3 values (x fastest)
+//  spectral planes float2 [z][y][kx], kx = 0..N/2 in rows of SP = N/2 + 2
+//                  complex (16-byte aligned rows); y and z are either real
+//                  coordinates or frequencies depending on the stage.
+// A 3-D transform is an x-pass (R2C / C2R on contiguous lines), a y-pass and
+// a z-pass (C2C on strided lines, tiles of P adjacent kx columns). The
+// pointwise steps of the iteration (nu, mu, H = F - g_N) live inside x-passes;
+// the spectral operators (Poisson, projections, gradient) inside z-passes,
+// between the forward and the inverse z transform. Transforms are
+// unnormalised; each z-pass multiplies by 1/N^3, the product of the s^3 and
+// L^-3 of App. Fourier.
+#pragma once
+#include "fft.cuh"
+
+namespace passes {
+
+constexpr int NT = 256;  // threads per CTA for every pass
+
+template <int N>
+struct XCfg {
+  static constexpr int L = N >= 384 ? 8 : 16;  // lines per CTA
+  static constexpr int LP = L + 1;             // padded line pitch in shared memory (bank spread)
+  static constexpr int H = N / 2;              // complex FFT length of the real transform
+  static constexpr int ROWS = H + 1;           // spectral positions 0..N/2
+  static constexpr int SP = N / 2 + 2;
+};
+
+template <int N>
+struct YZCfg {
+  static constexpr int P = N >= 384 ? 8 : 16;    // kx columns per tile
+  static constexpr int SP = N / 2 + 2;
+  static constexpr int NX = N / 2 + 1;           // valid kx columns
+  static constexpr int NBLK = (NX + P - 1) / P;  // tiles across kx
+};
+
+// x-pass modes
+enum XMode {
+  X_RHO = 0,       // int64 deposit -> FP32 density (exact rule), clear, R2C
+  X_NU_FIRST = 1,  // C2R g_N (store), F = g_N + H0, g_M = nu(F) F, R2C
+  X_NU = 2,        // C2R H (optionally store, track dH), F = g_N + H, g_M = nu(F) F, R2C
+  X_MU = 3,        // C2R g_M, F = mu(g_M) g_M, H = F - g_N, R2C
+  X_INV = 4,       // C2R -> real planes
+  X_FWD = 5        // real planes -> R2C
+};
+
+// z-pass modes
+enum ZMode {
+  Z_NEWTON = 0,      // 1 -> 3 (+phi): g_N^ = i kappa 4 pi G A rho^
+  Z_CURL = 1,        // 3 -> 3: curl-free projection
+  Z_DIV = 2,         // 3 -> 3: divergence-free projection
+  Z_FINAL = 3,       // 3 -> 3 (+phi) to out: a^ = -i kappa phi^, phi^ = i A k'.g^
+  Z_SMOOTH = 5       // 3 -> 3: times the smoothing kernel spectrum
+};
+
+struct XArgs {
+  float2* spec;          // spectral planes in/out (in place), component c at spec + c * pstride
+  int64_t pstride;       // spectral plane stride (complex elements)
+  float* real_out;       // X_INV destinations: compact real planes, stride N^3
+  float* real_out2;      // X_INV second destinations (may be null)
+  const float* real_in;  // X_FWD sources, stride N^3
+  const float* gN;       // 3 real planes
+  float* gN_out;         // X_NU_FIRST: where g_N is written
+  const float* H0;       // X_NU_FIRST: warm H (3 real planes) or null
+  float* Hs_out;         // X_NU: store H (3 real planes) or null
+  uint64_t* dep;         // X_RHO: accumulator
+  float* rho_out;        // X_RHO: density plane (may be null)
+  double rho_scale;      // X_RHO: 2^-Kacc / s^3
+  double* red;           // dH reduction slots (2 doubles) or null
+  const float2* tw;      // twiddles, N entries
+  uint32_t* status;
+  int mu_kind;
+  float a0;
+  int ncomp;
+};
+
+struct ZArgs {
+  float2* in;       // input planes, component c at in + c * pstride
+  float2* out;      // Z_NEWTON / Z_FINAL outputs (same stride)
+  int64_t pstride;
+  int nout;         // 3 or 4 (4: also phi)
+  const float* kv;  // k values per index (N)
+  const float* kp;  // kappa = sin(k s)/s per index (N)
+  const float2* tw;
+  const float* khat;  // smoothing kernel spectrum [z][y][kx] (N * N * (N/2+1))
+  float norm;         // 1/N^3
+  float coef;         // Z_NEWTON: 4 pi G
+};
+
+struct YArgs {
+  float2* spec;  // component c at spec + c * pstride
+  int64_t pstride;
+  const float2* tw;
+};
+
+// ---------------------------------------------------------------------------
+// Interpolation functions (Eq. mu and the pair relation of Sect. 2.1), FP32.
+// nu_factor returns |g_M| / |F| for |F| = Fm; mu_factor returns |F| / |g_M|.
+// Both are 0 at zero field.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float nu_factor(int kind, float Fm, float a0) {
+  if (!(Fm > 0.0f)) return 0.0f;
+  float y = Fm / a0;
+  switch (kind) {
+    case 0: return sqrtf(a0 / Fm);                       // deep: 1/sqrt(y)
+    case 1: return 0.5f + sqrtf(0.25f + a0 / Fm);        // simple
+    case 2:                                              // standard
+      if (y > 1.0f) return sqrtf(0.5f + 0.5f * sqrtf(1.0f + 4.0f / (y * y)));
+      return sqrtf((y + sqrtf(y * y + 4.0f)) / (2.0f * y));
+    default: return 1.0f;
+  }
+}
+__device__ __forceinline__ float mu_factor(int kind, float gm, float a0) {
+  float x = gm / a0;
+  switch (kind) {
+    case 0: return x;                                    // deep
+    case 1: return x / (1.0f + x);                       // simple
+    case 2:                                              // standard
+      if (x > 1.0f) return 1.0f / sqrtf(1.0f + 1.0f / (x * x));
+      return x / sqrtf(1.0f + x * x);
+    default: return 1.0f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x-pass
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict__ g, int64_t line0, int tid) {
+  using C = XCfg<N>;
+  constexpr int Q = C::SP / 2;  // float4 per line
+  const float4* src = reinterpret_cast<const float4*>(g + line0 * C::SP);
+  for (int i = tid; i < C::L * Q; i += NT) {
+    int l = i / Q, kk = (i % Q) * 2;
+    float4 v = __ldcs(src + i);
+    sm[kk * C::LP + l] = make_float2(v.x, v.y);
+    if (kk + 1 <= C::H) sm[(kk + 1) * C::LP + l] = make_float2(v.z, v.w);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void x_store_spec(const float2* sm, float2* __restrict__ g, int64_t line0, int tid) {
+  using C = XCfg<N>;
+  constexpr int Q = C::SP / 2;
+  float4* dst = reinterpret_cast<float4*>(g + line0 * C::SP);
+  for (int i = tid; i < C::L * Q; i += NT) {
+    int l = i / Q, kk = (i % Q) * 2;
+    float2 a = sm[kk * C::LP + l];
+    float2 b = (kk + 1 <= C::H) ? sm[(kk + 1) * C::LP + l] : make_float2(0.f, 0.f);
+    __stcs(dst + i, make_float4(a.x, a.y, b.x, b.y));
+  }
+}
+
+// Half-spectrum X[0..N/2] -> Y[0..N/2-1] = 2E + 2iO (see x_post for E, O);
+// a length-N/2 inverse transform of Y then yields x[2j] + i x[2j+1].
+// The imaginary parts of X[0] and X[N/2] are dropped (real part of the inverse).
+template <int N>
+__device__ __forceinline__ void x_pre_c2r(float2* sm, const float2* tw, int tid) {
+  using C = XCfg<N>;
+  constexpr int NP = N / 4 + 1;  // pairs (k, N/2 - k), k = 0..N/4
+  for (int i = tid; i < NP * C::L; i += NT) {
+    int l = i % C::L, k = i / C::L;
+    if (k == 0) {
+      float x0 = sm[0 * C::LP + l].x, xn = sm[C::H * C::LP + l].x;
+      sm[0 * C::LP + l] = make_float2(x0 + xn, x0 - xn);
+    } else {
+      int k2 = C::H - k;
+      float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
+      float2 w = tw[k];  // e^{+2 pi i k / N}
+      float2 ya = cadd(cadd(a, cconj(b)), cmul_i<1>(cmul(w, csub(a, cconj(b)))));
+      if (k2 != k) {
+        float2 w2 = make_float2(-w.x, w.y);  // e^{+2 pi i (N/2-k)/N} = -conj(w)
+        float2 yb = cadd(cadd(b, cconj(a)), cmul_i<1>(cmul(w2, csub(b, cconj(a)))));
+        sm[k2 * C::LP + l] = yb;
+      }
+      sm[k * C::LP + l] = ya;
+    }
+  }
+  __syncthreads();
+}
+
+// Z = DFT_{N/2}(x[2j] + i x[2j+1]) -> X[k] = E[k] + W^k O[k], k = 0..N/2,
+// E = (Z[k] + conj Z[N/2-k])/2, O = (Z[k] - conj Z[N/2-k])/(2i), W = e^{-2 pi i/N}.
+template <int N>
+__device__ __forceinline__ void x_post_r2c(float2* sm, const float2* tw, int tid) {
+  using C = XCfg<N>;
+  constexpr int NP = N / 4 + 1;
+  for (int i = tid; i < NP * C::L; i += NT) {
+    int l = i % C::L, k = i / C::L;
+    if (k == 0) {
+      float2 z = sm[0 * C::LP + l];
+      sm[0 * C::LP + l] = make_float2(z.x + z.y, 0.f);
+      sm[C::H * C::LP + l] = make_float2(z.x - z.y, 0.f);
+    } else {
+      int k2 = C::H - k;
+      float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
+      float2 w = tw[k];               // (cos, sin)(2 pi k/N)
+      float2 wc = cconj(w);           // e^{-2 pi i k/N}
+      float2 e = cscale(cadd(a, cconj(b)), 0.5f);
+      float2 d = cscale(csub(a, cconj(b)), 0.5f);
+      float2 xa = csub(e, cmul_i<1>(cmul(wc, d)));  // E - i W^k (a - conj b)/2
+      if (k2 != k) {
+        float2 e2 = cscale(cadd(b, cconj(a)), 0.5f);
+        float2 d2 = cscale(csub(b, cconj(a)), 0.5f);
+        float2 xb = cadd(e2, cmul_i<1>(cmul(w, d2)));  // X[N/2-k]
+        sm[k2 * C::LP + l] = xb;
+      }
+      sm[k * C::LP + l] = xa;
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
+  using C = XCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;                       // N twiddles
+  float2* buf = smem + N;                  // ncomp tiles of ROWS x LP
+  constexpr int TILE = C::ROWS * C::LP;
+  const int tid = threadIdx.x;
+  const int64_t line0 = (int64_t)blockIdx.x * C::L;
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+  const int nc = (MODE == X_RHO) ? 1 : a.ncomp;
+
+  constexpr bool INV = (MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_INV);
+  constexpr bool FWD = (MODE == X_RHO || MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_FWD);
+
+  if constexpr (INV) {
+    for (int c = 0; c < nc; c++) x_load_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
+    __syncthreads();
+    for (int c = 0; c < nc; c++) {
+      x_pre_c2r<N>(buf + c * TILE, tw, tid);
+      fftk::fft<C::H, +1, C::L, NT>(buf + c * TILE, C::LP, 1, tw, 2, tid);
+    }
+  }
+
+  // Pointwise stage on real samples: point (j, l) holds x[2j], x[2j+1] of line l.
+  const int64_t rbase = line0 * N;  // real index of the first sample of the tile
+  float sq_dh = 0.f, sq_gn = 0.f;
+  bool bad = false;
+  for (int i = tid; i < C::L * C::H; i += NT) {
+    int j = i % C::H, l = i / C::H;
+    int64_t ri = rbase + (int64_t)l * N + 2 * j;
+    float2* const p0 = buf + j * C::LP + l;  // component c at p0 + c * TILE
+    if constexpr (MODE == X_RHO) {
+      ulonglong2 u = *reinterpret_cast<const ulonglong2*>(a.dep + ri);
+      float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.x), a.rho_scale));
+      float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.y), a.rho_scale));
+      *reinterpret_cast<ulonglong2*>(a.dep + ri) = make_ulonglong2(0ull, 0ull);
+      if (a.rho_out) *reinterpret_cast<float2*>(a.rho_out + ri) = make_float2(r0, r1);
+      *p0 = make_float2(r0, r1);
+    } else if constexpr (MODE == X_FWD) {
+      for (int c = 0; c < nc; c++) p0[c * TILE] = *reinterpret_cast<const float2*>(a.real_in + (int64_t)c * N * N * N + ri);
+    } else if constexpr (MODE == X_INV) {
+      for (int c = 0; c < nc; c++) {
+        float2 v = p0[c * TILE];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        *reinterpret_cast<float2*>(a.real_out + (int64_t)c * N * N * N + ri) = v;
+        if (a.real_out2) *reinterpret_cast<float2*>(a.real_out2 + (int64_t)c * N * N * N + ri) = v;
+      }
+    } else {
+      // three components, two samples each
+      float v[3][2], gn[3][2];
+      for (int c = 0; c < 3; c++) {
+        float2 t = p0[c * TILE];
+        v[c][0] = t.x;
+        v[c][1] = t.y;
+      }
+      if constexpr (MODE == X_NU_FIRST) {
+        // input is g_N; store it; F = g_N + H0
+        for (int c = 0; c < 3; c++) {
+          *reinterpret_cast<float2*>(a.gN_out + (int64_t)c * N * N * N + ri) = make_float2(v[c][0], v[c][1]);
+          gn[c][0] = v[c][0];
+          gn[c][1] = v[c][1];
+          float2 h0 = a.H0 ? *reinterpret_cast<const float2*>(a.H0 + (int64_t)c * N * N * N + ri)
+                           : make_float2(0.f, 0.f);
+          v[c][0] += h0.x;
+          v[c][1] += h0.y;
+        }
+      } else {
+        for (int c = 0; c < 3; c++) {
+          float2 t = *reinterpret_cast<const float2*>(a.gN + (int64_t)c * N * N * N + ri);
+          gn[c][0] = t.x;
+          gn[c][1] = t.y;
+        }
+      }
+      if constexpr (MODE == X_NU) {
+        // input is H after the divergence-free projection
+        if (a.Hs_out) {
+          for (int c = 0; c < 3; c++) {
+            float* hp = a.Hs_out + (int64_t)c * N * N * N + ri;
+            if (a.red) {
+              float2 old = *reinterpret_cast<const float2*>(hp);
+              float d0 = v[c][0] - old.x, d1 = v[c][1] - old.y;
+              sq_dh += d0 * d0 + d1 * d1;
+              sq_gn += gn[c][0] * gn[c][0] + gn[c][1] * gn[c][1];
+            }
+            *reinterpret_cast<float2*>(hp) = make_float2(v[c][0], v[c][1]);
+          }
+        }
+        for (int c = 0; c < 3; c++) {
+          v[c][0] += gn[c][0];
+          v[c][1] += gn[c][1];
+        }
+      }
+      for (int e = 0; e < 2; e++) {
+        float m2 = v[0][e] * v[0][e] + v[1][e] * v[1][e] + v[2][e] * v[2][e];
+        float mag = sqrtf(m2);
+        float f;
+        if constexpr (MODE == X_MU) f = mu_factor(a.mu_kind, mag, a.a0);
+        else f = nu_factor(a.mu_kind, mag, a.a0);
+        for (int c = 0; c < 3; c++) {
+          float o = f * v[c][e];
+          if constexpr (MODE == X_MU) o -= gn[c][e];  // H = F - g_N
+          v[c][e] = o;
+        }
+        bad |= !isfinite(mag);
+      }
+      for (int c = 0; c < 3; c++) p0[c * TILE] = make_float2(v[c][0], v[c][1]);
+    }
+  }
+  if (bad) set_status(a.status, ST_NAN);
+  if (MODE == X_NU && a.red && a.Hs_out) {
+    // per-CTA partial sums of |dH|^2 and |g_N|^2
+    for (int o = 16; o > 0; o >>= 1) {
+      sq_dh += __shfl_xor_sync(0xffffffffu, sq_dh, o);
+      sq_gn += __shfl_xor_sync(0xffffffffu, sq_gn, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicAdd(a.red, (double)sq_dh);
+      atomicAdd(a.red + 1, (double)sq_gn);
+    }
+  }
+
+  if constexpr (FWD) {
+    __syncthreads();
+    for (int c = 0; c < nc; c++) {
+      fftk::fft<C::H, -1, C::L, NT>(buf + c * TILE, C::LP, 1, tw, 2, tid);
+      x_post_r2c<N>(buf + c * TILE, tw, tid);
+    }
+    for (int c = 0; c < nc; c++) x_store_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y-pass: C2C along y for one component per CTA, tile N (y) x P (kx).
+// grid (NBLK, N (z), ncomp)
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void yz_load(float2* sm, const float2* __restrict__ g, int64_t row_stride, int col0,
+                                        int tid) {
+  using C = YZCfg<N>;
+  constexpr int Q = C::P / 2;  // float4 per row
+  int ncol = C::SP - col0;     // columns remaining in the row (includes the pad column)
+  int q_valid = ncol >= C::P ? Q : (ncol + 1) / 2;
+  for (int i = tid; i < N * Q; i += NT) {
+    int row = i / Q, q = i % Q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < q_valid) v = __ldcs(reinterpret_cast<const float4*>(g + row * row_stride + col0) + q);
+    sm[row * C::P + 2 * q] = make_float2(v.x, v.y);
+    sm[row * C::P + 2 * q + 1] = make_float2(v.z, v.w);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void yz_store(const float2* sm, float2* __restrict__ g, int64_t row_stride, int col0,
+                                         int tid) {
+  using C = YZCfg<N>;
+  constexpr int Q = C::P / 2;
+  int ncol = C::SP - col0;
+  int q_valid = ncol >= C::P ? Q : (ncol + 1) / 2;
+  for (int i = tid; i < N * Q; i += NT) {
+    int row = i / Q, q = i % Q;
+    if (q < q_valid) {
+      float2 a = sm[row * C::P + 2 * q], b = sm[row * C::P + 2 * q + 1];
+      __stcs(reinterpret_cast<float4*>(g + row * row_stride + col0) + q, make_float4(a.x, a.y, b.x, b.y));
+    }
+  }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(NT) k_ypass(YArgs a) {
+  using C = YZCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* tile = smem + N;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+  const int col0 = blockIdx.x * C::P;
+  const int z = blockIdx.y;
+  float2* base = a.spec + blockIdx.z * a.pstride + (int64_t)z * N * C::SP;
+  yz_load<N>(tile, base, C::SP, col0, tid);
+  __syncthreads();
+  fftk::fft<N, DIR, C::P, NT>(tile, C::P, 1, tw, 1, tid);
+  yz_store<N>(tile, base, C::SP, col0, tid);
+}
+
+// ---------------------------------------------------------------------------
+// z-pass: forward z, spectral operator, inverse z. grid (NBLK, N (y)).
+// ---------------------------------------------------------------------------
+template <int N, int MODE>
+__global__ void __launch_bounds__(NT) k_zpass(ZArgs a) {
+  using C = YZCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float* kv = reinterpret_cast<float*>(smem + N);
+  float* kp = kv + N;
+  float2* tile = smem + 2 * N;  // tiles of N x P
+  constexpr int T = N * C::P;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NT) {
+    tw[i] = a.tw[i];
+    kv[i] = a.kv[i];
+    kp[i] = a.kp[i];
+  }
+  const int col0 = blockIdx.x * C::P;
+  const int y = blockIdx.y;
+  const int64_t rs = (int64_t)N * C::SP;  // z row stride
+  const int64_t off = (int64_t)y * C::SP;
+  constexpr int NIN = (MODE == Z_NEWTON) ? 1 : 3;
+  for (int c = 0; c < NIN; c++) yz_load<N>(tile + c * T, a.in + c * a.pstride + off, rs, col0, tid);
+  __syncthreads();
+  for (int c = 0; c < NIN; c++) fftk::fft<N, -1, C::P, NT>(tile + c * T, C::P, 1, tw, 1, tid);
+
+  // spectral operator at (kx = col, ky = y, kz = row)
+  const float ky = kv[y];
+  const bool ny = (y == N / 2);
+  const float kpy = kp[y];
+  int nout_extra = 0;
+  if constexpr (MODE == Z_NEWTON || MODE == Z_FINAL) nout_extra = a.nout;
+  for (int i = tid; i < T; i += NT) {
+    int row = i / C::P, cc = i % C::P;
+    int col = col0 + cc;
+    if (col > N / 2) continue;
+    float kx = kv[col], kz = kv[row];
+    bool nx = (col == N / 2), nz = (row == N / 2);
+    float kk = kx * kx + ky * ky + kz * kz;
+    float A = kk > 0.f ? 1.0f / kk : 0.f;
+    float kpx = kp[col], kpz = kp[row];
+    if constexpr (MODE == Z_NEWTON) {
+      float2 r = tile[i];
+      float f = a.coef * A * a.norm;  // 4 pi G A / N^3
+      float2 ir = cmul_i<1>(r);       // i rho^
+      tile[i] = cscale(ir, f * kpx);
+      tile[T + i] = cscale(ir, f * kpy);
+      tile[2 * T + i] = cscale(ir, f * kpz);
+      if (nout_extra == 4) tile[3 * T + i] = cscale(r, -f);  // phi_N^ = -4 pi G A rho^
+    } else if constexpr (MODE == Z_SMOOTH) {
+      int64_t kidx = ((int64_t)row * N + y) * (N / 2 + 1) + col;
+      float f = a.khat[kidx] * a.norm;
+      for (int c = 0; c < 3; c++) tile[c * T + i] = cscale(tile[c * T + i], f);
+    } else {
+      float2 g0 = tile[i], g1 = tile[T + i], g2 = tile[2 * T + i];
+      float k3[3] = {kx, ky, kz};
+      bool n3[3] = {nx, ny, nz};
+      if constexpr (MODE == Z_FINAL) {
+        // phi^ = i A sum_b k'_b g_b (k'_b = 0 on the Nyquist plane of axis b)
+        float2 S = make_float2(0.f, 0.f);
+        float2 gg[3] = {g0, g1, g2};
+        for (int b = 0; b < 3; b++)
+          if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
+        float f = A * a.norm;
+        float2 aS = cscale(S, f);
+        // a^ = -i kappa phi^ = kappa A S
+        float2* dst = tile;
+        dst[i] = cscale(aS, kpx);
+        dst[T + i] = cscale(aS, kpy);
+        dst[2 * T + i] = cscale(aS, kpz);
+        if (nout_extra == 4) dst[3 * T + i] = cmul_i<1>(aS);
+      }
+      if constexpr (MODE == Z_CURL || MODE == Z_DIV) {
+        // P_ab = k_a k_b A, off-diagonal terms dropped when exactly one of
+        // a, b sits on its Nyquist plane (real part of the inverse transform)
+        float2 gg[3] = {g0, g1, g2};
+        float2 o[3];
+        for (int aa = 0; aa < 3; aa++) {
+          float2 t = make_float2(0.f, 0.f);
+          for (int b = 0; b < 3; b++)
+            if (aa == b || n3[aa] == n3[b]) t = cadd(t, cscale(gg[b], k3[aa] * k3[b] * A));
+          o[aa] = (MODE == Z_DIV) ? csub(gg[aa], t) : t;
+        }
+        for (int c = 0; c < 3; c++) tile[c * T + i] = cscale(o[c], a.norm);
+      }
+    }
+  }
+  __syncthreads();
+  int nfin = (MODE == Z_NEWTON || MODE == Z_FINAL) ? a.nout : 3;
+  for (int c = 0; c < nfin; c++) fftk::fft<N, +1, C::P, NT>(tile + c * T, C::P, 1, tw, 1, tid);
+  if constexpr (MODE == Z_NEWTON || MODE == Z_FINAL) {
+    for (int c = 0; c < a.nout; c++) yz_store<N>(tile + c * T, a.out + c * a.pstride + off, rs, col0, tid);
+  } else {
+    for (int c = 0; c < 3; c++) yz_store<N>(tile + c * T, a.in + c * a.pstride + off, rs, col0, tid);
+  }
+}
+
+}  // namespace passes

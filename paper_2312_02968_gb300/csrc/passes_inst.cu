@@ -1,0 +1,84 @@
+// passes_inst.cu -- host launchers of the mesh passes for one FFT-domain side
+// N = MOND_N (this file is compiled once per supported size, in parallel).
+#include "passes.cuh"
+#include "launch.h"
+
+#ifndef MOND_N
+#error "compile with -DMOND_N=<size>"
+#endif
+
+namespace {
+using namespace passes;
+constexpr int N = MOND_N;
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+size_t x_smem(int nc) { return sizeof(float2) * (N + (size_t)nc * XCfg<N>::ROWS * XCfg<N>::LP); }
+size_t y_smem() { return sizeof(float2) * (N + (size_t)N * YZCfg<N>::P); }
+size_t z_smem(int ntiles) { return sizeof(float2) * (2 * N + (size_t)ntiles * N * YZCfg<N>::P); }
+
+template <int MODE>
+cudaError_t launch_x(const XArgs& a, cudaStream_t st) {
+  int nc = (MODE == X_RHO) ? 1 : a.ncomp;
+  size_t sm = x_smem(nc);
+  cudaError_t e = set_smem(k_xpass<N, MODE>, x_smem(4));
+  if (e != cudaSuccess) return e;
+  int64_t nlines = (int64_t)N * N;
+  k_xpass<N, MODE><<<(unsigned)(nlines / XCfg<N>::L), NT, sm, st>>>(a, nlines);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_z(const ZArgs& a, cudaStream_t st) {
+  int ntiles = (MODE == Z_NEWTON || MODE == Z_FINAL) ? (a.nout > 3 ? 4 : 3) : 3;
+  cudaError_t e = set_smem(k_zpass<N, MODE>, z_smem(4));
+  if (e != cudaSuccess) return e;
+  dim3 grid(YZCfg<N>::NBLK, N);
+  k_zpass<N, MODE><<<grid, NT, z_smem(ntiles), st>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+#define CAT2(a, b) a##b
+#define CAT(a, b) CAT2(a, b)
+
+cudaError_t CAT(mond_xpass_, MOND_N)(int mode, const passes::XArgs& a, cudaStream_t st) {
+  switch (mode) {
+    case X_RHO: return launch_x<X_RHO>(a, st);
+    case X_NU_FIRST: return launch_x<X_NU_FIRST>(a, st);
+    case X_NU: return launch_x<X_NU>(a, st);
+    case X_MU: return launch_x<X_MU>(a, st);
+    case X_INV: return launch_x<X_INV>(a, st);
+    case X_FWD: return launch_x<X_FWD>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t CAT(mond_ypass_, MOND_N)(int dir, const passes::YArgs& a, int ncomp, cudaStream_t st) {
+  dim3 grid(YZCfg<N>::NBLK, N, ncomp);
+  size_t sm = y_smem();
+  if (dir < 0) {
+    cudaError_t e = set_smem(k_ypass<N, -1>, sm);
+    if (e != cudaSuccess) return e;
+    k_ypass<N, -1><<<grid, NT, sm, st>>>(a);
+  } else {
+    cudaError_t e = set_smem(k_ypass<N, +1>, sm);
+    if (e != cudaSuccess) return e;
+    k_ypass<N, +1><<<grid, NT, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t CAT(mond_zpass_, MOND_N)(int mode, const passes::ZArgs& a, cudaStream_t st) {
+  switch (mode) {
+    case Z_NEWTON: return launch_z<Z_NEWTON>(a, st);
+    case Z_CURL: return launch_z<Z_CURL>(a, st);
+    case Z_DIV: return launch_z<Z_DIV>(a, st);
+    case Z_FINAL: return launch_z<Z_FINAL>(a, st);
+    case Z_SMOOTH: return launch_z<Z_SMOOTH>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,251 @@
+"""GPU path vs the CPU oracle, element by element on the same seeded inputs.
+
+Bars: the deposit is bit-exact (integer accumulator and FP32 density);
+fields and forces agree to a relative L2 error of 1e-5 (FP32 transforms
+against FP64: about log2(n) rounding steps per transform, 42 transforms, and a
+nonlinear step that at most doubles relative errors give a few 1e-6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02968_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2312_02968_gb300 import binding
+
+    return binding
+
+
+def make(B, n, pad, p, sigma, mu=0, box=None, a0=1.0, G=1.0, maxp=None):
+    dev = torch.device("cuda", 0)
+    h = B.MondPM(n, pad, box if box is not None else float(n), a0, G, mu, sigma, maxp or max(1, len(p["mass"])))
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    h.bind_particles(*t)
+    return h, t
+
+
+# ---------------------------------------------------------------------------
+# deposit: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,sigma,N,seed", [(16, 1.0, 1, 0), (16, 1.5, 37, 1), (32, 1.0, 5000, 2), (32, 2.0, 777, 3),
+                                            (48, 1.5, 20000, 4), (64, 1.0, 100000, 5), (32, 0.75, 3000, 6)])
+def test_deposit_bit_exact(B, n, sigma, N, seed):
+    p = W.uniform_random(n, N, seed=seed)  # covers the periodic wrap at the faces
+    h, _ = make(B, n, 1, p, sigma)
+    h.deposit()
+    acc, ka = h.get_deposit_acc()
+    acc = acc.cpu().numpy().view(np.uint64)
+    ref, ka_ref, _ = oracle.deposit_fixed(n, sigma, p["cell"], p["offset"], p["mass"])
+    assert ka == ka_ref
+    assert np.array_equal(acc, ref)
+    rho = h.get_field(B.FIELD_RHO).cpu().numpy()
+    r32, _ = oracle.acc_to_rho(ref, ka_ref, 1.0)
+    assert np.array_equal(rho.view(np.uint32), r32.view(np.uint32))
+
+
+def test_deposit_dense_cluster_bit_exact(B):
+    """Many particles per tile (shared-memory path) and sparse tiles (global path)."""
+    n = 64
+    p = W.isothermal(n, 1.0, 200000, 3.0, 25.0, seed=9)
+    h, _ = make(B, n, 1, p, 1.5)
+    h.deposit()
+    acc, ka = h.get_deposit_acc()
+    ref, ka_ref, _ = oracle.deposit_fixed(n, 1.5, p["cell"], p["offset"], p["mass"])
+    assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+
+
+def test_deposit_edge_cases(B):
+    n = 16
+    # empty set
+    p = W.uniform_random(n, 0, seed=0)
+    h, _ = make(B, n, 1, p, 1.0, maxp=4)
+    h.deposit()
+    acc, _ = h.get_deposit_acc()
+    assert int(acc.abs().sum()) == 0
+    # offsets exactly +-1/2, all particles in one cell, negative mass
+    cell = np.array([[3, 3, 3], [3, 3, 3], [15, 0, 7], [8, 8, 8]], np.int32)
+    off = np.array([[0.5, -0.5, 0.5], [-0.5, 0.5, -0.5], [0.4999999, -0.4999999, 0.0], [0, 0, 0]], np.float32)
+    mass = np.array([1.0, 2.0, 0.5, -0.25], np.float32)
+    p = {"cell": cell, "offset": off, "vel": np.zeros((4, 3), np.float32), "mass": mass}
+    h, _ = make(B, n, 1, p, 1.0)
+    h.deposit()
+    acc, ka = h.get_deposit_acc()
+    ref, ka_ref, _ = oracle.deposit_fixed(n, 1.0, cell, off, mass)
+    assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+
+
+def test_deposit_invalid_particle_reported(B):
+    n = 16
+    cell = np.array([[3, 3, 3], [16, 0, 0]], np.int32)
+    off = np.zeros((2, 3), np.float32)
+    p = {"cell": cell, "offset": off, "vel": np.zeros((2, 3), np.float32), "mass": np.ones(2, np.float32)}
+    h, _ = make(B, n, 1, p, 1.0)
+    h.deposit()
+    with pytest.raises(B.MondError) as e:
+        h.sync()
+    assert e.value.code == -5
+    acc, ka = h.get_deposit_acc()
+    ref, _, sk = oracle.deposit_fixed(n, 1.0, cell, off, np.ones(2, np.float32), ka)
+    assert sk == 1 and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+
+
+# ---------------------------------------------------------------------------
+# field solve
+# ---------------------------------------------------------------------------
+def oracle_fields(p, n, sigma, mu, K, s=1.0, a0=1.0, G=1.0, H0=None, finish=False):
+    acc, ka, _ = oracle.deposit_fixed(n, sigma, p["cell"], p["offset"], p["mass"])
+    _, rho = oracle.acc_to_rho(acc, ka, s)
+    return oracle.solve(rho, s, G, a0, mu, K, H0=H0, finish_h=finish)
+
+
+@pytest.mark.parametrize("n,mu,K,a0", [(16, 0, 0, 1.0), (32, 0, 1, 1.0), (32, 0, 4, 1.0), (48, 1, 3, 0.05),
+                                       (32, 2, 4, 0.02), (32, 3, 2, 1.0), (64, 0, 4, 1.0), (96, 2, 2, 0.05)])
+def test_solve_matches_oracle(B, n, mu, K, a0):
+    p = W.isothermal(n, 1.0, 4000, n / 10, 0.4 * n, seed=n + K)
+    sigma = 1.5
+    h, _ = make(B, n, 1, p, sigma, mu=mu, a0=a0)
+    h.set_option(B.OPT_KEEP_PHI, 1)
+    h.deposit()
+    h.solve_field(K)
+    ref = oracle_fields(p, n, sigma, mu, K, a0=a0)
+    assert rel(h.get_field(B.FIELD_GN).cpu().numpy(), ref["gN"]) < TOL
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
+    assert rel(h.get_field(B.FIELD_PHI).cpu().numpy() - 0, ref["phi"]) < TOL
+    if K >= 2:
+        assert rel(h.get_field(B.FIELD_H).cpu().numpy(), ref["H"]) < TOL
+
+
+def test_solve_padded_grid_two_body(B):
+    """pad = 2: 64^3 physical mesh in a 128^3 periodic domain (the two-body set-up)."""
+    n, pad, sigma = 64, 2, 2.0
+    p, _ = W.two_body(n * pad, 1.0, 16.0, 0.5, 0.5)
+    h, _ = make(B, n, pad, p, sigma, mu=1, box=64.0)
+    h.deposit()
+    h.solve_field(4)
+    g = h.gather().cpu().numpy()
+    ref = oracle_fields(p, n * pad, sigma, 1, 4)
+    g_ref = oracle.gather(sigma, ref["acc"], p["cell"], p["offset"])
+    assert rel(g, g_ref) < TOL
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
+
+
+@pytest.mark.parametrize("warm", ["prev", "guess"])
+def test_warm_start_matches_oracle(B, warm):
+    n, sigma, mu = 32, 1.5, 0
+    p = W.isothermal(n, 1.0, 3000, 3.0, 12.0, seed=21)
+    h, _ = make(B, n, 1, p, sigma, mu=mu)
+    h.deposit()
+    if warm == "prev":
+        h.solve_field(3)  # leaves the H of its iteration 2
+        H0 = h.get_field(B.FIELD_H).cpu().numpy().astype(np.float64)
+        h.solve_field(1, B.WARM_PREV)
+    else:
+        rng = np.random.default_rng(3)
+        guess = (1e-3 * rng.standard_normal((3, n, n, n))).astype(np.float32)
+        h.solve_field(1, B.WARM_GUESS, torch.from_numpy(guess).cuda())
+        H0 = oracle.project_div(guess.astype(np.float64), 1.0)
+    ref = oracle_fields(p, n, sigma, mu, 1, H0=H0, finish=True)
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
+    assert rel(h.get_field(B.FIELD_H).cpu().numpy(), ref["H"]) < TOL
+
+
+# ---------------------------------------------------------------------------
+# gather, smoothing, push, diagnostics
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("sigma", [1.0, 1.5, 2.0])
+def test_gather_matches_oracle(B, sigma):
+    n = 32
+    p = W.uniform_random(n, 3000, seed=int(10 * sigma))  # includes particles whose ball wraps
+    h, _ = make(B, n, 1, p, sigma)
+    h.deposit()
+    h.solve_field(2)
+    g = h.gather().cpu().numpy()
+    ref = oracle_fields(p, n, sigma, 0, 2)
+    g_ref = oracle.gather(sigma, ref["acc"], p["cell"], p["offset"])
+    assert rel(g, g_ref) < TOL
+
+
+def test_smooth_is_gather_at_nodes(B):
+    """Node-smoothed field = Eq. gi for a particle sitting on each pixel centre."""
+    n, sigma = 16, 1.0
+    p = W.uniform_random(n, 500, seed=4)
+    h, _ = make(B, n, 1, p, sigma)
+    h.deposit()
+    h.solve_field(2)
+    h.smooth()
+    sm = h.get_field(B.FIELD_SMOOTH).cpu().numpy()
+    ref = oracle_fields(p, n, sigma, 0, 2)
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    cells = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.int32)
+    g = oracle.gather(sigma, ref["acc"], cells, np.zeros_like(cells, dtype=np.float32))
+    want = np.stack([g[:, a].reshape(n, n, n) for a in range(3)])
+    assert rel(sm, want) < TOL
+
+
+def test_step_kick_drift_matches_oracle(B):
+    n, sigma, dt = 32, 1.5, 0.5
+    p = W.isothermal(n, 1.0, 2000, 3.0, 12.0, seed=5)
+    h, t = make(B, n, 1, p, sigma)
+    h.step(dt, 4)
+    h.sync()
+    c2, o2, v2, g, _, _ = oracle.step(n, 1.0, 1.0, 1.0, 0, sigma, 4, dt, p["cell"], p["offset"], p["vel"], p["mass"])
+    vel = t[2].cpu().numpy()
+    assert rel(vel - p["vel"], v2 - p["vel"]) < TOL
+    pos = t[0].cpu().numpy() + t[1].cpu().numpy().astype(np.float64)
+    pos_ref = c2 + o2
+    d = np.abs(((pos - pos_ref) + n / 2) % n - n / 2)
+    assert d.max() < 1e-5
+    assert np.all(np.abs(t[1].cpu().numpy()) <= 0.5)
+
+
+def test_half_kick_and_diagnostics(B):
+    n = 64
+    p, meta = W.two_body(n, 1.0, 16.0, 0.6, 0.4)
+    h, t = make(B, n, 1, p, 1.0)
+    d = h.diagnostics()
+    ref = oracle.particle_diag(n, 1.0, p["cell"], p["offset"], p["vel"], p["mass"])
+    assert abs(d["mass"] - ref["mass"]) < 1e-12
+    assert np.allclose(d["momentum"], ref["P"], atol=1e-9)
+    assert np.allclose(d["com"], ref["R"], atol=1e-9)
+    assert np.allclose(d["ang_mom"], ref["L"], rtol=1e-9, atol=1e-12)
+    assert abs(d["e_kin"] - ref["Ekin"]) < 1e-12
+    h.deposit()
+    h.solve_field(2)
+    h.half_kick(0.1)
+    v = t[2].cpu().numpy()
+    ref_f = oracle_fields(p, n, 1.0, 0, 2)
+    g = oracle.gather(1.0, ref_f["acc"], p["cell"], p["offset"])
+    assert rel(v - p["vel"], 0.1 * g) < TOL
+    assert np.array_equal(t[0].cpu().numpy(), p["cell"])  # no drift
+
+
+def test_track_dh(B):
+    n = 32
+    p = W.isothermal(n, 1.0, 3000, 3.0, 12.0, seed=8)
+    h, _ = make(B, n, 1, p, 1.5)
+    h.set_option(B.OPT_TRACK_DH, 1)
+    h.deposit()
+    h.solve_field(5)
+    d = h.diagnostics()
+    dh = np.array(d["dH"][:4])
+    assert np.all(np.isfinite(dh)) and dh[1] < dh[0]
+    assert np.isnan(d["dH"][4])
