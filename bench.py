@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the MOND particle-mesh time step on GB300.
+
+Workload: deep-MOND isothermal sphere (Sect. 4.3) of 1e6 equal-mass particles
+(b = 8 px, truncated at 0.4 box), 256^3 periodic mesh, Gaussian kernel
+sigma = 1.5 px, 4 field iterations per step, dt = 0.25, G = M = a0 = 1;
+synthetic, seeded. A step is one pass of the whole hot path: deposit, field
+solve, gather and leapfrog push.
+
+Prints one JSON line. ``value`` is time steps (each with one MOND force solve)
+per second with inputs resident in HBM; ``e2e`` is the same through host
+buffers; ``warm`` is the warm-started variant (previous H, one iteration);
+``roofline`` is the dominant kernel's achieved HBM bandwidth against the
+measured peak; ``cpu_baseline`` times the CPU oracle on a bounded sample.
+``--impl reference`` times the CPU oracle alone (the reference arm).
+Under torchrun each rank steps its own independent replica (the single-system
+solve does not shard); ``value`` sums the replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MOND force solves/s and particle-steps/s at 256^3 (plain vs warm-start) at ≤1e-4 rel err"
+WL = dict(n=256, pad=1, N=1_000_000, sigma=1.5, b=8.0, rmax=0.4 * 256, K=4, dt=0.25, mu=0, a0=1.0, G=1.0, box=256.0,
+          seed=1)
+WL_NAME = ("isothermal sphere 1e6 particles, 256^3 mesh, sigma 1.5 px, deep MOND, 4 iterations/step, dt 0.25 "
+           "(configs: isothermal)")
+REF_ITERS = 40  # converged reference: mean of iterates 40 and 41 (the undamped scheme ends in a 2-cycle)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.05)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank: int):
+    from paper_2312_02968_gb300 import workloads as W
+
+    return W.isothermal(WL["n"] * WL["pad"], WL["box"] / WL["n"], WL["N"], WL["b"], WL["rmax"], seed=WL["seed"] + rank)
+
+
+def cpu_baseline(p, sample_particles: int):
+    """The CPU oracle as it stands on this host: one field solve on the full
+    256^3 mesh (K = 4, 42 transforms) plus deposit, gather and push of a
+    sample of the particles, scaled to the full particle count."""
+    import numpy as np
+
+    import oracle
+
+    n, sigma, K = WL["n"] * WL["pad"], WL["sigma"], WL["K"]
+    s = WL["box"] / WL["n"]
+    Ns = min(sample_particles, len(p["mass"]))
+    sub = {k: np.ascontiguousarray(v[:Ns]) for k, v in p.items()}
+    sub["mass"] = (sub["mass"] * (len(p["mass"]) / Ns)).astype(np.float32)
+    t0 = time.perf_counter()
+    acc, ka, _ = oracle.deposit_fixed(n, sigma, sub["cell"], sub["offset"], sub["mass"])
+    t1 = time.perf_counter()
+    _, rho = oracle.acc_to_rho(acc, ka, s)
+    f = oracle.solve(rho, s, WL["G"], WL["a0"], WL["mu"], K, want=("acc",))
+    t2 = time.perf_counter()
+    g = oracle.gather(sigma, f["acc"], sub["cell"], sub["offset"])
+    oracle.push(n, s, WL["dt"], g, sub["cell"], sub["offset"], sub["vel"])
+    t3 = time.perf_counter()
+    scale = len(p["mass"]) / Ns
+    t_step = (t2 - t1) + scale * ((t1 - t0) + (t3 - t2))
+    return {"t_step": t_step, "t_solve": t2 - t1, "t_particles_sample": (t1 - t0) + (t3 - t2), "Ns": Ns,
+            "cores": oracle.num_threads(), "cpu_s": t3 - t0}
+
+
+_REF_FIELD = None
+
+
+def reference_step(p, sample_particles: int, rng):
+    """One bounded sample of a time step for the CPU oracle: one of the 42
+    scalar 3-D transforms of a K = 4 solve on the full 256^3 mesh (scaled x42)
+    and deposit, gather and push of a random sample of the particles (scaled to
+    all of them). The solve's pointwise loops are left out, so the scaled time
+    is a lower bound of the oracle's step time."""
+    import numpy as np
+
+    import oracle
+
+    n, sigma = WL["n"] * WL["pad"], WL["sigma"]
+    s = WL["box"] / WL["n"]
+    N = len(p["mass"])
+    idx = np.sort(rng.choice(N, size=min(sample_particles, N), replace=False))
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in p.items()}
+    global _REF_FIELD
+    if _REF_FIELD is None:  # allocated and touched once, as the oracle's solve reuses its arrays
+        _REF_FIELD = np.ascontiguousarray(rng.standard_normal((n, n, n)) + 0j)
+    t0 = time.perf_counter()
+    acc, ka, _ = oracle.deposit_fixed(n, sigma, sub["cell"], sub["offset"], sub["mass"])
+    t1 = time.perf_counter()
+    oracle.lib().ora_fft3_raw(n, _REF_FIELD.ctypes.data_as(ctypes.c_void_p), -1)
+    t2 = time.perf_counter()
+    g = oracle.gather(sigma, np.zeros((3, n, n, n)), sub["cell"], sub["offset"])
+    oracle.push(n, s, WL["dt"], g, sub["cell"], sub["offset"], sub["vel"])
+    t3 = time.perf_counter()
+    return 42.0 * (t2 - t1) + (N / len(idx)) * ((t1 - t0) + (t3 - t2))
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on this host's cores, same workload and metric."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    p = make_workload(0)
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        reference_step(p, args.ref_sample, rng)
+    ts = [reference_step(p, args.ref_sample, rng) for _ in range(args.steps)]
+    cores = os.cpu_count()
+    import oracle
+
+    v = 1.0 / statistics.mean(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL_NAME, "l2": "inputs larger than L2"},
+            "particle_steps_per_s": v * WL["N"],
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"per step: one of the 42 scalar 256^3 transforms of a K=4 solve (x42) plus "
+                                       f"deposit/gather/push of {args.ref_sample} random particles (x"
+                                       f"{WL['N'] // args.ref_sample}); pointwise solve loops omitted (lower bound "
+                                       f"on the oracle's step time)"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "host_cores": cores}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=10_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    # the CPU baseline runs before any GPU work (no CUDA context in the oracle)
+    p = make_workload(rank)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, 50_000)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2312_02968_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n, pad, N = WL["n"], WL["pad"], WL["N"]
+    t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")}
+    init = {k: v.clone() for k, v in t.items()}
+    h = B.MondPM(n, pad, WL["box"], WL["a0"], WL["G"], WL["mu"], WL["sigma"], N)
+    h.bind_particles(t["cell"], t["offset"], t["vel"], t["mass"])
+    stream = h.stream
+    K, dt = WL["K"], WL["dt"]
+
+    for _ in range(args.warmup):
+        h.step(dt, K, B.WARM_NONE)
+    h.sync()
+
+    # ---- timed region: plain 4-iteration steps --------------------------------
+    h.set_option(B.OPT_TIMING, 1)
+    h.kernel_stats()
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    l0 = h.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        h.step(dt, K, B.WARM_NONE)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    launches = h.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    stats = h.kernel_stats()
+    h.set_option(B.OPT_TIMING, 0)
+    h.sync()
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # ---- warm-started steps (previous H, one iteration) ------------------------
+    for k in t:
+        t[k].copy_(init[k])
+    h.deposit()
+    h.solve_field(K, B.WARM_NONE)
+    h.gather_push(dt)
+    for _ in range(args.warmup):
+        h.step(dt, 1, B.WARM_PREV)
+    barrier()
+    w0 = torch.cuda.Event(enable_timing=True)
+    w1 = torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    for _ in range(args.steps):
+        h.step(dt, 1, B.WARM_PREV)
+    w1.record(stream)
+    w1.synchronize()
+    barrier()
+    wms = w0.elapsed_time(w1)
+    if dist is not None:
+        tt = torch.tensor([wms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        wms = float(tt.item())
+    warm_value = world * args.steps / (wms / 1000.0)
+
+    # ---- accuracy against the converged field (not timed) ----------------------
+    acc_info = None
+    if not args.no_accuracy:
+        h.deposit()
+        h.solve_field(1, B.WARM_PREV)  # the warm solve as the timed loop runs it
+        g_warm = h.gather().double()
+        h.solve_field(K, B.WARM_NONE)
+        g_plain = h.gather().double()
+        h.solve_field(REF_ITERS, B.WARM_NONE)
+        g_a = h.gather().double()
+        h.solve_field(REF_ITERS + 1, B.WARM_NONE)
+        g_b = h.gather().double()
+        g_ref = 0.5 * (g_a + g_b)
+        nr = float(torch.linalg.norm(g_ref))
+        acc_info = {"ref": f"mean of iterates {REF_ITERS} and {REF_ITERS + 1} from H=0",
+                    "plain_K4_rel_err": float(torch.linalg.norm(g_plain - g_ref)) / nr,
+                    "warm_K1_rel_err": float(torch.linalg.norm(g_warm - g_ref)) / nr,
+                    "ref_two_cycle_rel": float(torch.linalg.norm(g_a - g_b)) / nr}
+        h.sync()
+
+    # ---- end to end through host buffers -------------------------------------
+    cell_h = init["cell"].cpu().pin_memory()
+    off_h = init["offset"].cpu().pin_memory()
+    vel_h = init["vel"].cpu().pin_memory()
+    for _ in range(2):
+        h.step_host(dt, K, B.WARM_NONE, cell_h, off_h, vel_h)
+    barrier()
+    tq = time.perf_counter()
+    for _ in range(args.steps):
+        h.step_host(dt, K, B.WARM_NONE, cell_h, off_h, vel_h)
+    barrier()
+    e2e_s = time.perf_counter() - tq
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * args.steps / e2e_s
+
+    if rank == 0:
+        peak, peak_src = load_peaks()
+        hbm = [s for s in stats if s["name"].startswith(("xpass", "ypass", "zpass"))]
+        dom = max(hbm, key=lambda s: s["ms"]) if hbm else None
+        traffic = None
+        try:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+                tj = json.load(f)
+            traffic = tj.get(dom["name"], {}).get("bytes_per_launch") if dom else None
+        except Exception:
+            traffic = None
+        roof = None
+        if dom:
+            per_launch_ms = dom["ms"] / dom["launches"]
+            algo = dom["bytes"] / dom["launches"]
+            ach = algo / (per_launch_ms / 1000.0) / 1e9
+            roof = {"bound": "hbm", "kernel": dom["name"], "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": peak_src, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": algo, "ms_per_launch": per_launch_ms}
+        kern = [{"name": s["name"], "launches": s["launches"], "ms": round(s["ms"], 4),
+                 "share": round(s["ms"] / sum(x["ms"] for x in stats), 4),
+                 "GBps": round(s["bytes"] / (s["ms"] / 1000.0) / 1e9, 1) if s["ms"] > 0 else None} for s in stats]
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WL_NAME, "l2": "inputs larger than L2 (1.4 GB of fields per step)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "particle_steps_per_s": value * N,
+                "warm": {"value": warm_value, "unit": "solves/s", "mode": "previous H, 1 iteration",
+                         "particle_steps_per_s": warm_value * N, "speedup_vs_plain": warm_value / value},
+                "accuracy": acc_info,
+                "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 36 * N,
+                        "d2h_bytes_per_step": 36 * N},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern}
+        if cpu:
+            line["cpu_baseline"] = {"value": 1.0 / cpu["t_step"], "unit": "solves/s", "cores": cpu["cores"],
+                                    "kind": "oracle",
+                                    "sample": f"one full 256^3 K=4 oracle solve ({cpu['t_solve']:.1f} s) plus "
+                                              f"deposit/gather/push of {cpu['Ns']} of the {N} particles scaled "
+                                              f"x{N // cpu['Ns']}; {cpu['cpu_s']:.1f} s of CPU work"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -82,8 +82,19 @@ enum {
 enum {
   MOND_OPT_KEEP_PHI = 1,  /* value 1: also form the potential phi in the final pass */
   MOND_OPT_TRACK_DH = 2,  /* value 1: record ||H_j - H_{j-1}|| / ||g_N|| per iteration (costs one reduction) */
-  MOND_OPT_USE_GRAPH = 3  /* value 1: replay mond_pm_step as a captured CUDA graph (default 0) */
+  MOND_OPT_USE_GRAPH = 3, /* value 1: replay mond_pm_step as a captured CUDA graph (default 0) */
+  MOND_OPT_TIMING = 4     /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
 };
+
+/* Per kernel class: launches, device time between the events around each
+ * launch, and the algorithmic bytes the launches must move (each input
+ * element read once, each output element written once). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double bytes;
+} mond_pm_kstat;
 
 typedef struct {
   double mass;          /* sum of m_i */
@@ -201,6 +212,11 @@ const char* mond_pm_last_error(mond_pm_t h);
 /* Number of kernels this handle has launched since creation (each graph
  * replay counts its kernels). */
 int64_t mond_pm_kernel_launches(mond_pm_t h);
+
+/* Kernel statistics gathered while MOND_OPT_TIMING is on: fills up to cap
+ * entries (one per kernel class that ran), sets *count, and resets the
+ * statistics. Synchronises. */
+int mond_pm_kernel_stats(mond_pm_t h, mond_pm_kstat* out, int cap, int* count);
 
 #ifdef __cplusplus
 }

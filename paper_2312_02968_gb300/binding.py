@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libmondpm.so")
 MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
 WARM_NONE, WARM_PREV, WARM_GUESS = 0, 1, 2
 FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
-OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH = 1, 2, 3
+OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING = 1, 2, 3, 4
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
 
@@ -35,6 +35,10 @@ class Diag(ctypes.Structure):
     _fields_ = [("mass", _D), ("momentum", _D * 3), ("com", _D * 3), ("ang_mom", _D * 3), ("e_kin", _D),
                 ("e_pot", _D), ("rho_mass", _D), ("n_iter_done", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("dH", _D * 64)]
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _I64), ("ms", _D), ("bytes", _D)]
 
 
 SIGNATURES = {
@@ -57,6 +61,7 @@ SIGNATURES = {
     "mond_pm_sync": (_I, [_P]),
     "mond_pm_last_error": (ctypes.c_char_p, [_P]),
     "mond_pm_kernel_launches": (_I64, [_P]),
+    "mond_pm_kernel_stats": (_I, [_P, ctypes.POINTER(KStat), _I, ctypes.POINTER(_I)]),
 }
 
 _lib = None
@@ -213,3 +218,12 @@ class MondPM:
 
     def kernel_launches(self) -> int:
         return int(lib().mond_pm_kernel_launches(self.h))
+
+    def kernel_stats(self) -> list:
+        """Per kernel class since the last call (needs OPT_TIMING): name,
+        launches, device ms, algorithmic bytes."""
+        arr = (KStat * 32)()
+        cnt = ctypes.c_int(0)
+        self._check(lib().mond_pm_kernel_stats(self.h, arr, 32, ctypes.byref(cnt)))
+        return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "ms": float(arr[i].ms),
+                 "bytes": float(arr[i].bytes)} for i in range(min(cnt.value, 32))]

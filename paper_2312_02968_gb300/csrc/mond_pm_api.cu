@@ -144,6 +144,21 @@ __global__ void k_dep_sum(int64_t n3, const uint64_t* dep, unsigned long long* o
 
 }  // namespace
 
+enum KClass {
+  KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_Y_FWD, KC_Y_INV,
+  KC_Z_NEWTON, KC_Z_CURL, KC_Z_DIV, KC_Z_FINAL, KC_Z_SMOOTH, KC_BIN, KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_COUNT
+};
+const char* const kKName[KC_COUNT] = {"xpass_rho", "xpass_nu_first", "xpass_nu", "xpass_mu", "xpass_inv",
+                                      "xpass_fwd", "ypass_fwd", "ypass_inv", "zpass_newton", "zpass_curl",
+                                      "zpass_div", "zpass_final", "zpass_smooth", "bin", "deposit",
+                                      "gather_push", "other"};
+
+struct TimedLaunch {
+  int cls;
+  double bytes;
+  cudaEvent_t a, b;
+};
+
 struct mond_pm {
   int n, npad, nf;
   double box, s, a0, G, sigma;
@@ -163,13 +178,64 @@ struct mond_pm {
   const float* mass = nullptr;
   int kacc = 0;
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false;
-  int keep_phi = 0, track_dh = 0, use_graph = 0;
+  int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0;
+  std::vector<TimedLaunch> tl;      // launches recorded since the last read
+  std::vector<cudaEvent_t> evpool;  // recycled events
+  int64_t st_launch[KC_COUNT] = {};
+  double st_ms[KC_COUNT] = {}, st_bytes[KC_COUNT] = {};
   int last_iters = 0;
   int64_t launches = 0;
   std::string err;
 };
 
 namespace {
+
+cudaEvent_t get_event(mond_pm* h) {
+  if (!h->evpool.empty()) {
+    cudaEvent_t e = h->evpool.back();
+    h->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch with events when timing is on (begin before, end after).
+struct Timed {
+  mond_pm* h;
+  TimedLaunch t{};
+  Timed(mond_pm* hh, int cls, double bytes) : h(hh) {
+    h->launches++;
+    if (!h->timing) return;
+    t.cls = cls;
+    t.bytes = bytes;
+    t.a = get_event(h);
+    t.b = get_event(h);
+    cudaEventRecord(t.a, h->st);
+  }
+  ~Timed() {
+    if (!h->timing) return;
+    cudaEventRecord(t.b, h->st);
+    h->tl.push_back(t);
+  }
+};
+
+// Fold recorded launches into the per-class totals (synchronises).
+void collect_timing(mond_pm* h) {
+  if (h->tl.empty()) return;
+  cudaStreamSynchronize(h->st);
+  for (auto& t : h->tl) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    h->st_launch[t.cls]++;
+    h->st_ms[t.cls] += ms;
+    h->st_bytes[t.cls] += t.bytes;
+    h->evpool.push_back(t.a);
+    h->evpool.push_back(t.b);
+  }
+  h->tl.clear();
+}
 
 int fail(mond_pm* h, int code, const char* fmt, ...) {
   char buf[512];
@@ -188,13 +254,27 @@ int fail(mond_pm* h, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(h, MOND_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// algorithmic bytes: spectral plane = n^2 (n/2+1) complex, real plane = n^3 floats
+double spec_bytes(mond_pm* h) { return 8.0 * h->nf * h->nf * (h->nf / 2 + 1); }
+double real_bytes(mond_pm* h) { return 4.0 * h->n3; }
+
 cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
   a.tw = h->w.tw;
   a.status = h->w.status;
   a.mu_kind = h->mu_kind;
   a.a0 = (float)h->a0;
   a.pstride = h->plane;
-  h->launches++;
+  const double S = spec_bytes(h), R = real_bytes(h);
+  double bytes = 0;
+  switch (mode) {
+    case passes::X_RHO: bytes = 2 * R + R + S; break;  // int64 in, FP32 density out, spectrum out
+    case passes::X_NU_FIRST: bytes = 6 * S + 3 * R + (a.H0 ? 3 * R : 0); break;
+    case passes::X_NU: bytes = 6 * S + 3 * R + (a.Hs_out ? 3 * R * (a.red ? 2 : 1) : 0); break;
+    case passes::X_MU: bytes = 6 * S + 3 * R; break;
+    case passes::X_INV: bytes = a.ncomp * (S + R * (a.real_out2 ? 2 : 1)); break;
+    case passes::X_FWD: bytes = a.ncomp * (S + R); break;
+  }
+  Timed tm(h, KC_X_RHO + mode, bytes);
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_xpass_##k(mode, a, h->st);
@@ -209,7 +289,7 @@ cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
   a.spec = spec;
   a.pstride = h->plane;
   a.tw = h->w.tw;
-  h->launches++;
+  Timed tm(h, dir < 0 ? KC_Y_FWD : KC_Y_INV, 2.0 * ncomp * spec_bytes(h));
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_ypass_##k(dir, a, ncomp, h->st);
@@ -231,7 +311,12 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
   a.khat = h->w.khat;
   a.norm = (float)(1.0 / ((double)h->nf * h->nf * h->nf));
   a.coef = (float)(4.0 * M_PI * h->G);
-  h->launches++;
+  int nin = (mode == passes::Z_NEWTON) ? 1 : 3;
+  int nwr = (mode == passes::Z_NEWTON || mode == passes::Z_FINAL) ? nout : 3;
+  double zb = (nin + nwr) * spec_bytes(h) + (mode == passes::Z_SMOOTH ? 0.5 * real_bytes(h) : 0.0);
+  int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : mode == passes::Z_DIV ? KC_Z_DIV
+           : mode == passes::Z_FINAL ? KC_Z_FINAL : KC_Z_SMOOTH;
+  Timed tm(h, zc, zb);
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_zpass_##k(mode, a, h->st);
@@ -279,14 +364,16 @@ int do_bin(mond_pm* h) {
   CK(cudaMemsetAsync(h->w.fill, 0, sizeof(int) * (h->ntile + 2), h->st));
   unsigned nb = (unsigned)((h->N + 255) / 256);
   if (h->N > 0) {
+    Timed tm(h, KC_BIN, 32.0 * h->N);
     parts::k_bin_count<<<nb, 256, 0, h->st>>>(b);
-    h->launches++;
   }
-  parts::k_bin_scan<<<1, 1024, 0, h->st>>>(b);
-  h->launches++;
+  {
+    Timed tm(h, KC_BIN, 12.0 * (h->ntile + 1));
+    parts::k_bin_scan<<<1, 1024, 0, h->st>>>(b);
+  }
   if (h->N > 0) {
+    Timed tm(h, KC_BIN, 12.0 * h->N);
     parts::k_bin_scatter<<<nb, 256, 0, h->st>>>(b);
-    h->launches++;
   }
   CK(cudaGetLastError());
   return MOND_OK;
@@ -325,8 +412,11 @@ int do_deposit(mond_pm* h) {
   CK(cudaMemsetAsync(h->w.counters, 0, sizeof(int), h->st));
   size_t sm = dep_smem(h);
   CK(cudaFuncSetAttribute(parts::k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  parts::k_deposit<<<h->sms * 4, parts::DEP_NT, sm, h->st>>>(d);
-  h->launches++;
+  {
+    // algorithmic bytes: particle reads (perm, cell, offset, mass) and one int64 write per touched cell
+    Timed tm(h, KC_DEPOSIT, 32.0 * h->N + 8.0 * h->n3);
+    parts::k_deposit<<<h->sms * 4, parts::DEP_NT, sm, h->st>>>(d);
+  }
   CK(cudaGetLastError());
   h->have_dep = true;
   h->have_solve = false;
@@ -360,8 +450,11 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   CK(cudaMemsetAsync(h->w.counters + 1, 0, sizeof(int), h->st));
   size_t sm = gat_smem(h);
   CK(cudaFuncSetAttribute(parts::k_gather_push, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  parts::k_gather_push<<<h->sms * 2, parts::GAT_NT, sm, h->st>>>(g);
-  h->launches++;
+  {
+    // algorithmic bytes: the acceleration mesh once, particles read and written
+    Timed tm(h, KC_GATHER, 3.0 * real_bytes(h) + 64.0 * h->N);
+    parts::k_gather_push<<<h->sms * 2, parts::GAT_NT, sm, h->st>>>(g);
+  }
   CK(cudaGetLastError());
   return MOND_OK;
 }
@@ -577,6 +670,8 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
 int mond_pm_destroy(mond_pm_t h) {
   if (!h) return MOND_EINVAL;
   cudaStreamSynchronize(h->st);
+  collect_timing(h);
+  for (auto e : h->evpool) cudaEventDestroy(e);
   delete h;
   return MOND_OK;
 }
@@ -587,6 +682,10 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_KEEP_PHI: h->keep_phi = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_TRACK_DH: h->track_dh = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_USE_GRAPH: h->use_graph = value ? 1 : 0; return MOND_OK;
+    case MOND_OPT_TIMING:
+      collect_timing(h);
+      h->timing = value ? 1 : 0;
+      return MOND_OK;
   }
   return fail(h, MOND_EINVAL, "unknown option %d", option);
 }
@@ -800,5 +899,27 @@ int mond_pm_sync(mond_pm_t h) {
 const char* mond_pm_last_error(mond_pm_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 int64_t mond_pm_kernel_launches(mond_pm_t h) { return h ? h->launches : 0; }
+
+int mond_pm_kernel_stats(mond_pm_t h, mond_pm_kstat* out, int cap, int* count) {
+  if (!h || !count || (cap > 0 && !out)) return MOND_EINVAL;
+  collect_timing(h);
+  int k = 0;
+  for (int c = 0; c < KC_COUNT; c++) {
+    if (h->st_launch[c] == 0) continue;
+    if (k < cap) {
+      memset(out[k].name, 0, sizeof out[k].name);
+      strncpy(out[k].name, kKName[c], sizeof out[k].name - 1);
+      out[k].launches = h->st_launch[c];
+      out[k].ms = h->st_ms[c];
+      out[k].bytes = h->st_bytes[c];
+    }
+    k++;
+    h->st_launch[c] = 0;
+    h->st_ms[c] = 0;
+    h->st_bytes[c] = 0;
+  }
+  *count = k;
+  return MOND_OK;
+}
 
 }  // extern "C"

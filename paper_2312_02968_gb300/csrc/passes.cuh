@@ -39,7 +39,7 @@ struct YZCfg {
 
 // x-pass modes
 enum XMode {
-  X_RHO = 0,       // int64 deposit -> FP32 density (exact rule), clear, R2C
+  X_RHO = 0,       // int64 deposit -> FP32 density (exact rule), R2C
   X_NU_FIRST = 1,  // C2R g_N (store), F = g_N + H0, g_M = nu(F) F, R2C
   X_NU = 2,        // C2R H (optionally store, track dH), F = g_N + H, g_M = nu(F) F, R2C
   X_MU = 3,        // C2R g_M, F = mu(g_M) g_M, H = F - g_N, R2C
@@ -250,7 +250,6 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
       ulonglong2 u = *reinterpret_cast<const ulonglong2*>(a.dep + ri);
       float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.x), a.rho_scale));
       float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.y), a.rho_scale));
-      *reinterpret_cast<ulonglong2*>(a.dep + ri) = make_ulonglong2(0ull, 0ull);
       if (a.rho_out) *reinterpret_cast<float2*>(a.rho_out + ri) = make_float2(r0, r1);
       *p0 = make_float2(r0, r1);
     } else if constexpr (MODE == X_FWD) {
