@@ -218,6 +218,27 @@ int64_t mond_pm_kernel_launches(mond_pm_t h);
  * statistics. Synchronises. */
 int mond_pm_kernel_stats(mond_pm_t h, mond_pm_kstat* out, int cap, int* count);
 
+/* Mass deposit for callers that cannot allocate device memory.
+ * The paper has no counterpart; this entry point exists because some callers
+ * cannot call cudaMalloc (a host framework that owns every device
+ * allocation, a plug-in that must not grow the process's device footprint).
+ * It computes the same density as mond_pm_deposit followed by
+ * mond_pm_get_field(MOND_FIELD_RHO) -- bit for bit -- for N particles on an
+ * n_f^3 periodic domain of pixel width s, writing rho_out (device float32,
+ * n_f^3, caller-owned). Inputs are device arrays in the layout above.
+ * It allocates nothing: its scratch (int64 accumulator of at most 128^3
+ * cells, the lookup table for kernel widths up to 2 px, the ball of taps) is
+ * held in fixed-size __device__ arrays that every GPU loading the library
+ * keeps until the process exits (about 21 MiB per device).
+ * Limits: 8 <= n_f <= 128, 0.75 <= kernel_width <= 2, N < 2^31; anything
+ * else returns MOND_EINVAL with a message in mond_pm_last_error(NULL).
+ * The first call on a device, and any call that changes kernel_width, sets
+ * the scratch up and synchronises cuda_stream; make that call before any
+ * stream capture. Every call shares the scratch: calls whose work overlaps on
+ * the GPU race and give wrong results, so order them on one stream. */
+int mond_pm_deposit_noalloc(int32_t n_f, double s, double kernel_width, int64_t N, const int32_t* cell,
+                            const float* offset, const float* mass, float* rho_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

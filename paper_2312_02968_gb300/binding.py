@@ -62,6 +62,7 @@ SIGNATURES = {
     "mond_pm_last_error": (ctypes.c_char_p, [_P]),
     "mond_pm_kernel_launches": (_I64, [_P]),
     "mond_pm_kernel_stats": (_I, [_P, ctypes.POINTER(KStat), _I, ctypes.POINTER(_I)]),
+    "mond_pm_deposit_noalloc": (_I, [ctypes.c_int32, _D, _D, _I64, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -98,6 +99,20 @@ def workspace_bytes(n: int, pad: int, kernel_width: float, max_particles: int) -
     if rc != 0:
         raise MondError(rc, "unsupported grid or kernel width")
     return int(out.value)
+
+
+def deposit_noalloc(n_f: int, s: float, kernel_width: float, cell, offset, mass, rho_out, stream=None):
+    """Density of the particles on an n_f^3 domain into rho_out (device
+    float32 [n_f, n_f, n_f]) without allocating device memory: the library
+    keeps fixed-size scratch for this call (n_f <= 128). For callers that
+    cannot call cudaMalloc. Uses torch's current stream unless one is given."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().mond_pm_deposit_noalloc(int(n_f), float(s), float(kernel_width), int(mass.numel()), _ptr(cell),
+                                       _ptr(offset), _ptr(mass), _ptr(rho_out), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise MondError(rc, lib().mond_pm_last_error(None).decode())
 
 
 class MondPM:

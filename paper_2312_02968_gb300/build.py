@@ -47,7 +47,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     jobs = [([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "mond_pm_api.cu"), "-o", os.path.join(OUT, "api.o")],
-             os.path.join(OUT, "api.o"))]
+             os.path.join(OUT, "api.o")),
+            ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "deposit_noalloc.cu"), "-o",
+                                      os.path.join(OUT, "deposit_noalloc.o")], os.path.join(OUT, "deposit_noalloc.o"))]
     for n in SIZES:
         o = os.path.join(OUT, f"passes_{n}.o")
         jobs.append(([nvcc] + ARCH + FLAGS + [f"-DMOND_N={n}", "-c", os.path.join(SRC, "passes_inst.cu"), "-o", o], o))

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/mond_pm.h"
+#include "internal.h"
 #include "launch.h"
 #include "particles.cuh"
 
@@ -143,6 +144,8 @@ __global__ void k_dep_sum(int64_t n3, const uint64_t* dep, unsigned long long* o
 }
 
 }  // namespace
+
+void mond_pm_set_create_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
 enum KClass {
   KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_Y_FWD, KC_Y_INV,

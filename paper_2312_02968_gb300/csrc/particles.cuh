@@ -3,6 +3,7 @@
 // leapfrog of Eq. motion, and FP64 particle diagnostics.
 #pragma once
 #include "common.cuh"
+#include "fixed_point.cuh"
 
 namespace parts {
 
@@ -142,18 +143,6 @@ struct DepArgs {
   int* work_counter;  // persistent-grid work queue (zeroed before launch)
 };
 
-// One tap: 2^-24 axis weights -> w3 in 2^-40 units (two round-half-up
-// narrowings) -> times the mass significand -> 2^-Kacc units (round half up).
-__device__ __forceinline__ uint64_t tap_contrib(uint32_t wx, uint32_t wy, uint32_t wz, uint32_t msig, int sh) {
-  uint64_t wxy = (uint64_t)wx * (uint64_t)wy;
-  uint64_t wxy16 = (wxy + 32768ull) >> 16;
-  uint64_t w3 = (wxy16 * (uint64_t)wz + 32768ull) >> 16;
-  uint64_t p = w3 * (uint64_t)msig;
-  if (p == 0) return 0;
-  if (sh <= 0) return p << (-sh);
-  if (sh >= 64) return 0;
-  return (p + (1ull << (sh - 1))) >> sh;
-}
 
 template <bool DENSE>
 __device__ __forceinline__ void deposit_particles(const DepArgs& a, int p0, int p1, int ox, int oy, int oz, int hw,
