@@ -83,7 +83,9 @@ enum {
   MOND_OPT_KEEP_PHI = 1,  /* value 1: also form the potential phi in the final pass */
   MOND_OPT_TRACK_DH = 2,  /* value 1: record ||H_j - H_{j-1}|| / ||g_N|| per iteration (costs one reduction) */
   MOND_OPT_USE_GRAPH = 3, /* value 1: replay mond_pm_step as a captured CUDA graph (default 0) */
-  MOND_OPT_TIMING = 4     /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
+  MOND_OPT_TIMING = 4,    /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
+  MOND_OPT_PIPELINED = 5  /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
+                             0: one tile per CTA with plain loads (same results) */
 };
 
 /* Per kernel class: launches, device time between the events around each

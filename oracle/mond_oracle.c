@@ -197,14 +197,15 @@ int ora_kacc(int64_t n, const float* mass) {
   return 62 - E - L;
 }
 
-/* Contribution of one tap: the three axis weights (2^-24 units) are combined
- * with two round-half-up narrowing steps to w3 (2^-40 units), multiplied by the
- * mass significand and shifted to 2^-Kacc units with round-half-up. */
-static uint64_t tap_contrib(uint32_t wx, uint32_t wy, uint32_t wz, uint32_t msig, int sh) {
-  uint64_t wxy = (uint64_t)wx * (uint64_t)wy;
-  uint64_t wxy16 = (wxy + 32768u) >> 16;
-  uint64_t w3 = (wxy16 * (uint64_t)wz + 32768u) >> 16;
-  uint64_t p = w3 * (uint64_t)msig;
+/* Integer rule of one tap. Axis weights W (2^-24 units) come from the table.
+ * The mass significand msig is folded into the x weights,
+ *   MX[j]    = (Wx[j] msig + 2^15) >> 16,
+ * the y and z weights are combined per row,
+ *   R[dy,dz] = (Wy[dy] Wz[dz] + 2^15) >> 16,
+ * and the tap's contribution is P = R MX (exact, < 2^62) shifted to 2^-Kacc
+ * mass units with round-half-up: c = (P + 2^(sh-1)) >> sh, sh = 40 - Kacc - e2
+ * where |m| = msig 2^e2. */
+static uint64_t round_shift(uint64_t p, int sh) {
   if (p == 0) return 0;
   if (sh <= 0) return p << (-sh);
   if (sh >= 64) return 0;
@@ -253,9 +254,13 @@ int64_t ora_deposit_fixed(int n, double sigma, int64_t N, const int32_t* cell,
     const uint32_t* Wx = lut + (int64_t)(q[0] + ORA_QHALF) * w;
     const uint32_t* Wy = lut + (int64_t)(q[1] + ORA_QHALF) * w;
     const uint32_t* Wz = lut + (int64_t)(q[2] + ORA_QHALF) * w;
+    uint64_t MX[64], R[64][64];
+    for (int j = 0; j < w; j++) MX[j] = ((uint64_t)Wx[j] * msig + 32768u) >> 16;
+    for (int a = 0; a < w; a++)
+      for (int b = 0; b < w; b++) R[a][b] = ((uint64_t)Wy[a] * Wz[b] + 32768u) >> 16;
     for (int t = 0; t < nb; t++) {
       int dx = ball[3 * t], dy = ball[3 * t + 1], dz = ball[3 * t + 2];
-      uint64_t cval = tap_contrib(Wx[dx + r], Wy[dy + r], Wz[dz + r], msig, sh);
+      uint64_t cval = round_shift(R[dy + r][dz + r] * MX[dx + r], sh);
       if (neg) cval = (uint64_t)0 - cval;
       int64_t j = idx3(n, wrap(c[0] + dx, n), wrap(c[1] + dy, n), wrap(c[2] + dz, n));
 #pragma omp atomic

@@ -1,5 +1,8 @@
 // mond_pm_api.cu -- the C ABI of include/mond_pm.h: handle, workspace
 // carve-up, host-built tables, and the pass sequence of a time step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,6 +30,8 @@ struct Workspace {
   float* kp;
   uint32_t* lut;
   uint32_t* ball;
+  int32_t* ball_lin;   // per tap: linear mesh offset of an interior ball
+  int32_t* ball_hlin;  // per tap: linear offset inside a tile plus its reach
   uint64_t* dep;
   float2* W;         // 3 spectral planes
   float2* A;         // 4 spectral planes
@@ -38,8 +43,9 @@ struct Workspace {
   float* khat;       // N * N * (N/2 + 1)
   uint32_t* key;
   uint32_t* perm;
-  int* count;
-  int* fill;
+  int* count;        // n^3 + 1 key counters
+  int* cstart;       // n^3 + 2 sorted starts
+  int* bsum;         // scan block sums
   int* tile_start;
   int* chunk_start;
 };
@@ -85,6 +91,8 @@ size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
   t.kp = (float*)take(sizeof(float) * n);
   t.lut = (uint32_t*)take(sizeof(uint32_t) * 65537 * lw);
   t.ball = (uint32_t*)take(sizeof(uint32_t) * nb);
+  t.ball_lin = (int32_t*)take(sizeof(int32_t) * nb);
+  t.ball_hlin = (int32_t*)take(sizeof(int32_t) * nb);
   t.dep = (uint64_t*)take(sizeof(uint64_t) * n3);
   t.W = (float2*)take(sizeof(float2) * 3 * plane);
   t.A = (float2*)take(sizeof(float2) * 4 * plane);
@@ -96,12 +104,60 @@ size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
   t.khat = (float*)take(sizeof(float) * (int64_t)n * n * (n / 2 + 1));
   t.key = (uint32_t*)take(sizeof(uint32_t) * (maxp > 0 ? maxp : 1));
   t.perm = (uint32_t*)take(sizeof(uint32_t) * (maxp > 0 ? maxp : 1));
-  t.count = (int*)take(sizeof(int) * (ntile + 2));
-  t.fill = (int*)take(sizeof(int) * (ntile + 2));
+  t.count = (int*)take(sizeof(int) * (n3 + 2));
+  t.cstart = (int*)take(sizeof(int) * (n3 + 2));
+  t.bsum = (int*)take(sizeof(int) * ((n3 + 1) / parts::SCAN_B + 2));
   t.tile_start = (int*)take(sizeof(int) * (ntile + 2));
   t.chunk_start = (int*)take(sizeof(int) * (ntile + 2));
   if (w) *w = t;
   return off;
+}
+
+// The driver's tensor-map encoder (null when the driver does not provide it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  return enc;
+}
+
+// TMA view of a spectral buffer: 3-D float tensor (x: 2 SP floats of a row,
+// y: N rows of a plane, z: ncomp N planes), box (bx, by, bz).
+bool encode_spectral_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx, int by, int bz) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int sp = n / 2 + 2;
+  cuuint64_t dims[3] = {(cuuint64_t)2 * sp, (cuuint64_t)n, (cuuint64_t)ncomp * n};
+  cuuint64_t strides[2] = {(cuuint64_t)2 * sp * 4, (cuuint64_t)2 * sp * 4 * n};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 4-D view (x: 2 SP floats, component: ncomp planes, y: N rows, z: N planes)
+// with box (bx, bc, 1, bz): z-pass tiles [z][component][column].
+bool encode_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx, int bc, int bz) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int sp = n / 2 + 2;
+  const cuuint64_t row = (cuuint64_t)2 * sp * 4, plane = row * n * n;
+  cuuint64_t dims[4] = {(cuuint64_t)2 * sp, (cuuint64_t)ncomp, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[3] = {plane, row, row * n};
+  cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)bc, 1, (cuuint32_t)bz};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // Gaussian of Eq. smooth along one axis, width sigma pixels.
@@ -181,7 +237,11 @@ struct mond_pm {
   const float* mass = nullptr;
   int kacc = 0;
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false;
-  int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0;
+  int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
+  // TMA views of the spectral buffers: y-pass tiles (3-D), z-pass tiles with
+  // the component as a dimension (4-D; W with 1 or 3 components per box, A
+  // with 3 or 4)
+  tma::TensorMap map_wy, map_ay, map_wz1, map_wz3, map_az1, map_az3;
   std::vector<TimedLaunch> tl;      // launches recorded since the last read
   std::vector<cudaEvent_t> evpool;  // recycled events
   int64_t st_launch[KC_COUNT] = {};
@@ -288,6 +348,21 @@ cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
 }
 
 cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
+  if (h->pipelined) {
+    passes::PipeYArgs p{};
+    p.ncomp = ncomp;
+    p.tw = h->w.tw;
+    p.status = h->w.status;
+    const tma::TensorMap& m = spec == h->w.W ? h->map_wy : h->map_ay;
+    Timed tm(h, dir < 0 ? KC_Y_FWD : KC_Y_INV, 2.0 * ncomp * spec_bytes(h));
+    switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_ypass_pipe_##k(dir, m, p, h->st);
+      MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+    }
+    return cudaErrorInvalidValue;
+  }
   passes::YArgs a{};
   a.spec = spec;
   a.pstride = h->plane;
@@ -320,6 +395,29 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
   int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : mode == passes::Z_DIV ? KC_Z_DIV
            : mode == passes::Z_FINAL ? KC_Z_FINAL : KC_Z_SMOOTH;
   Timed tm(h, zc, zb);
+  if (h->pipelined) {
+    passes::PipeZArgs p{};
+    p.nout = nout;
+    p.kv = a.kv;
+    p.kp = a.kp;
+    p.tw = a.tw;
+    p.khat = a.khat;
+    p.norm = a.norm;
+    p.coef = a.coef;
+    p.status = h->w.status;
+    // input: rho^ (component 0 of W) for Newton, else three components;
+    // output: three components, phi^ separately as component 3 of A
+    const tma::TensorMap& mi =
+        in == h->w.W ? (mode == passes::Z_NEWTON ? h->map_wz1 : h->map_wz3) : h->map_az3;
+    const tma::TensorMap& mo = out == h->w.W ? h->map_wz3 : h->map_az3;
+    switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_zpass_pipe_##k(mode, mi, mo, h->map_az1, p, h->st);
+      MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_zpass_##k(mode, a, h->st);
@@ -352,43 +450,74 @@ int do_bin(mond_pm* h) {
   b.n = h->nf;
   b.ntx = h->ntx;
   b.ntile = h->ntile;
+  b.ncell = h->n3;
   b.N = h->N;
   b.cell = h->cell;
   b.off = h->off;
   b.mass = h->mass;
   b.key = h->w.key;
   b.count = h->w.count;
-  b.fill = h->w.fill;
+  b.cstart = h->w.cstart;
+  b.bsum = h->w.bsum;
   b.tile_start = h->w.tile_start;
   b.chunk_start = h->w.chunk_start;
   b.perm = h->w.perm;
   b.status = h->w.status;
-  CK(cudaMemsetAsync(h->w.count, 0, sizeof(int) * (h->ntile + 2), h->st));
-  CK(cudaMemsetAsync(h->w.fill, 0, sizeof(int) * (h->ntile + 2), h->st));
+  const int64_t M = h->n3 + 1;
+  const int nblk = (int)((M + parts::SCAN_B - 1) / parts::SCAN_B);
+  CK(cudaMemsetAsync(h->w.count, 0, sizeof(int) * M, h->st));
   unsigned nb = (unsigned)((h->N + 255) / 256);
   if (h->N > 0) {
     Timed tm(h, KC_BIN, 32.0 * h->N);
     parts::k_bin_count<<<nb, 256, 0, h->st>>>(b);
   }
   {
-    Timed tm(h, KC_BIN, 12.0 * (h->ntile + 1));
-    parts::k_bin_scan<<<1, 1024, 0, h->st>>>(b);
+    Timed tm(h, KC_BIN, 4.0 * M);
+    parts::k_scan_reduce<<<nblk, 1024, 0, h->st>>>(h->w.count, M, h->w.bsum);
+  }
+  {
+    Timed tm(h, KC_BIN, 8.0 * nblk);
+    parts::k_scan_blocks<<<1, 1024, 0, h->st>>>(h->w.bsum, nblk);
+  }
+  {
+    Timed tm(h, KC_BIN, 8.0 * M);
+    parts::k_scan_apply<<<nblk, 1024, 0, h->st>>>(h->w.count, M, h->w.bsum, h->w.cstart);
   }
   if (h->N > 0) {
-    Timed tm(h, KC_BIN, 12.0 * h->N);
+    Timed tm(h, KC_BIN, 16.0 * h->N);
     parts::k_bin_scatter<<<nb, 256, 0, h->st>>>(b);
+  }
+  {
+    Timed tm(h, KC_BIN, 12.0 * h->ntile);
+    parts::k_tile_chunks<<<1, 1024, 0, h->st>>>(b);
   }
   CK(cudaGetLastError());
   return MOND_OK;
 }
 
+// taps per lane kept in registers: the smallest instantiated width covering
+// the ball, 0 when it is too wide (the kernels then read the taps from shared
+// memory)
+int taps_per_lane(int nb) {
+  const int need = (nb + 31) / 32;
+  return need <= 3 ? 3 : need <= 8 ? 8 : need <= 28 ? 28 : 0;
+}
+
 size_t dep_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(unsigned long long) * (size_t)hw * hw * hw + sizeof(uint32_t) * h->nb;
+  return sizeof(uint32_t) * 2 * (size_t)hw * hw * hw + sizeof(uint32_t) * 3 * h->nb;
 }
 size_t gat_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(float) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * h->nb;
+  return sizeof(float) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * 2 * h->nb;
+}
+
+template <typename K>
+cudaError_t launch_smem(K kern, unsigned grid, unsigned block, size_t sm, cudaStream_t st, const void* args) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  void* a[] = {const_cast<void*>(args)};
+  return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(block), a, sm, st);
 }
 
 int do_deposit(mond_pm* h) {
@@ -409,16 +538,21 @@ int do_deposit(mond_pm* h) {
   d.chunk_start = h->w.chunk_start;
   d.lut = h->w.lut;
   d.ball = h->w.ball;
+  d.ball_lin = h->w.ball_lin;
+  d.ball_hlin = h->w.ball_hlin;
   d.dep = h->w.dep;
   d.kacc = h->kacc;
   d.work_counter = h->w.counters;
   CK(cudaMemsetAsync(h->w.counters, 0, sizeof(int), h->st));
   size_t sm = dep_smem(h);
-  CK(cudaFuncSetAttribute(parts::k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   {
     // algorithmic bytes: particle reads (perm, cell, offset, mass) and one int64 write per touched cell
     Timed tm(h, KC_DEPOSIT, 32.0 * h->N + 8.0 * h->n3);
-    parts::k_deposit<<<h->sms * 4, parts::DEP_NT, sm, h->st>>>(d);
+    const int tpl = taps_per_lane(h->nb);
+    if (tpl == 3) CK(launch_smem(parts::k_deposit<3>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
+    else if (tpl == 8) CK(launch_smem(parts::k_deposit<8>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
+    else if (tpl == 28) CK(launch_smem(parts::k_deposit<28>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
+    else CK(launch_smem(parts::k_deposit<0>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
   }
   CK(cudaGetLastError());
   h->have_dep = true;
@@ -441,6 +575,7 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.chunk_start = h->w.chunk_start;
   g.acc = h->w.acc;
   g.ball = h->w.ball;
+  g.ball_hlin = h->w.ball_hlin;
   g.g_out = g_out;
   g.dt = (float)dt;
   g.dt_over_s = (float)(dt / h->s);
@@ -452,11 +587,14 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.status = h->w.status;
   CK(cudaMemsetAsync(h->w.counters + 1, 0, sizeof(int), h->st));
   size_t sm = gat_smem(h);
-  CK(cudaFuncSetAttribute(parts::k_gather_push, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   {
     // algorithmic bytes: the acceleration mesh once, particles read and written
     Timed tm(h, KC_GATHER, 3.0 * real_bytes(h) + 64.0 * h->N);
-    parts::k_gather_push<<<h->sms * 2, parts::GAT_NT, sm, h->st>>>(g);
+    const int tpl = taps_per_lane(h->nb);
+    if (tpl == 3) CK(launch_smem(parts::k_gather_push<3>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
+    else if (tpl == 8) CK(launch_smem(parts::k_gather_push<8>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
+    else if (tpl == 28) CK(launch_smem(parts::k_gather_push<28>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
+    else CK(launch_smem(parts::k_gather_push<0>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
   }
   CK(cudaGetLastError());
   return MOND_OK;
@@ -630,6 +768,15 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
           ball.push_back((uint32_t)(dx + h->r) | ((uint32_t)(dy + h->r) << 8) | ((uint32_t)(dz + h->r) << 16));
   h->nb = (int)ball.size();
   carve(n, h->r, h->nb, max_particles, (char*)workspace, &h->w);
+  // per-tap linear offsets: in the mesh (for balls away from the faces) and in
+  // a tile plus its reach (hw = 8 + 2r)
+  std::vector<int32_t> blin(h->nb), bhlin(h->nb);
+  const int hw = parts::TILE + 2 * h->r;
+  for (int t = 0; t < h->nb; t++) {
+    int dx = ball[t] & 0xFF, dy = (ball[t] >> 8) & 0xFF, dz = (ball[t] >> 16) & 0xFF;
+    blin[t] = ((dz - h->r) * n + (dy - h->r)) * n + (dx - h->r);
+    bhlin[t] = (dz * hw + dy) * hw + dx;
+  }
   // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))
   const int lw = 2 * h->r + 1;
   std::vector<uint32_t> lut((size_t)65537 * lw);
@@ -651,9 +798,21 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
     kv[m] = (float)k;
     kp[m] = (2 * m == n) ? 0.0f : (float)(sin(2.0 * M_PI * f / n) / h->s);
   }
+  {
+    const int py = passes::pipe_py(n), pz = passes::pipe_pz(n), bx = passes::pipe_box(n);
+    bool ok = encode_spectral_map(&h->map_wy, h->w.W, n, 3, 2 * py, bx, 1) &&
+              encode_spectral_map(&h->map_ay, h->w.A, n, 4, 2 * py, bx, 1) &&
+              encode_component_map(&h->map_wz1, h->w.W, n, 3, 2 * pz, 1, bx) &&
+              encode_component_map(&h->map_wz3, h->w.W, n, 3, 2 * pz, 3, bx) &&
+              encode_component_map(&h->map_az1, h->w.A, n, 4, 2 * pz, 1, bx) &&
+              encode_component_map(&h->map_az3, h->w.A, n, 4, 2 * pz, 3, bx);
+    if (!ok) h->pipelined = 0;  // no driver entry point: the unpipelined passes
+  }
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemcpyAsync(h->w.lut, lut.data(), sizeof(uint32_t) * lut.size(), cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.ball, ball.data(), sizeof(uint32_t) * ball.size(), cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.ball_lin, blin.data(), sizeof(int32_t) * h->nb, cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.ball_hlin, bhlin.data(), sizeof(int32_t) * h->nb, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.kv, kv.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.kp, kp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
@@ -685,6 +844,9 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_KEEP_PHI: h->keep_phi = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_TRACK_DH: h->track_dh = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_USE_GRAPH: h->use_graph = value ? 1 : 0; return MOND_OK;
+    case MOND_OPT_PIPELINED:
+      h->pipelined = value ? 1 : 0;
+      return MOND_OK;
     case MOND_OPT_TIMING:
       collect_timing(h);
       h->timing = value ? 1 : 0;

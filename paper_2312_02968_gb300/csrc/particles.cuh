@@ -7,29 +7,39 @@
 
 namespace parts {
 
-constexpr int TILE = 8;       // mesh tile side used for binning
+constexpr int TILE = 8;       // mesh tile side: work items never span two tiles
 constexpr int DEP_NT = 256;   // threads per deposit CTA
 constexpr int GAT_NT = 256;   // threads per gather CTA
-constexpr int CHUNK = 1024;   // particles per work item
+constexpr int CHUNK = 2048;   // particles per work item
 constexpr int QHALF = 32768;  // offset quantisation: q = round(offset * 2^16) + 32768
+constexpr int SCAN_B = 8192;  // elements per block of the key scan
+
+// Sort key of a cell: tile-major, then the cell inside its 8^3 tile, so the
+// particles of one tile are contiguous and, inside it, grouped by cell.
+__device__ __forceinline__ uint32_t cell_key(int c0, int c1, int c2, int ntx) {
+  uint32_t t = (uint32_t)(((c2 >> 3) * ntx + (c1 >> 3)) * ntx + (c0 >> 3));
+  return t * 512u + (uint32_t)(((c2 & 7) * 8 + (c1 & 7)) * 8 + (c0 & 7));
+}
 
 struct BinArgs {
   int n, ntx, ntile;
+  int64_t ncell;  // n^3 (the key of an invalid particle)
   int64_t N;
   const int32_t* cell;
   const float* off;
   const float* mass;
   uint32_t* key;
-  int* count;
-  int* fill;
-  int* tile_start;   // ntile + 2 (last = invalid bin end)
+  int* count;        // ncell + 1 counters (cleared before)
+  int* cstart;       // ncell + 2: first sorted position of each key
+  int* bsum;         // per-block sums of the scan
+  int* tile_start;   // ntile + 1
   int* chunk_start;  // ntile + 1
   uint32_t* perm;
   uint32_t* status;
 };
 
-// Bin key of each particle: its 8^3 tile, or ntile when the particle is invalid
-// (cell outside [0, n), offset outside [-1/2, 1/2] or non-finite, mass non-finite).
+// Key of each particle, or ncell when it is invalid (cell outside [0, n),
+// offset outside [-1/2, 1/2] or not finite, mass not finite).
 __global__ void k_bin_count(BinArgs a) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
@@ -40,78 +50,113 @@ __global__ void k_bin_count(BinArgs a) {
     float o = a.off[3 * i + d];
     ok &= (c[d] >= 0 && c[d] < a.n && o >= -0.5f && o <= 0.5f);
   }
-  float m = a.mass[i];
-  ok &= isfinite(m);
-  uint32_t k = ok ? (uint32_t)(((c[2] >> 3) * a.ntx + (c[1] >> 3)) * a.ntx + (c[0] >> 3)) : (uint32_t)a.ntile;
+  ok &= isfinite(a.mass[i]);
+  uint32_t k = ok ? cell_key(c[0], c[1], c[2], a.ntx) : (uint32_t)a.ncell;
   if (!ok) set_status(a.status, ST_DOMAIN);
   a.key[i] = k;
   atomicAdd(&a.count[k], 1);
 }
 
-// Single-CTA exclusive scans of the tile counts (particles and work chunks).
-__global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
-  __shared__ int wsum_p[32], wsum_c[32];
-  const int tid = threadIdx.x;
-  const int M = a.ntile + 1;  // includes the invalid bin
-  const int per = (M + 1023) / 1024;
-  const int b0 = tid * per, b1 = min(M, b0 + per);
-  int sp = 0, sc = 0;
-  for (int i = b0; i < b1; i++) {
-    int c = a.count[i];
-    sp += c;
-    if (i < a.ntile) sc += (c + CHUNK - 1) / CHUNK;
-  }
-  // block exclusive scan of (sp, sc)
-  int lane = tid & 31, w = tid >> 5;
-  int ip = sp, ic = sc;
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
   for (int o = 1; o < 32; o <<= 1) {
-    int tp = __shfl_up_sync(0xffffffffu, ip, o), tc = __shfl_up_sync(0xffffffffu, ic, o);
-    if (lane >= o) {
-      ip += tp;
-      ic += tc;
-    }
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
   }
-  if (lane == 31) {
-    wsum_p[w] = ip;
-    wsum_c[w] = ic;
-  }
+  if (lane == 31) wsum[w] = x;
   __syncthreads();
   if (w == 0) {
-    int vp = wsum_p[lane], vc = wsum_c[lane];
+    int y = lane < nw ? wsum[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
-      int tp = __shfl_up_sync(0xffffffffu, vp, o), tc = __shfl_up_sync(0xffffffffu, vc, o);
-      if (lane >= o) {
-        vp += tp;
-        vc += tc;
-      }
+      int t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
     }
-    wsum_p[lane] = vp;
-    wsum_c[lane] = vc;
+    wsum[lane] = y;
   }
   __syncthreads();
-  int base_p = (w > 0 ? wsum_p[w - 1] : 0) + ip - sp;
-  int base_c = (w > 0 ? wsum_c[w - 1] : 0) + ic - sc;
-  for (int i = b0; i < b1; i++) {
-    a.tile_start[i] = base_p;
-    int c = a.count[i];
-    base_p += c;
-    if (i < a.ntile) {
-      a.chunk_start[i] = base_c;
-      base_c += (c + CHUNK - 1) / CHUNK;
-    }
-  }
-  if (tid == 1023) {
-    a.tile_start[M] = base_p;
-    a.chunk_start[a.ntile] = base_c;
+  int r = (w > 0 ? wsum[w - 1] : 0) + x - v;
+  if (total) *total = wsum[nw - 1];
+  __syncthreads();
+  return r;
+}
+
+// Scan of the M = ncell + 1 counters in three launches.
+__global__ void __launch_bounds__(1024) k_scan_reduce(const int* cnt, int64_t M, int* bsum) {
+  __shared__ int wsum[32];
+  int64_t b0 = (int64_t)blockIdx.x * SCAN_B;
+  int s = 0;
+  for (int k = threadIdx.x; k < SCAN_B; k += 1024)
+    if (b0 + k < M) s += cnt[b0 + k];
+  int tot;
+  block_excl_scan(s, wsum, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(int* bsum, int nblk) {
+  __shared__ int wsum[32];
+  const int per = (nblk + 1023) / 1024;
+  const int i0 = threadIdx.x * per, i1 = min(nblk, i0 + per);
+  int s = 0;
+  for (int i = i0; i < i1; i++) s += bsum[i];
+  int base = block_excl_scan(s, wsum, nullptr);
+  for (int i = i0; i < i1; i++) {
+    int v = bsum[i];
+    bsum[i] = base;
+    base += v;
   }
 }
 
+__global__ void __launch_bounds__(1024) k_scan_apply(const int* cnt, int64_t M, const int* bsum, int* cstart) {
+  __shared__ int wsum[32];
+  constexpr int PER = SCAN_B / 1024;
+  const int64_t b0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * PER;
+  int v[PER], s = 0;
+  for (int k = 0; k < PER; k++) {
+    v[k] = (b0 + k < M) ? cnt[b0 + k] : 0;
+    s += v[k];
+  }
+  int tot;
+  int base = block_excl_scan(s, wsum, &tot) + bsum[blockIdx.x];
+  for (int k = 0; k < PER; k++) {
+    if (b0 + k < M) cstart[b0 + k] = base;
+    base += v[k];
+  }
+  if (b0 <= M - 1 && M - 1 < b0 + PER) cstart[M] = base;  // the thread holding the last key writes the total
+}
+
+// Particles -> sorted positions (the order inside a cell is immaterial).
 __global__ void k_bin_scatter(BinArgs a) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   uint32_t k = a.key[i];
-  int pos = a.tile_start[k] + atomicAdd(&a.fill[k], 1);
-  a.perm[pos] = (uint32_t)i;
+  int old = atomicSub(&a.count[k], 1);
+  a.perm[a.cstart[k] + old - 1] = (uint32_t)i;
+}
+
+// Tile ranges and the exclusive scan of work chunks per tile (single CTA).
+__global__ void __launch_bounds__(1024) k_tile_chunks(BinArgs a) {
+  __shared__ int wsum[32];
+  const int T = a.ntile;
+  const int per = (T + 1023) / 1024;
+  const int t0 = threadIdx.x * per, t1 = min(T, t0 + per);
+  int s = 0;
+  for (int t = t0; t < t1; t++) {
+    int c = a.cstart[(int64_t)(t + 1) * 512] - a.cstart[(int64_t)t * 512];
+    s += (c + CHUNK - 1) / CHUNK;
+  }
+  int tot;
+  int base = block_excl_scan(s, wsum, &tot);
+  for (int t = t0; t < t1; t++) {
+    int ts = a.cstart[(int64_t)t * 512], te = a.cstart[(int64_t)(t + 1) * 512];
+    a.tile_start[t] = ts;
+    a.chunk_start[t] = base;
+    base += (te - ts + CHUNK - 1) / CHUNK;
+  }
+  if (threadIdx.x == 0) {
+    a.tile_start[T] = a.cstart[a.ncell];
+    a.chunk_start[T] = tot;
+  }
 }
 
 // Work item w -> tile t with chunk_start[t] <= w < chunk_start[t + 1].
@@ -136,71 +181,179 @@ struct DepArgs {
   const uint32_t* perm;
   const int* tile_start;
   const int* chunk_start;
-  const uint32_t* lut;   // (65537) x (2r+1) words, row q + 32768
-  const uint32_t* ball;  // packed (dx+r) | (dy+r) << 8 | (dz+r) << 16
+  const uint32_t* lut;      // (65537) x (2r+1) words, row q + 32768
+  const uint32_t* ball;     // packed (dx+r) | (dy+r) << 8 | (dz+r) << 16
+  const int32_t* ball_lin;  // per tap: ((dz-r) n + (dy-r)) n + (dx-r)
+  const int32_t* ball_hlin; // per tap: ((dz+r') hw + (dy+r')) hw + (dx+r') with packed offsets
   uint64_t* dep;
   int kacc;
   int* work_counter;  // persistent-grid work queue (zeroed before launch)
 };
 
+// Per-warp scratch of the deposit: axis weights, mass-folded x weights and
+// y.z row weights of the particle being processed.
+struct DepWarp {
+  uint32_t W[3][16];
+  uint32_t MX[16];
+  uint32_t R[15 * 15];
+};
 
-template <bool DENSE>
-__device__ __forceinline__ void deposit_particles(const DepArgs& a, int p0, int p1, int ox, int oy, int oz, int hw,
-                                                  unsigned long long* sacc, const uint32_t* sball,
-                                                  uint32_t (*swt)[3][16]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// 64-bit add into a shared accumulator held as two 32-bit words: the low
+// word's carry goes to the high word, so the pair sums exactly modulo 2^64.
+__device__ __forceinline__ void sadd64(uint32_t* lo, uint32_t* hi, int idx, uint64_t v) {
+  uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
+  uint32_t old = atomicAdd(lo + idx, vl);
+  vh += (old + vl < old) ? 1u : 0u;
+  if (vh) atomicAdd(hi + idx, vh);
+}
+
+__device__ __forceinline__ bool ball_inside(int c0, int c1, int c2, int r, int n) {
+  return c0 >= r && c1 >= r && c2 >= r && c0 < n - r && c1 < n - r && c2 < n - r;
+}
+
+// Per-lane assignments of the per-particle tables, fixed for a kernel:
+// axis-weight slots (2 per lane cover 3w <= 45) and y.z rows (8 per lane cover
+// w^2 <= 225), packed (axis or row) << 8 | index, 0xFFFFFFFF when unused.
+struct LaneSlots {
+  uint32_t wl[2], rl[8];
+  __device__ __forceinline__ void init(int lane, int w) {
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const int t = lane + 32 * k;
+      wl[k] = t < 3 * w ? ((uint32_t)(t / w) << 8) | (uint32_t)(t % w) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int t = lane + 32 * k;
+      rl[k] = t < w * w ? ((uint32_t)(t / w) << 8) | (uint32_t)(t % w) : 0xFFFFFFFFu;
+    }
+  }
+};
+
+// One warp deposits the particles [q0, q1): per particle the lanes build the
+// mass-folded x weights and the y.z row weights, then each lane evaluates the
+// taps t = lane + 32 j with one exact 32x32->64 product and a round-half-up
+// shift, and adds the result to the shared tile (dense items) or to the global
+// accumulator (sparse items). Integer addition makes the order immaterial.
+// The taps a lane owns (t = lane + 32 j), held in registers when TPL > 0:
+// pk = y.z row index | x index << 8, and the tap's offset in the staged tile.
+template <int TPL>
+struct TapRegs {
+  uint32_t pk[TPL > 0 ? TPL : 1];
+  int32_t hl[TPL > 0 ? TPL : 1];
+  __device__ __forceinline__ void load(const uint32_t* spk, const int32_t* shlin, int nb, int lane) {
+#pragma unroll
+    for (int j = 0; j < TPL; j++) {
+      const int t = lane + 32 * j;
+      pk[j] = t < nb ? spk[t] : 0xFFFFFFFFu;
+      hl[j] = t < nb ? shlin[t] : 0;
+    }
+  }
+};
+
+template <bool DENSE, int TPL>
+__device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
+                                              uint32_t* slo, uint32_t* shi, const uint32_t* spk,
+                                              const int32_t* slin, const int32_t* shlin, const LaneSlots& ls,
+                                              const TapRegs<TPL>& tr, DepWarp* sw) {
+  const int lane = threadIdx.x & 31;
   const int w = 2 * a.r + 1;
-  for (int p = p0 + warp; p < p1; p += nw) {
-    uint32_t i = __ldg(a.perm + p);
-    int c0 = __ldg(a.cell + 3 * i), c1 = __ldg(a.cell + 3 * i + 1), c2 = __ldg(a.cell + 3 * i + 2);
-    uint32_t mb = __float_as_uint(__ldg(a.mass + i));
-    // axis weights of this particle into the warp's table
-    for (int t = lane; t < 3 * w; t += 32) {
-      int ax = t / w, j = t % w;
-      float o = __ldg(a.off + 3 * i + ax);
-      int q = __float2int_rn(o * 65536.0f) + QHALF;
-      swt[warp][ax][j] = __ldg(a.lut + (int64_t)q * w + j);
+  for (int p = q0; p < q1; p++) {
+    const uint32_t i = __ldg(a.perm + p);
+    const int c0 = __ldg(a.cell + 3 * i), c1 = __ldg(a.cell + 3 * i + 1), c2 = __ldg(a.cell + 3 * i + 2);
+    const uint32_t mb = __float_as_uint(__ldg(a.mass + i));
+    uint32_t msig;
+    int e2;
+    mass_parts(mb, &msig, &e2);
+    const bool neg = (mb >> 31) != 0;
+    const int sh = 40 - a.kacc - e2;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      if (ls.wl[k] != 0xFFFFFFFFu) {
+        const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
+        const int q = __float2int_rn(__ldg(a.off + 3 * i + ax) * 65536.0f) + QHALF;
+        sw->W[ax][j] = __ldg(a.lut + (int64_t)q * w + j);
+      }
     }
     __syncwarp();
-    int eb = (mb >> 23) & 0xFF;
-    uint32_t msig = eb ? ((mb & 0x7FFFFFu) | 0x800000u) : (mb & 0x7FFFFFu);
-    int e2 = eb ? eb - 150 : -149;
-    int sh = 40 - a.kacc - e2;
-    bool neg = (mb >> 31) != 0;
-    for (int t = lane; t < a.nb; t += 32) {
-      uint32_t pk = sball[t];
-      int dx = pk & 0xFF, dy = (pk >> 8) & 0xFF, dz = (pk >> 16) & 0xFF;
-      uint64_t c = tap_contrib(swt[warp][0][dx], swt[warp][1][dy], swt[warp][2][dz], msig, sh);
-      if (neg) c = 0ull - c;
-      if (c == 0) continue;
-      if constexpr (DENSE) {
-        // local halo index: (c - origin - r) + packed tap offset, in [0, hw)
-        int idx = ((c2 - oz - a.r + dz) * hw + (c1 - oy - a.r + dy)) * hw + (c0 - ox - a.r + dx);
-        atomicAdd(sacc + idx, (unsigned long long)c);
-      } else {
-        int gx = wrapi(c0 + dx - a.r, a.n), gy = wrapi(c1 + dy - a.r, a.n), gz = wrapi(c2 + dz - a.r, a.n);
-        atomicAdd((unsigned long long*)(a.dep + ((int64_t)gz * a.n + gy) * a.n + gx), (unsigned long long)c);
+    if (lane < w) sw->MX[lane] = fold_x(sw->W[0][lane], msig);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+      if (ls.rl[k] != 0xFFFFFFFFu) sw->R[lane + 32 * k] = row_yz(sw->W[1][ls.rl[k] >> 8], sw->W[2][ls.rl[k] & 0xFF]);
+    __syncwarp();
+    const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
+    if (DENSE && TPL > 0 && sh > 0 && sh < 64 && !neg) {
+      // common case: exact product, round-half-up shift, split shared add
+      const uint64_t rnd = 1ull << (sh - 1);
+#pragma unroll
+      for (int j = 0; j < TPL; j++) {
+        if (tr.pk[j] != 0xFFFFFFFFu) {
+          const uint64_t v = ((uint64_t)sw->R[tr.pk[j] & 0xFF] * sw->MX[tr.pk[j] >> 8] + rnd) >> sh;
+          sadd64(slo, shi, hbase + tr.hl[j], v);
+        }
+      }
+    } else {
+      const bool inside = ball_inside(c0, c1, c2, a.r, a.n);
+      const int64_t clin = ((int64_t)c2 * a.n + c1) * a.n + c0;
+      for (int t = lane; t < a.nb; t += 32) {
+        const uint32_t pk = spk[t];
+        uint64_t v = round_shift((uint64_t)sw->R[pk & 0xFF] * sw->MX[pk >> 8], sh);
+        if (neg) v = 0ull - v;
+        if (v == 0ull) continue;
+        if constexpr (DENSE) {
+          sadd64(slo, shi, hbase + shlin[t], v);
+        } else {
+          int64_t gi;
+          if (inside) {
+            gi = clin + slin[t];
+          } else {
+            const uint32_t q = __ldg(a.ball + t);
+            int gx = c0 + (int)(q & 0xFF) - a.r, gy = c1 + (int)((q >> 8) & 0xFF) - a.r,
+                gz = c2 + (int)((q >> 16) & 0xFF) - a.r;
+            gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
+            gy += gy < 0 ? a.n : (gy >= a.n ? -a.n : 0);
+            gz += gz < 0 ? a.n : (gz >= a.n ? -a.n : 0);
+            gi = ((int64_t)gz * a.n + gy) * a.n + gx;
+          }
+          atomicAdd((unsigned long long*)(a.dep + gi), (unsigned long long)v);
+        }
       }
     }
     __syncwarp();
   }
 }
 
-// Persistent deposit: CTAs take work items (chunks of up to CHUNK particles of
-// one tile) from a counter. Dense items accumulate into a shared-memory copy
-// of the tile plus its reach (int64, exact), then add it to the global
-// accumulator; sparse items add each tap to the global accumulator directly.
-// Integer addition makes the result independent of all ordering.
+// Persistent deposit: CTAs take work items (chunks of up to CHUNK cell-sorted
+// particles of one tile) from a counter. Each warp takes a contiguous slice
+// of the chunk. Dense items accumulate into a shared copy of the tile plus its
+// reach and add it to the global accumulator once; sparse items add to the
+// global accumulator directly.
+template <int TPL>
 __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
-  extern __shared__ unsigned long long dsm[];
-  __shared__ uint32_t swt[DEP_NT / 32][3][16];
+  extern __shared__ uint32_t dsm[];
+  __shared__ DepWarp sw[DEP_NT / 32];
   __shared__ int s_item;
   const int hw = TILE + 2 * a.r;
   const int hv = hw * hw * hw;
-  unsigned long long* sacc = dsm;
-  uint32_t* sball = reinterpret_cast<uint32_t*>(dsm + hv);
-  for (int t = threadIdx.x; t < a.nb; t += blockDim.x) sball[t] = a.ball[t];
+  const int w = 2 * a.r + 1;
+  uint32_t* slo = dsm;
+  uint32_t* shi = dsm + hv;
+  uint32_t* spk = dsm + 2 * hv;
+  int32_t* slin = reinterpret_cast<int32_t*>(spk + a.nb);
+  int32_t* shlin = slin + a.nb;
+  for (int t = threadIdx.x; t < a.nb; t += blockDim.x) {
+    const uint32_t q = a.ball[t];
+    spk[t] = (((q >> 8) & 0xFF) * w + ((q >> 16) & 0xFF)) | ((q & 0xFF) << 8);
+    slin[t] = a.ball_lin[t];
+    shlin[t] = a.ball_hlin[t];
+  }
+  __syncthreads();
+  LaneSlots ls;
+  ls.init(threadIdx.x & 31, w);
+  TapRegs<TPL> tr;
+  tr.load(spk, shlin, a.nb, threadIdx.x & 31);
   const int nitems = __ldg(a.chunk_start + a.ntile);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
@@ -213,21 +366,34 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
     const int p1 = min(te, p0 + CHUNK);
     const int tx = t % a.ntx, ty = (t / a.ntx) % a.ntx, tz = t / (a.ntx * a.ntx);
     const int ox = tx * TILE - a.r, oy = ty * TILE - a.r, oz = tz * TILE - a.r;
-    const bool dense = (int64_t)(p1 - p0) * a.nb >= (int64_t)hv;
+    const int len = (p1 - p0 + nw - 1) / nw;
+    const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
+    const bool dense = (int64_t)(p1 - p0) * a.nb >= 2 * (int64_t)hv;
     if (dense) {
-      for (int k = threadIdx.x; k < hv; k += blockDim.x) sacc[k] = 0ull;
+      for (int k = threadIdx.x; k < 2 * hv; k += blockDim.x) dsm[k] = 0u;
       __syncthreads();
-      deposit_particles<true>(a, p0, p1, ox, oy, oz, hw, sacc, sball, swt);
+      deposit_range<true, TPL>(a, q0, q1, ox, oy, oz, hw, slo, shi, spk, slin, shlin, ls, tr, sw + warp);
       __syncthreads();
-      for (int k = threadIdx.x; k < hv; k += blockDim.x) {
-        unsigned long long v = sacc[k];
-        if (v == 0ull) continue;
-        int lx = k % hw, ly = (k / hw) % hw, lz = k / (hw * hw);
-        int gx = wrapi(ox + lx, a.n), gy = wrapi(oy + ly, a.n), gz = wrapi(oz + lz, a.n);
-        atomicAdd((unsigned long long*)(a.dep + ((int64_t)gz * a.n + gy) * a.n + gx), v);
+      const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
+      // one halo row (fixed ly, lz) per warp step, lanes over x
+      for (int row = warp; row < hw * hw; row += nw) {
+        const int ly = row % hw, lz = row / hw;
+        int gy = oy + ly, gz = oz + lz;
+        if (!inside) {
+          gy += gy < 0 ? a.n : (gy >= a.n ? -a.n : 0);
+          gz += gz < 0 ? a.n : (gz >= a.n ? -a.n : 0);
+        }
+        for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
+          const int k = row * hw + lx;
+          const unsigned long long v = ((unsigned long long)shi[k] << 32) | slo[k];
+          if (v == 0ull) continue;
+          int gx = ox + lx;
+          if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
+          atomicAdd((unsigned long long*)(a.dep + ((int64_t)gz * a.n + gy) * a.n + gx), v);
+        }
       }
     } else {
-      deposit_particles<false>(a, p0, p1, ox, oy, oz, hw, sacc, sball, swt);
+      deposit_range<false, TPL>(a, q0, q1, ox, oy, oz, hw, slo, shi, spk, slin, shlin, ls, tr, sw + warp);
     }
   }
 }
@@ -245,6 +411,7 @@ struct GatArgs {
   const int* chunk_start;
   const float* acc;       // 3 real planes
   const uint32_t* ball;
+  const int32_t* ball_hlin;  // per tap: offset inside a tile plus its reach
   float* g_out;           // optional [N][3] force output
   float dt;               // kick time step
   float dt_over_s;        // drift: offset += v dt / s
@@ -255,18 +422,111 @@ struct GatArgs {
   uint32_t* status;
 };
 
+struct GatWarp {
+  float W[3][16];
+  float WYZ[15 * 15];
+};
+
+// One warp gathers the particles [q0, q1) from the staged tile: per particle
+// the lanes build the x weights and the y.z row weights (FP32 exp), then each
+// lane sums its taps t = lane + 32 j as w = WYZ[row] W[x] times the three
+// staged components, a warp sum gives Eq. gi, and lanes 0..2 kick and drift.
+template <int TPL>
+__device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
+                                             const float* sa, int hv, const uint32_t* spk, const int32_t* shlin,
+                                             const LaneSlots& ls, const TapRegs<TPL>& tr, GatWarp* sw) {
+  const int lane = threadIdx.x & 31;
+  for (int p = q0; p < q1; p++) {
+    const uint32_t i = __ldg(a.perm + p);
+    const int c0 = a.cell[3 * i], c1 = a.cell[3 * i + 1], c2 = a.cell[3 * i + 2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      if (ls.wl[k] != 0xFFFFFFFFu) {
+        const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
+        const float u = (float)(j - a.r) - a.off[3 * i + ax];
+        sw->W[ax][j] = expf(-u * u * a.inv2s2) * a.gnorm;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+      if (ls.rl[k] != 0xFFFFFFFFu) sw->WYZ[lane + 32 * k] = sw->W[1][ls.rl[k] >> 8] * sw->W[2][ls.rl[k] & 0xFF];
+    __syncwarp();
+    const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if constexpr (TPL > 0) {
+#pragma unroll
+      for (int j = 0; j < TPL; j++) {
+        if (tr.pk[j] != 0xFFFFFFFFu) {
+          const float wgt = sw->WYZ[tr.pk[j] & 0xFF] * sw->W[0][tr.pk[j] >> 8];
+          const int idx = hbase + tr.hl[j];
+          gx = fmaf(wgt, sa[idx], gx);
+          gy = fmaf(wgt, sa[hv + idx], gy);
+          gz = fmaf(wgt, sa[2 * hv + idx], gz);
+        }
+      }
+    } else {
+      for (int t = lane; t < a.nb; t += 32) {
+        const uint32_t pk = spk[t];
+        const float wgt = sw->WYZ[pk & 0xFF] * sw->W[0][pk >> 8];
+        const int idx = hbase + shlin[t];
+        gx = fmaf(wgt, sa[idx], gx);
+        gy = fmaf(wgt, sa[hv + idx], gy);
+        gz = fmaf(wgt, sa[2 * hv + idx], gz);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      gx += __shfl_xor_sync(0xffffffffu, gx, o);
+      gy += __shfl_xor_sync(0xffffffffu, gy, o);
+      gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    }
+    if (lane < 3) {
+      const float g = lane == 0 ? gx : (lane == 1 ? gy : gz);
+      if (a.g_out) a.g_out[3 * i + lane] = g;
+      if (!isfinite(g)) set_status(a.status, ST_NAN);
+      if (a.do_kick) {
+        const float v = a.vel[3 * i + lane] + g * a.dt;
+        a.vel[3 * i + lane] = v;
+        if (a.do_drift) {
+          const float o = a.off[3 * i + lane] + v * a.dt_over_s;
+          const float sh = floorf(o + 0.5f);
+          int c = (lane == 0 ? c0 : (lane == 1 ? c1 : c2)) + (int)sh;
+          c += c < 0 ? a.n : (c >= a.n ? -a.n : 0);
+          a.off[3 * i + lane] = o - sh;
+          a.cell[3 * i + lane] = c;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Persistent gather: CTAs take work items (chunks of one tile) from a
+// counter, stage the acceleration mesh over the tile plus its reach (periodic
+// wrap) in shared memory, one row per warp step, and gather from it.
+template <int TPL>
 __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
   extern __shared__ float gsm[];
-  __shared__ float swt[GAT_NT / 32][3][16];
+  __shared__ GatWarp sw[GAT_NT / 32];
   __shared__ int s_item;
   const int hw = TILE + 2 * a.r;
   const int hv = hw * hw * hw;
-  float* sa = gsm;                                      // 3 x hv
-  uint32_t* sball = reinterpret_cast<uint32_t*>(gsm + 3 * hv);
-  for (int t = threadIdx.x; t < a.nb; t += blockDim.x) sball[t] = a.ball[t];
-  const int nitems = __ldg(a.chunk_start + a.ntile);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int w = 2 * a.r + 1;
+  float* sa = gsm;  // 3 x hv
+  uint32_t* spk = reinterpret_cast<uint32_t*>(gsm + 3 * hv);
+  int32_t* shlin = reinterpret_cast<int32_t*>(spk + a.nb);
+  for (int t = threadIdx.x; t < a.nb; t += blockDim.x) {
+    const uint32_t q = a.ball[t];
+    spk[t] = (((q >> 8) & 0xFF) * w + ((q >> 16) & 0xFF)) | ((q & 0xFF) << 8);
+    shlin[t] = a.ball_hlin[t];
+  }
+  __syncthreads();
+  LaneSlots ls;
+  ls.init(threadIdx.x & 31, w);
+  TapRegs<TPL> tr;
+  tr.load(spk, shlin, a.nb, threadIdx.x & 31);
+  const int nitems = __ldg(a.chunk_start + a.ntile);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t n3 = (int64_t)a.n * a.n * a.n;
   while (true) {
     __syncthreads();
@@ -280,59 +540,28 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
     const int p1 = min(te, p0 + CHUNK);
     const int tx = t % a.ntx, ty = (t / a.ntx) % a.ntx, tz = t / (a.ntx * a.ntx);
     const int ox = tx * TILE - a.r, oy = ty * TILE - a.r, oz = tz * TILE - a.r;
-    // stage the tile plus its reach (periodic wrap) for the three components
-    for (int k = threadIdx.x; k < hv; k += blockDim.x) {
-      int lx = k % hw, ly = (k / hw) % hw, lz = k / (hw * hw);
-      int gx = wrapi(ox + lx, a.n), gy = wrapi(oy + ly, a.n), gz = wrapi(oz + lz, a.n);
-      int64_t gi = ((int64_t)gz * a.n + gy) * a.n + gx;
-      sa[k] = __ldg(a.acc + gi);
-      sa[hv + k] = __ldg(a.acc + n3 + gi);
-      sa[2 * hv + k] = __ldg(a.acc + 2 * n3 + gi);
+    const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
+    for (int row = warp; row < hw * hw; row += nw) {
+      const int ly = row % hw, lz = row / hw;
+      int gy = oy + ly, gz = oz + lz;
+      if (!inside) {
+        gy += gy < 0 ? a.n : (gy >= a.n ? -a.n : 0);
+        gz += gz < 0 ? a.n : (gz >= a.n ? -a.n : 0);
+      }
+      const int64_t rbase = ((int64_t)gz * a.n + gy) * a.n;
+      for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
+        int gx = ox + lx;
+        if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
+        const int k = row * hw + lx;
+        sa[k] = __ldg(a.acc + rbase + gx);
+        sa[hv + k] = __ldg(a.acc + n3 + rbase + gx);
+        sa[2 * hv + k] = __ldg(a.acc + 2 * n3 + rbase + gx);
+      }
     }
     __syncthreads();
-    for (int p = p0 + warp; p < p1; p += nw) {
-      uint32_t i = __ldg(a.perm + p);
-      int c0 = a.cell[3 * i], c1 = a.cell[3 * i + 1], c2 = a.cell[3 * i + 2];
-      for (int tt = lane; tt < 3 * w; tt += 32) {
-        int ax = tt / w, j = tt % w;
-        float u = (float)(j - a.r) - a.off[3 * i + ax];
-        swt[warp][ax][j] = expf(-u * u * a.inv2s2) * a.gnorm;
-      }
-      __syncwarp();
-      float gx = 0.f, gy = 0.f, gz = 0.f;
-      const int base = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
-      for (int tt = lane; tt < a.nb; tt += 32) {
-        uint32_t pk = sball[tt];
-        int dx = pk & 0xFF, dy = (pk >> 8) & 0xFF, dz = (pk >> 16) & 0xFF;
-        float wgt = swt[warp][0][dx] * swt[warp][1][dy] * swt[warp][2][dz];
-        int idx = base + (dz * hw + dy) * hw + dx;
-        gx = fmaf(wgt, sa[idx], gx);
-        gy = fmaf(wgt, sa[hv + idx], gy);
-        gz = fmaf(wgt, sa[2 * hv + idx], gz);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        gx += __shfl_xor_sync(0xffffffffu, gx, o);
-        gy += __shfl_xor_sync(0xffffffffu, gy, o);
-        gz += __shfl_xor_sync(0xffffffffu, gz, o);
-      }
-      if (lane < 3) {
-        float g = lane == 0 ? gx : (lane == 1 ? gy : gz);
-        if (a.g_out) a.g_out[3 * i + lane] = g;
-        if (!isfinite(g)) set_status(a.status, ST_NAN);
-        if (a.do_kick) {
-          float v = a.vel[3 * i + lane] + g * a.dt;
-          a.vel[3 * i + lane] = v;
-          if (a.do_drift) {
-            float o = a.off[3 * i + lane] + v * a.dt_over_s;
-            float sh = floorf(o + 0.5f);
-            int c = (lane == 0 ? c0 : (lane == 1 ? c1 : c2)) + (int)sh;
-            a.off[3 * i + lane] = o - sh;
-            a.cell[3 * i + lane] = wrapi(c, a.n);
-          }
-        }
-      }
-      __syncwarp();
-    }
+    const int len = (p1 - p0 + nw - 1) / nw;
+    const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
+    gather_range<TPL>(a, q0, q1, ox, oy, oz, hw, sa, hv, spk, shlin, ls, tr, sw + warp);
   }
 }
 

@@ -497,3 +497,291 @@ __global__ void __launch_bounds__(NT) k_zpass(ZArgs a) {
 }
 
 }  // namespace passes
+
+// ===========================================================================
+// Pipelined y- and z-passes: persistent CTAs stream tiles through a two-stage
+// shared-memory ring. One thread issues TMA tile loads (completion on an
+// mbarrier) for tile i+1 and TMA stores of tile i-1 while all threads
+// transform tile i, so HBM traffic overlaps the shared-memory FFT.
+// ===========================================================================
+#include "tma.cuh"
+
+namespace passes {
+
+// Tile geometry of the pipelined passes: P columns per tile (y: PY, z: PZ),
+// row boxes of at most 256 (the TMA box limit) dividing N.
+constexpr int pipe_py(int n) { return n >= 384 ? 8 : 16; }
+constexpr int pipe_pz(int n) { return n >= 384 ? 4 : (n >= 192 ? 8 : 16); }
+constexpr int pipe_box(int n) { return n <= 256 ? n : (n % 256 == 0 ? 256 : 128); }
+
+template <int N>
+struct PipeCfg {
+  static constexpr int PY = pipe_py(N);
+  static constexpr int PZ = pipe_pz(N);
+  static constexpr int BOX = pipe_box(N);
+  static constexpr int NBOX = N / BOX;
+  static constexpr int NX = N / 2 + 1;
+  static constexpr int NBLKY = (NX + PY - 1) / PY;
+  static constexpr int NBLKZ = (NX + PZ - 1) / PZ;
+};
+
+struct PipeYArgs {
+  int ncomp;  // components to transform (tiles = NBLKY * N * ncomp)
+  const float2* tw;
+  uint32_t* status;
+};
+
+struct PipeZArgs {
+  int nout;  // Z_NEWTON / Z_FINAL outputs (3 or 4)
+  const float* kv;
+  const float* kp;
+  const float2* tw;
+  const float* khat;
+  float norm;
+  float coef;
+  uint32_t* status;
+};
+
+// Common ring driver. LoadF(tile, stage_ptr, bar) issues the loads of a tile
+// and returns the bytes expected; ComputeF(tile, stage_ptr) transforms it in
+// place; StoreF(tile, stage_ptr) issues its stores (called by thread 0 after
+// the proxy fence). Returns false when a bounded wait gave up.
+template <typename LoadF, typename ComputeF, typename StoreF>
+__device__ __forceinline__ void pipe_run(int ntiles, float2* stage0, int stage_elems, uint64_t* bars, uint32_t* status,
+                                         LoadF load, ComputeF compute, StoreF store) {
+  const int tid = threadIdx.x;
+  const int cnt = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (tid == 0) {
+    tma::mbar_init(&bars[0], 1);
+    tma::mbar_init(&bars[1], 1);
+    tma::fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0 && cnt > 0) {
+    const uint32_t bytes = load(blockIdx.x, stage0, &bars[0]);
+    (void)bytes;
+  }
+  for (int i = 0; i < cnt; i++) {
+    const int s = i & 1;
+    float2* st = stage0 + s * stage_elems;
+    const int tile = blockIdx.x + i * gridDim.x;
+    if (tid == 0 && i + 1 < cnt) {
+      tma::bulk_wait_read<0>();  // the other stage's store has finished reading it
+      load(tile + gridDim.x, stage0 + (s ^ 1) * stage_elems, &bars[s ^ 1]);
+    }
+    const bool ok = tma::mbar_wait(&bars[s], (uint32_t)((i >> 1) & 1), status);
+    if (__syncthreads_or(!ok)) {
+      // give up: wait (bounded) for the load already issued into the other stage
+      if (tid == 0 && i + 1 < cnt) tma::mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1), status);
+      break;
+    }
+    compute(tile, st);
+    tma::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      store(tile, st);
+      tma::bulk_commit();
+    }
+  }
+  if (tid == 0) tma::bulk_wait_all();
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(NT) k_ypass_pipe(const __grid_constant__ tma::TensorMap map, PipeYArgs a) {
+  using C = PipeCfg<N>;
+  constexpr int P = C::PY;
+  extern __shared__ __align__(128) float2 psm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  float2* tw = psm;
+  float2* stage0 = psm + N;  // N twiddles (16-byte multiple for N >= 2)
+  constexpr int SE = N * P;  // elements per stage
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+  const int ntiles = C::NBLKY * N * a.ncomp;
+  // tile -> (column block, z, component); coordinates of the 3-D map
+  // (x: floats of a row, y: row within the plane, z: component * N + plane z)
+  auto coords = [&](int t, int& x, int& zz) {
+    const int blk = t % C::NBLKY;
+    const int rest = t / C::NBLKY;  // component * N + z
+    x = blk * 2 * P;
+    zz = rest;
+  };
+  auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
+    int x, zz;
+    coords(t, x, zz);
+    tma::mbar_expect_tx(bar, SE * 8);
+    for (int b = 0; b < C::NBOX; b++) tma::load_3d(dst + b * C::BOX * P, &map, x, b * C::BOX, zz, bar);
+    return SE * 8;
+  };
+  auto compute = [&](int, float2* st) { fftk::fft<N, DIR, P, NT>(st, P, 1, tw, 1, tid); };
+  auto store = [&](int t, const float2* src) {
+    int x, zz;
+    coords(t, x, zz);
+    for (int b = 0; b < C::NBOX; b++) tma::store_3d(&map, x, b * C::BOX, zz, src + b * C::BOX * P);
+  };
+  pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
+}
+
+// Spectral operator of a z-pass at one point (kx = col, ky = y, kz = row) of a
+// tile with ntile components at stride T; see k_zpass for the formulas.
+template <int N, int MODE>
+__device__ __forceinline__ void zop(float2* tile, int T, int i, int col, int row, int y, const float* kv,
+                                    const float* kp, const PipeZArgs& a) {
+  const float kx = kv[col], ky = kv[y], kz = kv[row];
+  const bool nx = (col == N / 2), ny = (y == N / 2), nz = (row == N / 2);
+  const float kk = kx * kx + ky * ky + kz * kz;
+  const float A = kk > 0.f ? 1.0f / kk : 0.f;
+  const float kpx = kp[col], kpy = kp[y], kpz = kp[row];
+  if constexpr (MODE == Z_NEWTON) {
+    const float2 r = tile[i];
+    const float f = a.coef * A * a.norm;
+    const float2 ir = cmul_i<1>(r);
+    tile[i] = cscale(ir, f * kpx);
+    tile[T + i] = cscale(ir, f * kpy);
+    tile[2 * T + i] = cscale(ir, f * kpz);
+    if (a.nout == 4) tile[3 * T + i] = cscale(r, -f);
+  } else if constexpr (MODE == Z_SMOOTH) {
+    const int64_t kidx = ((int64_t)row * N + y) * (N / 2 + 1) + col;
+    const float f = a.khat[kidx] * a.norm;
+    for (int c = 0; c < 3; c++) tile[c * T + i] = cscale(tile[c * T + i], f);
+  } else {
+    const float2 gg[3] = {tile[i], tile[T + i], tile[2 * T + i]};
+    const float k3[3] = {kx, ky, kz};
+    const bool n3[3] = {nx, ny, nz};
+    if constexpr (MODE == Z_FINAL) {
+      float2 S = make_float2(0.f, 0.f);
+      for (int b = 0; b < 3; b++)
+        if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
+      const float2 aS = cscale(S, A * a.norm);
+      tile[i] = cscale(aS, kpx);
+      tile[T + i] = cscale(aS, kpy);
+      tile[2 * T + i] = cscale(aS, kpz);
+      if (a.nout == 4) tile[3 * T + i] = cmul_i<1>(aS);
+    } else {
+      for (int aa = 0; aa < 3; aa++) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int b = 0; b < 3; b++)
+          if (aa == b || n3[aa] == n3[b]) t = cadd(t, cscale(gg[b], k3[aa] * k3[b] * A));
+        const float2 o = (MODE == Z_DIV) ? csub(gg[aa], t) : t;
+        tile[aa * T + i] = cscale(o, a.norm);
+      }
+    }
+  }
+}
+
+// z-pass over the tile of (column block, y): forward z, the spectral
+// operator, inverse z. Each stage holds a vector region [z row][3][column]
+// (4-D maps with the component as a dimension, so one FFT call transforms the
+// three components) and, for Z_NEWTON and Z_FINAL, a scalar region
+// [z row][column] for rho^ (input) or phi^ (output, component 3 of A).
+// threads per pipelined z-pass CTA: the projections use 512 (all 3 P
+// sequences of a stage in one round); the modes with a scalar region stay at
+// 256 to keep their registers.
+template <int MODE>
+constexpr int zthreads() { return (MODE == Z_NEWTON || MODE == Z_FINAL) ? 256 : 512; }
+
+template <int N, int MODE, int NTZ = zthreads<MODE>()>
+__global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
+                                                   const __grid_constant__ tma::TensorMap out_map,
+                                                   const __grid_constant__ tma::TensorMap phi_map, PipeZArgs a) {
+  using C = PipeCfg<N>;
+  constexpr int P = C::PZ;
+  constexpr bool SCALAR = (MODE == Z_NEWTON || MODE == Z_FINAL);
+  constexpr int VP = 3 * P;                     // vector row pitch
+  constexpr int SE = N * VP + (SCALAR ? N * P : 0);
+  extern __shared__ __align__(128) float2 psm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  float2* tw = psm;
+  float* kv = reinterpret_cast<float*>(psm + N);
+  float* kp = kv + N;
+  float2* stage0 = psm + 2 * N;
+  const bool phi = SCALAR && a.nout > 3;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NTZ) {
+    tw[i] = a.tw[i];
+    kv[i] = a.kv[i];
+    kp[i] = a.kp[i];
+  }
+  const int ntiles = C::NBLKZ * N;
+  auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
+    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    if constexpr (MODE == Z_NEWTON) {
+      tma::mbar_expect_tx(bar, N * P * 8);
+      for (int b = 0; b < C::NBOX; b++)
+        tma::load_4d(dst + N * VP + b * C::BOX * P, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
+      return N * P * 8;
+    } else {
+      tma::mbar_expect_tx(bar, 3 * N * P * 8);
+      for (int b = 0; b < C::NBOX; b++) tma::load_4d(dst + b * C::BOX * VP, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
+      return 3 * N * P * 8;
+    }
+  };
+  auto compute = [&](int t, float2* st) {
+    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    float2* sv = st;            // vector region
+    float2* ss = st + N * VP;   // scalar region
+    if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(ss, P, 1, tw, 1, tid);
+    else fftk::fft<N, -1, 3 * P, NTZ>(sv, VP, 1, tw, 1, tid);
+    const float ky = kv[y], kpy = kp[y];
+    const bool ny = (y == N / 2);
+    for (int i = tid; i < N * P; i += NTZ) {
+      const int row = i / P, cc = i % P, col = blk * P + cc;
+      if (col > N / 2) continue;
+      float2* v = sv + row * VP + cc;  // component c at v[c * P]
+      float2* sc = ss + row * P + cc;
+      const float kx = kv[col], kz = kv[row];
+      const bool nx = (col == N / 2), nz = (row == N / 2);
+      const float kk = kx * kx + ky * ky + kz * kz;
+      const float A = kk > 0.f ? 1.0f / kk : 0.f;
+      if constexpr (MODE == Z_NEWTON) {
+        const float2 r = *sc;
+        const float f = a.coef * A * a.norm;  // 4 pi G A / N^3
+        const float2 ir = cmul_i<1>(r);
+        v[0] = cscale(ir, f * kp[col]);
+        v[P] = cscale(ir, f * kpy);
+        v[2 * P] = cscale(ir, f * kp[row]);
+        *sc = cscale(r, -f);  // phi_N^ = -4 pi G A rho^
+      } else if constexpr (MODE == Z_SMOOTH) {
+        const float f = a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] * a.norm;
+        for (int c = 0; c < 3; c++) v[c * P] = cscale(v[c * P], f);
+      } else {
+        const float2 gg[3] = {v[0], v[P], v[2 * P]};
+        const float k3[3] = {kx, ky, kz};
+        const bool n3[3] = {nx, ny, nz};
+        if constexpr (MODE == Z_FINAL) {
+          // phi^ = i A sum_b k'_b g_b (k'_b = 0 on b's Nyquist plane); a^ = -i kappa phi^
+          float2 S = make_float2(0.f, 0.f);
+          for (int b = 0; b < 3; b++)
+            if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
+          const float2 aS = cscale(S, A * a.norm);
+          v[0] = cscale(aS, kp[col]);
+          v[P] = cscale(aS, kpy);
+          v[2 * P] = cscale(aS, kp[row]);
+          *sc = cmul_i<1>(aS);
+        } else {
+          // P_ab = k_a k_b A, off-diagonal terms dropped when exactly one of a, b is on its Nyquist plane
+          for (int aa = 0; aa < 3; aa++) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int b = 0; b < 3; b++)
+              if (aa == b || n3[aa] == n3[b]) acc = cadd(acc, cscale(gg[b], k3[aa] * k3[b] * A));
+            v[aa * P] = cscale((MODE == Z_DIV) ? csub(gg[aa], acc) : acc, a.norm);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    fftk::fft<N, +1, 3 * P, NTZ>(sv, VP, 1, tw, 1, tid);
+    if (phi) fftk::fft<N, +1, P, NTZ>(ss, P, 1, tw, 1, tid);
+  };
+  auto store = [&](int t, const float2* src) {
+    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    const tma::TensorMap* m = SCALAR ? &out_map : &in_map;
+    for (int b = 0; b < C::NBOX; b++) tma::store_4d(m, blk * 2 * P, 0, y, b * C::BOX, src + b * C::BOX * VP);
+    if (phi)
+      for (int b = 0; b < C::NBOX; b++)
+        tma::store_4d(&phi_map, blk * 2 * P, 3, y, b * C::BOX, src + N * VP + b * C::BOX * P);
+  };
+  pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
+}
+
+}  // namespace passes

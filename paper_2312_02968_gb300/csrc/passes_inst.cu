@@ -72,6 +72,62 @@ cudaError_t CAT(mond_ypass_, MOND_N)(int dir, const passes::YArgs& a, int ncomp,
   return cudaGetLastError();
 }
 
+namespace {
+template <typename K>
+int pipe_grid(K kern, size_t sm, int nt = NT) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nt, sm);
+  return sms * (per > 0 ? per : 1);
+}
+
+template <int DIR>
+cudaError_t launch_ypipe(const tma::TensorMap& map, const PipeYArgs& a, cudaStream_t st) {
+  size_t sm = sizeof(float2) * (N + 2 * (size_t)N * PipeCfg<N>::PY);
+  cudaError_t e = set_smem(k_ypass_pipe<N, DIR>, sm);
+  if (e != cudaSuccess) return e;
+  static int grid = 0;
+  if (!grid) grid = pipe_grid(k_ypass_pipe<N, DIR>, sm);
+  const int ntiles = PipeCfg<N>::NBLKY * N * a.ncomp;
+  k_ypass_pipe<N, DIR><<<grid < ntiles ? grid : ntiles, NT, sm, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_zpipe(const tma::TensorMap& in, const tma::TensorMap& out, const tma::TensorMap& phi,
+                         const PipeZArgs& a, cudaStream_t st) {
+  constexpr bool SCALAR = (MODE == Z_NEWTON || MODE == Z_FINAL);
+  const size_t stage = (size_t)N * PipeCfg<N>::PZ * (SCALAR ? 4 : 3);
+  const size_t sm = sizeof(float2) * (2 * N + 2 * stage);
+  cudaError_t e = set_smem(k_zpass_pipe<N, MODE>, sm);
+  if (e != cudaSuccess) return e;
+  static int grid = 0;
+  constexpr int nt = zthreads<MODE>();
+  if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE>, sm, nt);
+  const int ntiles = PipeCfg<N>::NBLKZ * N;
+  k_zpass_pipe<N, MODE><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t CAT(mond_ypass_pipe_, MOND_N)(int dir, const tma::TensorMap& map, const passes::PipeYArgs& a,
+                                          cudaStream_t st) {
+  return dir < 0 ? launch_ypipe<-1>(map, a, st) : launch_ypipe<+1>(map, a, st);
+}
+
+cudaError_t CAT(mond_zpass_pipe_, MOND_N)(int mode, const tma::TensorMap& in, const tma::TensorMap& out,
+                                          const tma::TensorMap& phi, const passes::PipeZArgs& a, cudaStream_t st) {
+  switch (mode) {
+    case Z_NEWTON: return launch_zpipe<Z_NEWTON>(in, out, phi, a, st);
+    case Z_CURL: return launch_zpipe<Z_CURL>(in, out, phi, a, st);
+    case Z_DIV: return launch_zpipe<Z_DIV>(in, out, phi, a, st);
+    case Z_FINAL: return launch_zpipe<Z_FINAL>(in, out, phi, a, st);
+    case Z_SMOOTH: return launch_zpipe<Z_SMOOTH>(in, out, phi, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t CAT(mond_zpass_, MOND_N)(int mode, const passes::ZArgs& a, cudaStream_t st) {
   switch (mode) {
     case Z_NEWTON: return launch_z<Z_NEWTON>(a, st);

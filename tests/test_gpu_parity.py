@@ -276,3 +276,28 @@ def test_track_dh(B):
     dh = np.array(d["dH"][:4])
     assert np.all(np.isfinite(dh)) and dh[1] < dh[0]
     assert np.isnan(d["dH"][4])
+
+
+@pytest.mark.parametrize("n,mu,K", [(32, 0, 0), (32, 0, 4), (48, 2, 3), (64, 1, 2)])
+def test_pipelined_passes_match_unpipelined(B, n, mu, K):
+    """The TMA-pipelined y/z passes do the same arithmetic per element as the
+    one-tile-per-CTA passes; only the compiler's fused multiply-add choices
+    differ. Fields agree to FP32 rounding; H, a difference field, carries
+    that rounding amplified, so the bar is the parity bar of 1e-5."""
+    p = W.isothermal(n, 1.0, 3000, n / 10, 0.4 * n, seed=n + 7)
+    out = []
+    for pipe in (0, 1):
+        h, _ = make(B, n, 1, p, 1.5, mu=mu, a0=0.05 if mu else 1.0)
+        h.set_option(B.OPT_PIPELINED, pipe)
+        h.set_option(B.OPT_KEEP_PHI, 1)
+        h.deposit()
+        h.solve_field(K)
+        f = [h.get_field(B.FIELD_ACC).cpu(), h.get_field(B.FIELD_PHI).cpu(), h.get_field(B.FIELD_GN).cpu()]
+        if K > 0:
+            g = torch.from_numpy((1e-3 * np.random.default_rng(1).standard_normal((3, n, n, n))).astype(np.float32))
+            h.solve_field(1, B.WARM_GUESS, g.cuda())
+            h.smooth()
+            f += [h.get_field(B.FIELD_ACC).cpu(), h.get_field(B.FIELD_H).cpu(), h.get_field(B.FIELD_SMOOTH).cpu()]
+        out.append(f)
+    for a, b in zip(out[0], out[1]):
+        assert rel(a.numpy(), b.numpy()) < TOL
