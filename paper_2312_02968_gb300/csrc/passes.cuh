@@ -674,11 +674,10 @@ __device__ __forceinline__ void zop(float2* tile, int T, int i, int col, int row
 // (4-D maps with the component as a dimension, so one FFT call transforms the
 // three components) and, for Z_NEWTON and Z_FINAL, a scalar region
 // [z row][column] for rho^ (input) or phi^ (output, component 3 of A).
-// threads per pipelined z-pass CTA: the projections use 512 (all 3 P
-// sequences of a stage in one round); the modes with a scalar region stay at
-// 256 to keep their registers.
+// threads per pipelined z-pass CTA: 384 = one radix-16 butterfly per thread
+// for the 3 x 8 sequences of a 256-point tile, so no thread holds two.
 template <int MODE>
-constexpr int zthreads() { return (MODE == Z_NEWTON || MODE == Z_FINAL) ? 256 : 512; }
+constexpr int zthreads() { return 384; }
 
 template <int N, int MODE, int NTZ = zthreads<MODE>()>
 __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
