@@ -148,6 +148,11 @@ int mond_pm_bind_particles(mond_pm_t h, int64_t N, int32_t* cell, float* offset,
  * particles by 8^3 mesh tile for the gather. */
 int mond_pm_deposit(mond_pm_t h);
 
+/* Use a mesh density instead of a deposit for the next solves: rho (device
+ * float32, n_f^3, mass per s^3) is copied in; the next mond_pm_deposit
+ * replaces it. Particle calls (gather, push) need a deposit. */
+int mond_pm_set_density(mond_pm_t h, const float* rho);
+
 /* Field solve (Sect. 2.1 iteration; App. Flow steps 3-9) on the last
  * deposit: Newtonian field, then n_iter iterations of
  * F = g_N + H, g_M = nu(|F|/a0) F, curl-free projection, F = mu(|g_M|/a0) g_M,
@@ -199,6 +204,13 @@ int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out);
 /* Copy a mesh field (MOND_FIELD_*) into dst (device float32, compact n_f^3
  * per plane). Synchronises and returns any latched device error. */
 int mond_pm_get_field(mond_pm_t h, int which, float* dst);
+
+/* Device address of the handle's own buffer of MOND_FIELD_GN, MOND_FIELD_H or
+ * MOND_FIELD_ACC (3 compact planes, float32, owned by the handle), for
+ * kernels that read a field on the handle's stream without a copy: the
+ * contents are those of the last call that wrote the field, in stream order.
+ * Does not synchronise. Other fields: MOND_EINVAL. */
+int mond_pm_field_ptr(mond_pm_t h, int which, const float** out);
 
 /* Copy the raw int64 deposit accumulator of the last deposit (n_f^3 words)
  * into dst (device) and report Kacc (units are 2^-Kacc mass). Synchronises. */

@@ -48,6 +48,7 @@ SIGNATURES = {
     "mond_pm_set_option": (_I, [_P, _I, _I64]),
     "mond_pm_bind_particles": (_I, [_P, _I64, _P, _P, _P, _P]),
     "mond_pm_deposit": (_I, [_P]),
+    "mond_pm_set_density": (_I, [_P, _P]),
     "mond_pm_solve_field": (_I, [_P, _I, _I, _P]),
     "mond_pm_smooth": (_I, [_P, _P]),
     "mond_pm_gather_push": (_I, [_P, _D]),
@@ -57,6 +58,7 @@ SIGNATURES = {
     "mond_pm_step_host": (_I, [_P, _D, _I, _I, _P, _P, _P]),
     "mond_pm_diagnostics": (_I, [_P, ctypes.POINTER(Diag)]),
     "mond_pm_get_field": (_I, [_P, _I, _P]),
+    "mond_pm_field_ptr": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "mond_pm_get_deposit_acc": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "mond_pm_sync": (_I, [_P]),
     "mond_pm_last_error": (ctypes.c_char_p, [_P]),
@@ -64,6 +66,28 @@ SIGNATURES = {
     "mond_pm_kernel_stats": (_I, [_P, ctypes.POINTER(KStat), _I, ctypes.POINTER(_I)]),
     "mond_pm_deposit_noalloc": (_I, [ctypes.c_int32, _D, _D, _I64, _P, _P, _P, _P, _P]),
 }
+
+
+class FnoShape(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("width", ctypes.c_int32), ("modes", ctypes.c_int32),
+                ("layers", ctypes.c_int32)]
+
+
+_F = ctypes.c_float
+SIGNATURES.update({
+    "mond_fno_param_count": (_I, [FnoShape, ctypes.POINTER(_I64)]),
+    "mond_fno_workspace_bytes": (_I, [FnoShape, ctypes.POINTER(ctypes.c_size_t)]),
+    "mond_fno_init": (_I, [FnoShape, ctypes.c_uint64, _P, _P]),
+    "mond_fno_cast": (_I, [FnoShape, _P, _P, _P]),
+    "mond_fno_forward": (_I, [FnoShape, _P, _P, _P, _P, _P]),
+    "mond_fno_backward": (_I, [FnoShape, _P, _P, _P, _P, _P, _P]),
+    "mond_fno_loss": (_I, [_I64, _P, _P, _P, _F, _P, _P]),
+    "mond_fno_adam": (_I, [_I64, _P, _P, _P, _P, _F, _F, _F, _F, _I, _P]),
+    "mond_fno_input": (_I, [_I, _I, _F, _P, _P, _P, _P]),
+    "mond_fno_output": (_I, [_I, _I, _P, _P, _P, _P]),
+    "mond_fno_coarsen": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
+    "mond_fno_mixture_density": (_I, [_I, _D, _I, _P, _P, _P, _P, _F, _P, _P]),
+})
 
 _lib = None
 
@@ -177,6 +201,10 @@ class MondPM:
     def deposit(self):
         self._check(lib().mond_pm_deposit(self.h))
 
+    def set_density(self, rho):
+        """Mesh density (device float32 [n_f, n_f, n_f]) for the next solves."""
+        self._check(lib().mond_pm_set_density(self.h, _ptr(rho)))
+
     def solve_field(self, n_iter: int = 4, warm: int = WARM_NONE, H_guess=None):
         self._check(lib().mond_pm_solve_field(self.h, int(n_iter), int(warm), _ptr(H_guess)))
 
@@ -220,6 +248,12 @@ class MondPM:
             out = torch.empty(shape, dtype=torch.float32, device=self.device)
         self._check(lib().mond_pm_get_field(self.h, int(which), _ptr(out)))
         return out
+
+    def field_ptr(self, which: int) -> int:
+        """Device address of the handle's GN, H or ACC buffer (no copy, no sync)."""
+        p = _P()
+        self._check(lib().mond_pm_field_ptr(self.h, int(which), ctypes.byref(p)))
+        return int(p.value)
 
     def get_deposit_acc(self):
         torch = self.torch

@@ -33,8 +33,9 @@ def _sources_digest() -> str:
         with open(os.path.join(SRC, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
-    with open(os.path.join(HERE, "..", "include", "mond_pm.h"), "rb") as f:
-        h.update(f.read())
+    for hdr in ("mond_pm.h", "mond_fno.h"):
+        with open(os.path.join(HERE, "..", "include", hdr), "rb") as f:
+            h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
 
@@ -49,7 +50,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = [([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "mond_pm_api.cu"), "-o", os.path.join(OUT, "api.o")],
              os.path.join(OUT, "api.o")),
             ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "deposit_noalloc.cu"), "-o",
-                                      os.path.join(OUT, "deposit_noalloc.o")], os.path.join(OUT, "deposit_noalloc.o"))]
+                                      os.path.join(OUT, "deposit_noalloc.o")], os.path.join(OUT, "deposit_noalloc.o")),
+            ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "fno.cu"), "-o", os.path.join(OUT, "fno.o")],
+             os.path.join(OUT, "fno.o"))]
     for n in SIZES:
         o = os.path.join(OUT, f"passes_{n}.o")
         jobs.append(([nvcc] + ARCH + FLAGS + [f"-DMOND_N={n}", "-c", os.path.join(SRC, "passes_inst.cu"), "-o", o], o))

@@ -236,7 +236,7 @@ struct mond_pm {
   float* vel = nullptr;
   const float* mass = nullptr;
   int kacc = 0;
-  bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false;
+  bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false, density_given = false;
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   // TMA views of the spectral buffers: y-pass tiles (3-D), z-pass tiles with
   // the component as a dimension (4-D; W with 1 or 3 components per box, A
@@ -557,6 +557,7 @@ int do_deposit(mond_pm* h) {
   CK(cudaGetLastError());
   h->have_dep = true;
   h->have_solve = false;
+  h->density_given = false;
   return MOND_OK;
 }
 
@@ -611,7 +612,16 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   x.dep = h->w.dep;
   x.rho_out = h->w.rho;
   x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
-  PK(xpass(h, passes::X_RHO, x));
+  if (h->density_given) {
+    // density set by mond_pm_set_density: forward x-transform of the FP32 plane
+    passes::XArgs xf{};
+    xf.ncomp = 1;
+    xf.spec = W;
+    xf.real_in = h->w.rho;
+    PK(xpass(h, passes::X_FWD, xf));
+  } else {
+    PK(xpass(h, passes::X_RHO, x));
+  }
   PK(ypass(h, -1, W, 1));
   if (K == 0) {
     PK(zpass(h, passes::Z_NEWTON, W, A, nout));
@@ -889,6 +899,15 @@ int mond_pm_deposit(mond_pm_t h) {
   return do_deposit(h);
 }
 
+int mond_pm_set_density(mond_pm_t h, const float* rho) {
+  if (!h || !rho) return MOND_EINVAL;
+  CK(cudaMemcpyAsync(h->w.rho, rho, sizeof(float) * h->n3, cudaMemcpyDeviceToDevice, h->st));
+  h->density_given = true;
+  h->have_dep = true;
+  h->have_solve = false;
+  return MOND_OK;
+}
+
 int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess) {
   if (!h) return MOND_EINVAL;
   if (!h->have_dep) return fail(h, MOND_ESTATE, "solve_field before deposit");
@@ -1047,6 +1066,17 @@ int mond_pm_get_field(mond_pm_t h, int which, float* dst) {
   }
   CK(cudaMemcpyAsync(dst, src, sizeof(float) * planes * h->n3, cudaMemcpyDeviceToDevice, h->st));
   return read_status(h);
+}
+
+int mond_pm_field_ptr(mond_pm_t h, int which, const float** out) {
+  if (!h || !out) return MOND_EINVAL;
+  switch (which) {
+    case MOND_FIELD_GN: *out = h->w.gN; break;
+    case MOND_FIELD_H: *out = h->w.Hs; break;
+    case MOND_FIELD_ACC: *out = h->w.acc; break;
+    default: return fail(h, MOND_EINVAL, "field %d has no stable device buffer", which);
+  }
+  return MOND_OK;
 }
 
 int mond_pm_get_deposit_acc(mond_pm_t h, uint64_t* dst, int32_t* kacc) {

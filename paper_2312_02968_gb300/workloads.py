@@ -110,23 +110,36 @@ def isothermal(n_f: int, s: float, N: int, b_px: float, r_max_px: float, seed: i
     return _pack(pos, vel, mass, n_f)
 
 
-def sphere_mixture(n_f: int, N: int, seed: int, n_spheres=None):
-    """Mixture of 1-8 Plummer or Hernquist spheres: masses log-uniform over
-    [1e-2, 1], scale radii uniform over [4, 32] px, centres keeping three scale
-    radii inside the central 0.8 of the box, radii truncated at 0.4 box.
-    Particles are allotted in proportion to mass; velocities zero."""
+def mixture_spheres(n_f: int, seed: int, n_spheres=None):
+    """Parameters of a mixture of 1-8 Plummer (kind 0) or Hernquist (kind 1)
+    spheres: masses log-uniform over [1e-2, 1], scale radii uniform over
+    [4, 32] px, centres (pixels from the domain centre) keeping three scale
+    radii inside the central 0.8 of the box."""
     rng = np.random.default_rng(seed)
     K = int(rng.integers(1, 9)) if n_spheres is None else int(n_spheres)
-    kinds = rng.integers(0, 2, K)
+    kinds = rng.integers(0, 2, K).astype(np.int32)
     masses = np.exp(rng.uniform(math.log(1e-2), math.log(1.0), K))
     radii = rng.uniform(4.0, 32.0, K)
+    centres = np.zeros((K, 3))
+    for j in range(K):
+        lim = max(0.0, 0.4 * n_f - 3 * radii[j])
+        centres[j] = rng.uniform(-lim, lim, 3)
+    return {"K": K, "kind": kinds, "mass": masses, "radius": radii, "centre": centres}
+
+
+def sphere_mixture(n_f: int, N: int, seed: int, n_spheres=None):
+    """N equal-mass particles drawn from mixture_spheres(n_f, seed): particles
+    allotted in proportion to mass, radii truncated at 0.4 box (textbook
+    inverse cumulative mass profiles); velocities zero."""
+    sp = mixture_spheres(n_f, seed, n_spheres)
+    rng = np.random.default_rng([seed, 1])
+    K, kinds, masses, radii = sp["K"], sp["kind"], sp["mass"], sp["radius"]
     counts = np.floor(N * masses / masses.sum()).astype(np.int64)
     counts[0] += N - counts.sum()
     rmax = 0.4 * n_f
     parts = []
     for j in range(K):
-        lim = max(0.0, 0.4 * n_f - 3 * radii[j])
-        centre = rng.uniform(-lim, lim, 3)
+        centre = sp["centre"][j]
         got = np.zeros((0, 3))
         while got.shape[0] < counts[j]:
             k = int((counts[j] - got.shape[0]) * 1.2) + 16
@@ -146,7 +159,7 @@ def sphere_mixture(n_f: int, N: int, seed: int, n_spheres=None):
     pos = np.concatenate(parts)
     mass = np.full(N, masses.sum() / N)
     vel = np.zeros((N, 3))
-    return _pack(pos, vel, mass, n_f), {"K": K, "kinds": kinds, "masses": masses, "radii": radii}
+    return _pack(pos, vel, mass, n_f), sp
 
 
 def isothermal_density_mesh(n_f: int, s: float, b: float, M: float = 1.0):

@@ -1,5 +1,5 @@
 """The C-ABI library loads without a GPU and exports every symbol that
-include/mond_pm.h declares; host-only entry points answer without a device."""
+include/*.h declares; host-only entry points answer without a device."""
 import ctypes
 import os
 import re
@@ -7,13 +7,16 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "mond_pm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("mond_pm.h", "mond_fno.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mond_pm_\w+)\s*\(", text)))
+    names = set()
+    for hdr in HEADERS:
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(mond_(?:pm|fno)_\w+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
