@@ -29,8 +29,8 @@ extern "C" {
 #endif
 
 typedef struct {
-  int32_t n;       /* coarse grid side (8..128, a multiple of 4, 2M <= n) */
-  int32_t width;   /* channels C (<= 32) */
+  int32_t n;       /* coarse grid side (8..64, a multiple of 4, 2M <= n) */
+  int32_t width;   /* channels C (even, 2..32) */
   int32_t modes;   /* modes per axis M */
   int32_t layers;  /* Fourier layers L */
 } mond_fno_shape;
@@ -80,7 +80,8 @@ int mond_fno_adam(int64_t count, float* params, float* grad, float* m, float* v,
 int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* scale_out, void* stream);
 
 /* Fine field from a coarse network output: H [3][N^3] = s * trilinear
- * upsampling (periodic, cell centred) of y [3][n^3]; s read from scale. */
+ * upsampling (periodic, cell centred) of y [3][n^3]; s read from scale.
+ * N must be a multiple of n and of 16. */
 int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* stream);
 
 /* Means of f^3 blocks of a fine field: fine [ncomp][N^3] -> coarse

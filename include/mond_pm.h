@@ -52,8 +52,9 @@ typedef struct {
 enum { MOND_MU_DEEP = 0, MOND_MU_SIMPLE = 1, MOND_MU_STANDARD = 2, MOND_MU_NEWTON = 3 };
 
 /* Initial H of the iteration: zero (App. Flow step 7), the H of the previous
- * solve (Sect. 5.2 item iv), or a caller-supplied guess. */
-enum { MOND_WARM_NONE = 0, MOND_WARM_PREV = 1, MOND_WARM_GUESS = 2 };
+ * solve (Sect. 5.2 item iv), a caller-supplied guess projected onto its
+ * divergence-free part, or a caller-supplied guess used as given. */
+enum { MOND_WARM_NONE = 0, MOND_WARM_PREV = 1, MOND_WARM_GUESS = 2, MOND_WARM_GUESS_RAW = 3 };
 
 /* Mesh fields readable with mond_pm_get_field. */
 enum {
@@ -159,10 +160,14 @@ int mond_pm_set_density(mond_pm_t h, const float* rho);
  * H = F - g_N, divergence-free projection; the last iteration stops after the
  * curl-free projection and the acceleration mesh a = -grad_FD phi is formed.
  * n_iter = 0 gives the Newtonian solve (a = g_N). warm: MOND_WARM_NONE
- * (H = 0), MOND_WARM_PREV (H of the previous solve) or MOND_WARM_GUESS
+ * (H = 0), MOND_WARM_PREV (H of the previous solve), MOND_WARM_GUESS
  * (H_guess: device float32, 3 planes; it is projected onto its
- * divergence-free part first). With PREV or GUESS the last iteration also
- * completes the H update so the next solve can start from it. 0 <= n_iter <= 64. */
+ * divergence-free part first) or MOND_WARM_GUESS_RAW (H_guess used as
+ * given). With a warm start the last iteration also completes the H update
+ * so the next solve can start from it. The Newtonian field is computed once
+ * per density: a solve on the density of the previous solve (no deposit or
+ * mond_pm_set_density in between) starts from the stored g_N.
+ * 0 <= n_iter <= 64. */
 int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess);
 
 /* Node-smoothed acceleration: the periodic discrete convolution of the

@@ -36,7 +36,8 @@ struct Shape {
 };
 
 bool make_shape(const mond_fno_shape& s, Shape* o) {
-  if (s.n < 8 || s.n > 128 || s.n % 4 || s.width < 1 || s.width > 32 || s.modes < 1 || 2 * s.modes > s.n ||
+  if (s.n < 8 || s.n > 64 || s.n % 4 || s.width < 2 || s.width > 32 || s.width % 2 || s.modes < 1 ||
+      2 * s.modes > s.n ||
       s.layers < 1 || s.layers > 8)
     return false;
   o->n = s.n;
@@ -48,18 +49,35 @@ bool make_shape(const mond_fno_shape& s, Shape* o) {
   return true;
 }
 
+// Tables of the truncated transforms, rebuilt by every forward/backward call:
+//   fx  [n][SXF]   x-forward: (cos, -sin)(2 pi kx x/n) for kx < M, zero padded
+//   ix  [2M][SXI]  x-inverse, weight a(kx)/V: rows (cos, -sin)(2 pi kx x/n)
+//   ixa [2M][SXI]  the same with weight 1 (adjoint of the x-forward)
+//   tf  [2M][n]    forward along y or z: e^{-2 pi i f(p) q / n}
+//   ti  [n][2M]    inverse along y or z: e^{+2 pi i f(q) p / n}
+// SXF = 16 ceil(M/8) and SXI = 16 ceil(n/16) floats (zero beyond the data).
+struct Tabs {
+  float* fx;
+  float* ix;
+  float* ixa;
+  float2* tf;
+  float2* ti;
+};
+__host__ __device__ inline int sxf(int M) { return 16 * ((M + 7) / 8); }
+__host__ __device__ inline int sxi(int n) { return 16 * ((n + 15) / 16); }
+
 // Workspace layout for one sample.
 struct Work {
   float* v;      // (L+1) x C x V activations (v_0 .. v_L)
   float* z;      // L x C x V pre-activations
   float2* shat;  // L x C x K truncated spectra of v_l
-  float2* a;     // C x n x n x M  (x-transformed)
-  float2* b;     // C x n x 2M x M (y-transformed)
+  float2* b;     // C x n x 2M x M (x- and y-transformed planes)
   float2* c;     // C x K          (z-transformed / mixed)
   float2* d;     // C x K
   float* dv;     // C x V
   float* dv2;    // C x V
   float* dz;     // C x V
+  Tabs tab;      // transform tables
 };
 
 size_t carve(const Shape& s, char* base, Work* w) {
@@ -74,13 +92,17 @@ size_t carve(const Shape& s, char* base, Work* w) {
   t.v = (float*)take(sizeof(float) * CV * (s.L + 1));
   t.z = (float*)take(sizeof(float) * CV * s.L);
   t.shat = (float2*)take(sizeof(float2) * (size_t)s.C * s.K * s.L);
-  t.a = (float2*)take(sizeof(float2) * (size_t)s.C * s.n * s.n * s.M);
   t.b = (float2*)take(sizeof(float2) * (size_t)s.C * s.n * 2 * s.M * s.M);
   t.c = (float2*)take(sizeof(float2) * (size_t)s.C * s.K);
   t.d = (float2*)take(sizeof(float2) * (size_t)s.C * s.K);
   t.dv = (float*)take(sizeof(float) * CV);
   t.dv2 = (float*)take(sizeof(float) * CV);
   t.dz = (float*)take(sizeof(float) * CV);
+  t.tab.fx = (float*)take(sizeof(float) * s.n * 64);
+  t.tab.ix = (float*)take(sizeof(float) * 2 * s.M * 64);
+  t.tab.ixa = (float*)take(sizeof(float) * 2 * s.M * 64);
+  t.tab.tf = (float2*)take(sizeof(float2) * 2 * s.M * s.n);
+  t.tab.ti = (float2*)take(sizeof(float2) * 2 * s.M * s.n);
   if (w) *w = t;
   return off;
 }
@@ -98,25 +120,37 @@ __device__ __forceinline__ float2 cis(int64_t m, int n, float sign) {
 }
 __device__ __forceinline__ int sfreq(int i, int M) { return i < M ? i : i - 2 * M; }
 
-// out[o][v] (+)= sum_i W[o][i] in[i][v] (+ b[o]); transpose uses W[i][o].
-__global__ void k_pw(const float* in, int Cin, const uint16_t* W, const uint16_t* b, int Cout, float* out, int64_t V,
-                     int accumulate, int transpose) {
-  __shared__ float sW[32 * 32];
+// out[o][v] = sum_i W[o][i] in[i][v] (+ b[o]); transpose uses W[i][o].
+// CMAX >= Cin: the input channels sit in registers, the weights in shared
+// memory zero-padded to CMAX columns.
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_pw(const float* __restrict__ in, int Cin, const uint16_t* __restrict__ W,
+                                            const uint16_t* __restrict__ b, int Cout, float* __restrict__ out,
+                                            int64_t V, int transpose) {
+  __shared__ __align__(16) float sW[32 * CMAX];
   __shared__ float sb[32];
-  for (int i = threadIdx.x; i < Cin * Cout; i += blockDim.x) {
-    const int o = i / Cin, j = i % Cin;
-    sW[i] = transpose ? bf(W, (int64_t)j * Cout + o) : bf(W, i);
+  for (int e = threadIdx.x; e < Cout * CMAX; e += blockDim.x) {
+    const int o = e / CMAX, i = e % CMAX;
+    sW[e] = i < Cin ? (transpose ? bf(W, (int64_t)i * Cout + o) : bf(W, (int64_t)o * Cin + i)) : 0.f;
   }
   for (int o = threadIdx.x; o < Cout; o += blockDim.x) sb[o] = b ? bf(b, o) : 0.f;
   __syncthreads();
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-    float x[32];
-    for (int i = 0; i < Cin; i++) x[i] = in[i * V + v];
+    float x[CMAX];
+#pragma unroll
+    for (int i = 0; i < CMAX; i++) x[i] = i < Cin ? in[i * V + v] : 0.f;
     for (int o = 0; o < Cout; o++) {
       float acc = sb[o];
-      for (int i = 0; i < Cin; i++) acc = fmaf(sW[o * Cin + i], x[i], acc);
-      if (accumulate) out[o * V + v] += acc;
-      else out[o * V + v] = acc;
+      const float4* w4 = reinterpret_cast<const float4*>(sW + o * CMAX);
+#pragma unroll
+      for (int i = 0; i < CMAX / 4; i++) {
+        const float4 w = w4[i];
+        acc = fmaf(w.x, x[4 * i], acc);
+        acc = fmaf(w.y, x[4 * i + 1], acc);
+        acc = fmaf(w.z, x[4 * i + 2], acc);
+        acc = fmaf(w.w, x[4 * i + 3], acc);
+      }
+      out[o * V + v] = acc;
     }
   }
 }
@@ -124,7 +158,7 @@ __global__ void k_pw(const float* in, int Cin, const uint16_t* W, const uint16_t
 // dW[o][i] += sum_v dout[o][v] in[i][v]; db[o] += sum_v dout[o][v].
 __global__ void k_wgrad(const float* dout, int Cout, const float* in, int Cin, int64_t V, float* dW, float* db) {
   constexpr int CH = 64;
-  __shared__ float so[32][CH], si[32][CH];
+  __shared__ float so[32][CH + 1], si[32][CH + 1];  // padded: conflict-free column reads
   const int npair = Cout * Cin + (db ? Cout : 0);
   float acc[5] = {0, 0, 0, 0, 0};
   for (int64_t v0 = (int64_t)blockIdx.x * CH; v0 < V; v0 += (int64_t)gridDim.x * CH) {
@@ -159,146 +193,6 @@ __global__ void k_wgrad(const float* dout, int Cout, const float* in, int Cin, i
   }
 }
 
-// Twiddle table e^{-2 pi i m / n}, m in [0, n), in shared memory (n <= 128);
-// e^{+...} is its conjugate. Every thread of the block must call it.
-__device__ __forceinline__ void load_twiddles(float2* tw, int n) {
-  for (int m = threadIdx.x; m < n; m += blockDim.x) tw[m] = cis(m, n, -1.f);
-  __syncthreads();
-}
-
-// Truncated forward DFT along x of real lines: out[line][kx] = sum_x in[line][x] e^{-2 pi i kx x/n}.
-__global__ void k_dft_x(const float* in, float2* out, int64_t nlines, int n, int M) {
-  __shared__ float2 tw[128];
-  load_twiddles(tw, n);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nlines * M) return;
-  const int64_t line = t / M;
-  const int kx = (int)(t % M);
-  const float* p = in + line * n;
-  float2 acc = make_float2(0.f, 0.f);
-  int m = 0;
-  for (int x = 0; x < n; x++) {
-    const float2 w = tw[m];
-    acc.x = fmaf(p[x], w.x, acc.x);
-    acc.y = fmaf(p[x], w.y, acc.y);
-    m += kx;
-    if (m >= n) m -= n;
-  }
-  out[t] = acc;
-}
-
-// Truncated DFT along an outer axis: in [B][len][inner] -> out [B][2M][inner]
-// with out[b][kp][i] = sum_m in[b][m][i] e^{-2 pi i f(kp) m / n}.
-__global__ void k_dft_outer(const float2* in, float2* out, int64_t B, int len, int inner, int M, int n) {
-  __shared__ float2 tw[128];
-  load_twiddles(tw, n);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tot = B * 2 * M * inner;
-  if (t >= tot) return;
-  const int i = (int)(t % inner);
-  const int kp = (int)((t / inner) % (2 * M));
-  const int64_t b = t / ((int64_t)inner * 2 * M);
-  const float2* p = in + b * len * inner + i;
-  const int f = (sfreq(kp, M) + n) % n;
-  float2 acc = make_float2(0.f, 0.f);
-  int e = 0;
-  for (int m = 0; m < len; m++) {
-    const float2 w = tw[e];
-    const float2 x = p[(int64_t)m * inner];
-    acc.x += x.x * w.x - x.y * w.y;
-    acc.y += x.x * w.y + x.y * w.x;
-    e += f;
-    if (e >= n) e -= n;
-  }
-  out[t] = acc;
-}
-
-// Inverse along an outer axis: in [B][2M][inner] -> out [B][n][inner],
-// out[b][m][i] = sum_kp in[b][kp][i] e^{+2 pi i f(kp) m / n}.
-__global__ void k_idft_outer(const float2* in, float2* out, int64_t B, int inner, int M, int n) {
-  __shared__ float2 tw[128];
-  load_twiddles(tw, n);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tot = B * n * inner;
-  if (t >= tot) return;
-  const int i = (int)(t % inner);
-  const int m = (int)((t / inner) % n);
-  const int64_t b = t / ((int64_t)inner * n);
-  const float2* p = in + b * 2 * M * inner + i;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int kp = 0; kp < 2 * M; kp++) {
-    const int e = (int)((((int64_t)sfreq(kp, M) * m) % n + n) % n);
-    const float2 w = make_float2(tw[e].x, -tw[e].y);
-    const float2 x = p[(int64_t)kp * inner];
-    acc.x += x.x * w.x - x.y * w.y;
-    acc.y += x.x * w.y + x.y * w.x;
-  }
-  out[t] = acc;
-}
-
-// Real lines from the kept x modes: out[line][x] (+)= scale sum_kx a(kx)
-// Re(in[line][kx] e^{+2 pi i kx x/n}), a(0) = 1, a(kx > 0) = a_pos.
-__global__ void k_idft_x(const float2* in, float* out, int64_t nlines, int n, int M, float a_pos, float scale,
-                         int accumulate) {
-  __shared__ float2 tw[128];
-  load_twiddles(tw, n);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nlines * n) return;
-  const int64_t line = t / n;
-  const int x = (int)(t % n);
-  const float2* p = in + line * M;
-  float acc = 0.f;
-  int e = 0;
-  for (int kx = 0; kx < M; kx++) {
-    const float2 v = p[kx];
-    // Re(v e^{+i th}) = v.x cos th - v.y sin th, with tw = (cos th, -sin th)
-    acc += (kx == 0 ? 1.f : a_pos) * (v.x * tw[e].x + v.y * tw[e].y);
-    e += x;
-    if (e >= n) e -= n;
-  }
-  acc *= scale;
-  if (accumulate) out[t] += acc;
-  else out[t] = acc;
-}
-
-// t[c][k] = sum_j R[k][j][c] s[j][k] (complex, bf16 weights).
-__global__ void k_mix_fwd(const float2* s, const uint16_t* R, float2* t, int C, int K) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (int64_t)K * C) return;
-  const int k = (int)(id / C), c = (int)(id % C);
-  float2 acc = make_float2(0.f, 0.f);
-  for (int j = 0; j < C; j++) {
-    const int64_t r = (((int64_t)k * C + j) * C + c) * 2;
-    const float2 w = make_float2(bf(R, r), bf(R, r + 1));
-    acc = make_float2(acc.x + w.x * s[(int64_t)j * K + k].x - w.y * s[(int64_t)j * K + k].y,
-                      acc.y + w.x * s[(int64_t)j * K + k].y + w.y * s[(int64_t)j * K + k].x);
-  }
-  t[(int64_t)c * K + k] = acc;
-}
-
-// Backward of the mixing with G_t scaled by a(kx)/V first:
-// gs[j][k] = sum_c conj(R[k][j][c]) g[c][k]; dR[k][j][c] += conj(s[j][k]) g[c][k].
-__global__ void k_mix_bwd(const float2* gt, const float2* s, const uint16_t* R, float2* gs, float* dR, int C, int K,
-                          int M, float invV) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (int64_t)K * C) return;
-  const int k = (int)(id / C), j = (int)(id % C);
-  const int kx = k % M;
-  const float a = (kx == 0 ? 1.f : 2.f) * invV;
-  const float2 sj = s[(int64_t)j * K + k];
-  float2 acc = make_float2(0.f, 0.f);
-  for (int c = 0; c < C; c++) {
-    const float2 g = make_float2(gt[(int64_t)c * K + k].x * a, gt[(int64_t)c * K + k].y * a);
-    const int64_t r = (((int64_t)k * C + j) * C + c) * 2;
-    const float2 w = make_float2(bf(R, r), bf(R, r + 1));
-    acc.x += w.x * g.x + w.y * g.y;  // conj(w) g
-    acc.y += w.x * g.y - w.y * g.x;
-    dR[r] += sj.x * g.x + sj.y * g.y;  // conj(s) g
-    dR[r + 1] += sj.x * g.y - sj.y * g.x;
-  }
-  gs[(int64_t)j * K + k] = acc;
-}
-
 __device__ __forceinline__ float gelu_t(float z, float* dgdz) {
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;
   const float u = k0 * (z + k1 * z * z * z);
@@ -307,10 +201,348 @@ __device__ __forceinline__ float gelu_t(float z, float* dgdz) {
   return 0.5f * z * (1.f + th);
 }
 
-__global__ void k_gelu(const float* z, float* v, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = gelu_t(z[i], nullptr);
+__global__ void k_tables(int n, int M, float invV, Tabs t) {
+  const int SXF = sxf(M), SXI = sxi(n);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * SXF; e += gridDim.x * blockDim.x) {
+    const int x = e / SXF, j = e % SXF, kx = j / 2;
+    float v = 0.f;
+    if (kx < M) {
+      const float2 w = cis((int64_t)kx * x, n, -1.f);
+      v = (j & 1) ? w.y : w.x;
+    }
+    t.fx[e] = v;
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * M * SXI; e += gridDim.x * blockDim.x) {
+    const int j = e / SXI, x = e % SXI, kx = j / 2;
+    float v = 0.f;
+    if (x < n) {
+      const float2 w = cis((int64_t)kx * x, n, -1.f);
+      v = (j & 1) ? w.y : w.x;
+    }
+    t.ixa[e] = v;
+    t.ix[e] = v * (kx == 0 ? 1.f : 2.f) * invV;
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * M * n; e += gridDim.x * blockDim.x) {
+    const int p = e / n, q = e % n;
+    t.tf[e] = cis((int64_t)sfreq(p, M) * q, n, -1.f);
+    const int pp = e / (2 * M), qq = e % (2 * M);
+    t.ti[e] = cis((int64_t)sfreq(qq, M) * pp, n, 1.f);
+  }
 }
+
+// Forward transform of (c, z) planes along x and y, fused, n <= 64, M <= 32:
+// the n x n real plane is staged in shared memory and transformed along x to
+// n x M complex, X[y][kx] = sum_x v[y][x] e^{-2 pi i kx x/n}, then along y,
+// out[p][kx] = sum_y e^{-2 pi i f(p) y/n} X[y][kx], p < 2M.
+// x: lane j owns output float j of a row (re/im of kx = j/2) and keeps its
+// table column in registers; the plane row is read as float4 broadcasts.
+// y: lane p owns an output row; X is read as broadcasts. Persistent CTAs
+// loop over planes, so the tables are read once per CTA.
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+size_t smem_xy_fwd(int n, int M) {
+  return sizeof(float) * ((size_t)n * n + (size_t)n * round4(2 * M) + (size_t)2 * M * M * 2) +
+         sizeof(float2) * (size_t)2 * M * (n + 1);
+}
+template <int NX>  // n <= NX
+__global__ void __launch_bounds__(256, 2) k_xy_fwd(const float* __restrict__ v, float2* __restrict__ out,
+                                                const float* __restrict__ fx, const float2* __restrict__ tf, int n,
+                                                int M, int64_t nplanes) {
+  extern __shared__ __align__(16) float smf[];
+  const int M2 = 2 * M, XS = round4(M2), SXF = sxf(M);
+  float* sP = smf;                                          // n * n
+  float* sX = sP + n * n;                                   // n * XS
+  float2* sO = reinterpret_cast<float2*>(sX + n * XS);      // M2 * M
+  float2* sY = sO + M2 * M;                                 // M2 * (n + 1)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float tx[NX];
+#pragma unroll
+  for (int x = 0; x < NX; x++) tx[x] = (x < n && lane < M2) ? fx[x * SXF + lane] : 0.f;
+  for (int e = tid; e < M2 * n; e += blockDim.x) sY[(e / n) * (n + 1) + e % n] = tf[e];
+  const int KPG = (M + 7) / 8;  // kx per warp in the y stage
+  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+    __syncthreads();
+    const float4* src = reinterpret_cast<const float4*>(v + plane * n * n);
+    float4* sP4 = reinterpret_cast<float4*>(sP);
+    {
+      // at most 4 float4 per thread (n <= 64): issue all loads, then store
+      float4 q[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int e = tid + k * 256;
+        if (e < n * n / 4) q[k] = src[e];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int e = tid + k * 256;
+        if (e < n * n / 4) sP4[e] = q[k];
+      }
+    }
+    __syncthreads();
+    for (int r = warp; r < n; r += 16) {
+      const int r2 = r + 8;
+      const float4* a0 = sP4 + r * (n / 4);
+      const float4* a1 = sP4 + (r2 < n ? r2 : r) * (n / 4);
+      float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < NX / 4; q++) {
+        if (4 * q < n) {
+          const float4 u = a0[q], w = a1[q];
+          acc0 = fmaf(u.x, tx[4 * q], fmaf(u.y, tx[4 * q + 1], fmaf(u.z, tx[4 * q + 2], fmaf(u.w, tx[4 * q + 3], acc0))));
+          acc1 = fmaf(w.x, tx[4 * q], fmaf(w.y, tx[4 * q + 1], fmaf(w.z, tx[4 * q + 2], fmaf(w.w, tx[4 * q + 3], acc1))));
+        }
+      }
+      if (lane < M2) {
+        sX[r * XS + lane] = acc0;
+        if (r2 < n) sX[r2 * XS + lane] = acc1;
+      }
+    }
+    __syncthreads();
+    if (lane < M2) {
+      const float2* t = sY + lane * (n + 1);
+      float2 acc[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) acc[k] = make_float2(0.f, 0.f);
+      for (int y = 0; y < n; y++) {
+        const float2 w = t[y];
+        const float* xr = sX + y * XS;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int kx = warp * KPG + k;
+          if (k < KPG && kx < M) {
+            const float a = xr[2 * kx], b = xr[2 * kx + 1];
+            acc[k].x = fmaf(w.x, a, fmaf(-w.y, b, acc[k].x));
+            acc[k].y = fmaf(w.x, b, fmaf(w.y, a, acc[k].y));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int kx = warp * KPG + k;
+        if (k < KPG && kx < M) sO[lane * M + kx] = acc[k];
+      }
+    }
+    __syncthreads();
+    float2* o = out + plane * M2 * M;
+    for (int e = tid; e < M2 * M; e += blockDim.x) o[e] = sO[e];
+  }
+}
+
+// Inverse of k_xy_fwd for planes, fused: in [2M][M] complex -> along y,
+// X[y][kx] = sum_p e^{+2 pi i f(p) y/n} in[p][kx], then along x to real,
+// z[y][x] += sum_j X_j[y] tab[j][x] over the 2M real parts (the table carries
+// a(kx)/V or 1), then v = gelu(z) (act 1), v = z (act 2) or nothing.
+// y: lane = y; x: thread = x with its table column in registers.
+size_t smem_xy_inv(int n, int M) {
+  return sizeof(float) * ((size_t)n * (round4(2 * M) + 4)) +
+         sizeof(float2) * ((size_t)n * (2 * M + 1) + (size_t)2 * M * M);
+}
+template <int NX, int MX>  // n <= NX, 2M <= MX
+__global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in, float* __restrict__ z,
+                                                float* __restrict__ v, const float* __restrict__ tab,
+                                                const float2* __restrict__ ti, int n, int M, int act,
+                                                int64_t nplanes) {
+  extern __shared__ __align__(16) float smf[];
+  const int M2 = 2 * M, XS = round4(M2) + 4, SXI = sxi(n);  // XS: 4-way write conflicts at most
+  float* sX = smf;                                          // n * XS
+  float2* sTi = reinterpret_cast<float2*>(sX + n * XS);     // n * (M2 + 1)
+  float2* sI = sTi + n * (M2 + 1);                          // M2 * M
+  const int tid = threadIdx.x;
+  const int xl = tid & 63, grp = tid >> 6;  // x stage: column x, row group (4 groups)
+  float tt[MX];
+#pragma unroll
+  for (int j = 0; j < MX; j++) tt[j] = (j < M2 && xl < n) ? tab[j * SXI + xl] : 0.f;
+  for (int e = tid; e < n * M2; e += blockDim.x) sTi[(e / M2) * (M2 + 1) + e % M2] = ti[e];
+  for (int e = tid; e < n * XS; e += blockDim.x) sX[e] = 0.f;  // the row padding is read (times 0) below
+  const int KPG = (M + 3) / 4;  // kx per group in the y stage
+  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+    __syncthreads();
+    const float2* ip = in + plane * M2 * M;
+    for (int e = tid; e < M2 * M; e += blockDim.x) sI[e] = ip[e];
+    __syncthreads();
+    if (xl < n) {
+      const float2* t = sTi + xl * (M2 + 1);  // row y = xl of the inverse table
+      float2 acc[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) acc[k] = make_float2(0.f, 0.f);
+      for (int p = 0; p < M2; p++) {
+        const float2 w = t[p];
+        const float2* ir = sI + p * M;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int kx = grp * KPG + k;
+          if (k < KPG && kx < M) {
+            const float2 a = ir[kx];
+            acc[k].x = fmaf(w.x, a.x, fmaf(-w.y, a.y, acc[k].x));
+            acc[k].y = fmaf(w.x, a.y, fmaf(w.y, a.x, acc[k].y));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int kx = grp * KPG + k;
+        if (k < KPG && kx < M) {
+          sX[xl * XS + 2 * kx] = acc[k].x;
+          sX[xl * XS + 2 * kx + 1] = acc[k].y;
+        }
+      }
+    }
+    __syncthreads();
+    if (xl < n) {
+      float* zp = z + plane * n * n;
+      float* vp = v ? v + plane * n * n : nullptr;
+      // all of this thread's z values are requested before any is used
+      float zr[NX / 4];
+#pragma unroll
+      for (int k = 0; k < NX / 4; k++) {
+        const int y = grp + 4 * k;
+        zr[k] = y < n ? zp[(int64_t)y * n + xl] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < NX / 4; k++) {
+        const int y = grp + 4 * k;
+        if (y < n) {
+          const float4* xr = reinterpret_cast<const float4*>(sX + y * XS);
+          float acc = 0.f;
+#pragma unroll
+          for (int q = 0; q < MX / 4; q++) {
+            if (4 * q < M2) {
+              const float4 u = xr[q];
+              acc = fmaf(u.x, tt[4 * q],
+                         fmaf(u.y, tt[4 * q + 1], fmaf(u.z, tt[4 * q + 2], fmaf(u.w, tt[4 * q + 3], acc))));
+            }
+          }
+          const float zz = zr[k] + acc;
+          const int64_t i = (int64_t)y * n + xl;
+          zp[i] = zz;
+          if (act == 1) vp[i] = gelu_t(zz, nullptr);
+          else if (act == 2) vp[i] = zz;
+        }
+      }
+    }
+  }
+}
+
+// Complex contraction along a middle axis: out[b][p][i] = sum_q T[p][q] in[b][q][i]
+// (P, Q <= 64). Tiles of 16 columns i; a thread owns one column and the
+// rows p = p0, p0 + 16, ...; T stays in shared memory (row stride Q + 1).
+constexpr int AXI = 16;
+__global__ void __launch_bounds__(256) k_axis(const float2* __restrict__ in, float2* __restrict__ out,
+                                              const float2* __restrict__ T, int64_t B, int P, int Q, int I) {
+  extern __shared__ float2 sma[];
+  const int QS = Q + 1;
+  float2* sT = sma;              // P * QS
+  float2* sIn = sma + P * QS;    // Q * AXI
+  for (int e = threadIdx.x; e < P * Q; e += blockDim.x) sT[(e / Q) * QS + e % Q] = T[e];
+  const int nchunk = (I + AXI - 1) / AXI;
+  const int64_t tiles = B * nchunk;
+  const int i = threadIdx.x % AXI, p0 = threadIdx.x / AXI;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t b = tile / nchunk;
+    const int i0 = (int)(tile % nchunk) * AXI;
+    __syncthreads();
+    {
+      // at most 4 elements per thread (Q <= 64): issue all loads, then store
+      float2 q4[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int e = threadIdx.x + k * 256;
+        const int q = e / AXI, ii = e % AXI;
+        q4[k] = (e < Q * AXI && i0 + ii < I) ? in[(b * Q + q) * I + i0 + ii] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int e = threadIdx.x + k * 256;
+        if (e < Q * AXI) sIn[e] = q4[k];
+      }
+    }
+    __syncthreads();
+    float2 acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) acc[k] = make_float2(0.f, 0.f);
+    for (int q = 0; q < Q; q++) {
+      const float2 x = sIn[q * AXI + i];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int p = p0 + 16 * k;
+        if (p < P) {
+          const float2 t = sT[p * QS + q];
+          acc[k].x = fmaf(t.x, x.x, fmaf(-t.y, x.y, acc[k].x));
+          acc[k].y = fmaf(t.x, x.y, fmaf(t.y, x.x, acc[k].y));
+        }
+      }
+    }
+    if (i0 + i < I) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int p = p0 + 16 * k;
+        if (p < P) out[(b * P + p) * I + i0 + i] = acc[k];
+      }
+    }
+  }
+}
+
+// t[c][k] = sum_j R[k][j][c] s[j][k] (complex, bf16 weights); one warp per
+// mode k, lane c (C <= 32): the weight loads are coalesced, s is broadcast.
+__global__ void k_mix_fwd(const float2* __restrict__ s, const uint16_t* __restrict__ R, float2* __restrict__ t,
+                          int C, int K) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= K) return;
+  float2 acc = make_float2(0.f, 0.f);
+  if (lane < C) {
+    const uint32_t* R2 = reinterpret_cast<const uint32_t*>(R);
+    for (int j = 0; j < C; j++) {
+      const uint32_t wbits = R2[((int64_t)k * C + j) * C + lane];
+      const float wr = __uint_as_float(wbits << 16), wi = __uint_as_float(wbits & 0xffff0000u);
+      const float2 sj = s[(int64_t)j * K + k];
+      acc.x = fmaf(wr, sj.x, fmaf(-wi, sj.y, acc.x));
+      acc.y = fmaf(wr, sj.y, fmaf(wi, sj.x, acc.y));
+    }
+    t[(int64_t)lane * K + k] = acc;
+  }
+}
+
+// Backward of the mixing, G_t scaled by a(kx)/V first (one warp per mode,
+// lane c): dR[k][j][c] += conj(s[j][k]) g[c][k];
+// gs[j][k] = sum_c conj(R[k][j][c]) g[c][k] (a warp reduction over c).
+__global__ void k_mix_bwd(const float2* __restrict__ gt, const float2* __restrict__ s,
+                          const uint16_t* __restrict__ R, float2* __restrict__ gs, float* __restrict__ dR, int C,
+                          int K, int M, float invV) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= K) return;
+  const float a = ((k % M) == 0 ? 1.f : 2.f) * invV;
+  float2 g = make_float2(0.f, 0.f);
+  if (lane < C) {
+    g = gt[(int64_t)lane * K + k];
+    g.x *= a;
+    g.y *= a;
+  }
+  const uint32_t* R2 = reinterpret_cast<const uint32_t*>(R);
+  float2* dR2 = reinterpret_cast<float2*>(dR);
+  for (int j = 0; j < C; j++) {
+    const float2 sj = s[(int64_t)j * K + k];
+    float px = 0.f, py = 0.f;
+    if (lane < C) {
+      const int64_t r = ((int64_t)k * C + j) * C + lane;
+      const uint32_t wbits = R2[r];
+      const float wr = __uint_as_float(wbits << 16), wi = __uint_as_float(wbits & 0xffff0000u);
+      px = wr * g.x + wi * g.y;  // conj(w) g
+      py = wr * g.y - wi * g.x;
+      float2 d = dR2[r];
+      d.x += sj.x * g.x + sj.y * g.y;  // conj(s) g
+      d.y += sj.x * g.y - sj.y * g.x;
+      dR2[r] = d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      px += __shfl_xor_sync(0xffffffffu, px, o);
+      py += __shfl_xor_sync(0xffffffffu, py, o);
+    }
+    if (lane == 0) gs[(int64_t)j * K + k] = make_float2(px, py);
+  }
+}
+
 __global__ void k_gelu_bwd(const float* z, const float* dv, float* dz, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float d;
@@ -382,27 +614,40 @@ __global__ void k_init(Shape s, uint64_t seed, float* p) {
   }
 }
 
-// Block means of f^3 cells, ncomp planes.
-__global__ void k_coarsen(int N, int n, int ncomp, const float* fine, const float* fine2, float* coarse,
-                          const float* scale) {
+// Block means over f^3 cells, one CTA per coarse row (c, z, y): threads run
+// along the fine x axis summing the f x f fine rows (coalesced), then f
+// neighbours are summed through shared memory.
+__global__ void k_coarsen(int N, int n, const float* __restrict__ fine, const float* __restrict__ fine2,
+                          float* __restrict__ coarse, const float* __restrict__ scale) {
+  extern __shared__ float sx[];  // N floats
   const int f = N / n;
-  const int64_t nc = (int64_t)n * n * n;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nc * ncomp) return;
-  const int c = (int)(t / nc);
-  const int64_t v = t % nc;
-  const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((int64_t)n * n));
-  const float* src = fine + (int64_t)c * N * N * N;
-  const float* src2 = fine2 ? fine2 + (int64_t)c * N * N * N : nullptr;
-  double acc = 0.0;
-  for (int dz = 0; dz < f; dz++)
-    for (int dy = 0; dy < f; dy++)
-      for (int dx = 0; dx < f; dx++) {
-        const int64_t i = ((int64_t)(z * f + dz) * N + (y * f + dy)) * N + (x * f + dx);
-        acc += src2 ? 0.5 * ((double)src[i] + (double)src2[i]) : (double)src[i];
+  const int row = blockIdx.x;  // (c n + z) n + y
+  const int y = row % n, z = (row / n) % n, c = row / (n * n);
+  const int64_t N3 = (int64_t)N * N * N;
+  const float* src = fine + c * N3;
+  const float* src2 = fine2 ? fine2 + c * N3 : nullptr;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    float acc = 0.f;
+    for (int dz = 0; dz < f; dz++)
+      for (int dy = 0; dy < f; dy++) {
+        const int64_t i = ((int64_t)(z * f + dz) * N + (y * f + dy)) * N + x;
+        acc += src2 ? 0.5f * (src[i] + src2[i]) : src[i];
       }
-  const double d = (double)f * f * f * (scale ? (double)*scale : 1.0);
-  coarse[t] = (float)(acc / d);
+    sx[x] = acc;
+  }
+  __syncthreads();
+  const float d = (float)f * f * f * (scale ? *scale : 1.f);
+  for (int xc = threadIdx.x; xc < n; xc += blockDim.x) {
+    float acc = 0.f;
+    for (int dx = 0; dx < f; dx++) acc += sx[xc * f + dx];
+    coarse[(int64_t)row * n + xc] = acc / d;
+  }
+}
+
+void launch_coarsen(int N, int n, int ncomp, const float* fine, const float* fine2, float* coarse,
+                    const float* scale, cudaStream_t st) {
+  const int threads = N < 256 ? ((N + 31) / 32) * 32 : 256;
+  k_coarsen<<<(unsigned)(ncomp * n * n), threads, sizeof(float) * N, st>>>(N, n, fine, fine2, coarse, scale);
 }
 
 __global__ void k_input(int n, float a0, const float* g, const double* sumsq, float* x, float* scale_out) {
@@ -418,27 +663,46 @@ __global__ void k_input(int n, float a0, const float* g, const double* sumsq, fl
   }
 }
 
-// Trilinear, periodic, cell-centred upsampling times the scale.
-__global__ void k_output(int N, int n, const float* y, const float* scale, float* H) {
-  const int64_t NF = (int64_t)N * N * N, V = (int64_t)n * n * n;
+// Trilinear, periodic, cell-centred upsampling times the scale. A CTA covers
+// OUT_ROWS fine rows (c, Z, Y0..Y0+OUT_ROWS-1): the coarse rows they blend
+// (two z planes, ny rows each) are staged in shared memory, a thread owns an
+// x column and writes its rows coalesced.
+constexpr int OUT_ROWS = 16;
+__global__ void __launch_bounds__(256) k_output(int N, int n, const float* __restrict__ y,
+                                                const float* __restrict__ scale, float* __restrict__ H) {
+  extern __shared__ float sc[];  // [2][ny][n]
   const int f = N / n;
+  const int row0 = blockIdx.x * OUT_ROWS;  // (c N + Z) N + Y0, N % OUT_ROWS == 0
+  const int Z = (row0 / N) % N, c = row0 / (N * N), Y0 = row0 % N;
+  const float fz = (Z + 0.5f) / f - 0.5f;
+  const int z0 = (int)floorf(fz);
+  const float wz = fz - z0;
+  const int ylo = (int)floorf((Y0 + 0.5f) / f - 0.5f);
+  const int ny = (int)floorf((Y0 + OUT_ROWS - 0.5f) / f - 0.5f) - ylo + 2;
+  const float* yc = y + (int64_t)c * n * n * n;
+  for (int e = threadIdx.x; e < 2 * ny * n; e += blockDim.x) {
+    const int xx = e % n, j = (e / n) % ny, dz = e / (n * ny);
+    const int zz = (z0 + dz + n) % n, yy = ((ylo + j) % n + n) % n;
+    sc[e] = yc[((int64_t)zz * n + yy) * n + xx];
+  }
+  __syncthreads();
   const float s = *scale;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * NF; t += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(t / NF);
-    const int64_t v = t % NF;
-    const int X = (int)(v % N), Y = (int)((v / N) % N), Z = (int)(v / ((int64_t)N * N));
-    float fx = (X + 0.5f) / f - 0.5f, fy = (Y + 0.5f) / f - 0.5f, fz = (Z + 0.5f) / f - 0.5f;
-    const int x0 = (int)floorf(fx), y0 = (int)floorf(fy), z0 = (int)floorf(fz);
-    const float wx = fx - x0, wy = fy - y0, wz = fz - z0;
-    float acc = 0.f;
-    for (int dz = 0; dz < 2; dz++)
-      for (int dy = 0; dy < 2; dy++)
-        for (int dx = 0; dx < 2; dx++) {
-          const int xx = (x0 + dx + n) % n, yy = (y0 + dy + n) % n, zz = (z0 + dz + n) % n;
-          const float w = (dx ? wx : 1 - wx) * (dy ? wy : 1 - wy) * (dz ? wz : 1 - wz);
-          acc += w * y[c * V + ((int64_t)zz * n + yy) * n + xx];
-        }
-    H[t] = s * acc;
+  for (int X = threadIdx.x; X < N; X += blockDim.x) {
+    const float fx = (X + 0.5f) / f - 0.5f;
+    const int x0 = (int)floorf(fx);
+    const float wx = fx - x0;
+    const int xa = (x0 + n) % n, xb = (x0 + 1) % n;
+    for (int r = 0; r < OUT_ROWS; r++) {
+      const float fy = (Y0 + r + 0.5f) / f - 0.5f;
+      const int y0 = (int)floorf(fy);
+      const float wy = fy - y0;
+      const float* p0 = sc + (y0 - ylo) * n;  // dz = 0, rows y0 and y0 + 1
+      const float* p1 = p0 + ny * n;          // dz = 1
+      const float a00 = (1 - wx) * p0[xa] + wx * p0[xb], a01 = (1 - wx) * p0[n + xa] + wx * p0[n + xb];
+      const float a10 = (1 - wx) * p1[xa] + wx * p1[xb], a11 = (1 - wx) * p1[n + xa] + wx * p1[n + xb];
+      H[(int64_t)(row0 + r) * N + X] =
+          s * ((1 - wz) * ((1 - wy) * a00 + wy * a01) + wz * ((1 - wy) * a10 + wy * a11));
+    }
   }
 }
 
@@ -467,27 +731,80 @@ __global__ void k_mixture(int N, float s, int K, const float* centre, const floa
   }
 }
 
-unsigned blocks_for(int64_t n) { return (unsigned)((n + TB - 1) / TB); }
 unsigned grid_stride(int64_t n) {
   int64_t b = (n + TB - 1) / TB;
   return (unsigned)(b < 4096 ? b : 4096);
 }
 
-// Spectral convolution forward: shat <- DFT(v); t <- mix; out (+)= IDFT(t).
-void spectral_fwd(const Shape& s, const Work& w, const float* v, float2* shat, const uint16_t* R, float* out,
-                  cudaStream_t st) {
+size_t smem_axis(int P, int Q) { return sizeof(float2) * ((size_t)P * (Q + 1) + (size_t)Q * AXI); }
+unsigned tiles_grid(int64_t tiles) { return (unsigned)(tiles < 152 * 8 ? tiles : 152 * 8); }
+
+// The fused plane kernels may need more than the default 48 KB of shared memory.
+template <typename K>
+bool opt_in(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) == cudaSuccess;
+}
+bool smem_opt_in() {
+  static const bool ok = opt_in(k_xy_fwd<16>) && opt_in(k_xy_fwd<32>) && opt_in(k_xy_fwd<64>) &&
+                         opt_in(k_xy_inv<16, 8>) && opt_in(k_xy_inv<16, 16>) && opt_in(k_xy_inv<32, 8>) &&
+                         opt_in(k_xy_inv<32, 16>) && opt_in(k_xy_inv<32, 32>) && opt_in(k_xy_inv<64, 8>) &&
+                         opt_in(k_xy_inv<64, 16>) && opt_in(k_xy_inv<64, 32>) && opt_in(k_xy_inv<64, 64>);
+  return ok;
+}
+
+// Forward transform of C channels of real fields v -> out [C][K] (kept modes).
+void dft3(const Shape& s, const Work& w, const float* v, float2* out, cudaStream_t st) {
   const int n = s.n, M = s.M, C = s.C;
-  const int64_t lines = (int64_t)C * n * n;
-  k_dft_x<<<blocks_for(lines * M), TB, 0, st>>>(v, w.a, lines, n, M);
-  // y: [C n][n][M] -> [C n][2M][M]
-  k_dft_outer<<<blocks_for((int64_t)C * n * 2 * M * M), TB, 0, st>>>(w.a, w.b, (int64_t)C * n, n, M, M, n);
+  // x and y per (c, z) plane: [C n][n][n] -> [C n][2M][M]
+  const unsigned g = tiles_grid((int64_t)C * n / 2);
+  const size_t sm = smem_xy_fwd(n, M);
+  const int64_t np = (int64_t)C * n;
+  if (n <= 16) k_xy_fwd<16><<<g, 256, sm, st>>>(v, w.b, w.tab.fx, w.tab.tf, n, M, np);
+  else if (n <= 32) k_xy_fwd<32><<<g, 256, sm, st>>>(v, w.b, w.tab.fx, w.tab.tf, n, M, np);
+  else k_xy_fwd<64><<<g, 256, sm, st>>>(v, w.b, w.tab.fx, w.tab.tf, n, M, np);
   // z: [C][n][2M M] -> [C][2M][2M M]
-  k_dft_outer<<<blocks_for((int64_t)C * s.K), TB, 0, st>>>(w.b, shat, C, n, 2 * M * M, M, n);
-  k_mix_fwd<<<blocks_for((int64_t)s.K * C), TB, 0, st>>>(shat, R, w.c, C, s.K);
-  // inverse: z then y then x (weights 1 / 2, 1/n^3)
-  k_idft_outer<<<blocks_for((int64_t)C * n * 2 * M * M), TB, 0, st>>>(w.c, w.b, C, 2 * M * M, M, n);
-  k_idft_outer<<<blocks_for((int64_t)C * n * n * M), TB, 0, st>>>(w.b, w.a, (int64_t)C * n, M, M, n);
-  k_idft_x<<<blocks_for(lines * n), TB, 0, st>>>(w.a, out, lines, n, M, 2.f, 1.f / (float)s.V, 1);
+  const int Iz = 2 * M * M;
+  k_axis<<<tiles_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(2 * M, n), st>>>(w.b, out, w.tab.tf, C,
+                                                                                              2 * M, n, Iz);
+}
+
+// Inverse transform of [C][K] kept modes, added into z; act as in k_xy_inv.
+void idft3(const Shape& s, const Work& w, const float2* in, float* z, float* v, const float* xtab, int act,
+           cudaStream_t st) {
+  const int n = s.n, M = s.M, C = s.C;
+  const int Iz = 2 * M * M;
+  k_axis<<<tiles_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(n, 2 * M), st>>>(in, w.b, w.tab.ti, C, n,
+                                                                                              2 * M, Iz);
+  const unsigned g = tiles_grid((int64_t)C * n / 2);
+  const size_t sm = smem_xy_inv(n, M);
+  const int64_t np = (int64_t)C * n;
+  const int M2 = 2 * M;
+#define XYI(NX, MX) k_xy_inv<NX, MX><<<g, 256, sm, st>>>(w.b, z, v, xtab, w.tab.ti, n, M, act, np)
+  if (n <= 16) {
+    if (M2 <= 8) XYI(16, 8);
+    else XYI(16, 16);
+  } else if (n <= 32) {
+    if (M2 <= 8) XYI(32, 8);
+    else if (M2 <= 16) XYI(32, 16);
+    else XYI(32, 32);
+  } else {
+    if (M2 <= 8) XYI(64, 8);
+    else if (M2 <= 16) XYI(64, 16);
+    else if (M2 <= 32) XYI(64, 32);
+    else XYI(64, 64);
+  }
+#undef XYI
+}
+
+void tables(const Shape& s, const Work& w, cudaStream_t st) {
+  k_tables<<<16, 256, 0, st>>>(s.n, s.M, 1.f / (float)s.V, w.tab);
+}
+
+void pw(const float* in, int Cin, const uint16_t* W, const uint16_t* b, int Cout, float* out, int64_t V,
+        int transpose, cudaStream_t st) {
+  const unsigned g = grid_stride(V);
+  if (Cin <= 4) k_pw<4><<<g, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
+  else k_pw<32><<<g, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
 }
 
 }  // namespace
@@ -526,22 +843,24 @@ int mond_fno_forward(mond_fno_shape sh, const uint16_t* P, const float* x, float
   Shape s;
   if (!P || !x || !y || !workspace || !make_shape(sh, &s)) return -1;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!smem_opt_in()) return -3;
   Work w;
   carve(s, (char*)workspace, &w);
   const int C = s.C;
   const int64_t V = s.V, CV = (int64_t)C * V;
-  const unsigned gv = grid_stride(V);
-  k_pw<<<gv, TB, 0, st>>>(x, 4, P + s.off_P(), P + s.off_p(), C, w.v, V, 0, 0);
+  const unsigned warps_grid = (unsigned)(((int64_t)s.K * 32 + TB - 1) / TB);
+  tables(s, w, st);
+  pw(x, 4, P + s.off_P(), P + s.off_p(), C, w.v, V, 0, st);
   for (int l = 0; l < s.L; l++) {
     const float* vl = w.v + l * CV;
     float* zl = w.z + l * CV;
-    k_pw<<<gv, TB, 0, st>>>(vl, C, P + s.off_W(l), P + s.off_b(l), C, zl, V, 0, 0);
-    spectral_fwd(s, w, vl, w.shat + (int64_t)l * C * s.K, P + s.off_R(l), zl, st);
-    float* vn = w.v + (l + 1) * CV;
-    if (l + 1 < s.L) k_gelu<<<grid_stride(CV), TB, 0, st>>>(zl, vn, CV);
-    else cudaMemcpyAsync(vn, zl, sizeof(float) * CV, cudaMemcpyDeviceToDevice, st);
+    float2* shat = w.shat + (int64_t)l * C * s.K;
+    pw(vl, C, P + s.off_W(l), P + s.off_b(l), C, zl, V, 0, st);
+    dft3(s, w, vl, shat, st);
+    k_mix_fwd<<<warps_grid, TB, 0, st>>>(shat, P + s.off_R(l), w.c, C, s.K);
+    idft3(s, w, w.c, zl, w.v + (l + 1) * CV, w.tab.ix, l + 1 < s.L ? 1 : 2, st);
   }
-  k_pw<<<gv, TB, 0, st>>>(w.v + s.L * CV, C, P + s.off_Q(), P + s.off_q(), 3, y, V, 0, 0);
+  pw(w.v + s.L * CV, C, P + s.off_Q(), P + s.off_q(), 3, y, V, 0, st);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -550,36 +869,41 @@ int mond_fno_backward(mond_fno_shape sh, const uint16_t* P, const float* x, cons
   Shape s;
   if (!P || !x || !dy || !grad || !workspace || !make_shape(sh, &s)) return -1;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!smem_opt_in()) return -3;
   Work w;
   carve(s, (char*)workspace, &w);
-  const int C = s.C, n = s.n, M = s.M;
-  const int64_t V = s.V, CV = (int64_t)C * V, lines = (int64_t)C * n * n;
-  const unsigned gv = grid_stride(V);
-  const unsigned gw = 152;
+  const int C = s.C, M = s.M;
+  const int64_t V = s.V, CV = (int64_t)C * V;
+  const unsigned gw = 152 * 4;
+  const unsigned warps_grid = (unsigned)(((int64_t)s.K * 32 + TB - 1) / TB);
+  tables(s, w, st);
   // projection
   k_wgrad<<<gw, TB, 0, st>>>(dy, 3, w.v + s.L * CV, C, V, grad + s.off_Q(), grad + s.off_q());
-  k_pw<<<gv, TB, 0, st>>>(dy, 3, P + s.off_Q(), nullptr, C, w.dv, V, 0, 1);
+  float* dv = w.dv;
+  float* dv2 = w.dv2;
+  pw(dy, 3, P + s.off_Q(), nullptr, C, dv, V, 1, st);
   for (int l = s.L - 1; l >= 0; l--) {
     const float* vl = w.v + l * CV;
     const float* zl = w.z + l * CV;
-    if (l + 1 < s.L) k_gelu_bwd<<<grid_stride(CV), TB, 0, st>>>(zl, w.dv, w.dz, CV);
-    else cudaMemcpyAsync(w.dz, w.dv, sizeof(float) * CV, cudaMemcpyDeviceToDevice, st);
+    const float* dz = dv;  // the last layer has no activation
+    if (l + 1 < s.L) {
+      k_gelu_bwd<<<grid_stride(CV), TB, 0, st>>>(zl, dv, w.dz, CV);
+      dz = w.dz;
+    }
     // pointwise part
-    k_wgrad<<<gw, TB, 0, st>>>(w.dz, C, vl, C, V, grad + s.off_W(l), grad + s.off_b(l));
-    k_pw<<<gv, TB, 0, st>>>(w.dz, C, P + s.off_W(l), nullptr, C, w.dv2, V, 0, 1);
+    k_wgrad<<<gw, TB, 0, st>>>(dz, C, vl, C, V, grad + s.off_W(l), grad + s.off_b(l));
+    pw(dz, C, P + s.off_W(l), nullptr, C, dv2, V, 1, st);
     // spectral part: G_t = (a/V) DFT(dz), through the mixing adjoint, back with the adjoint transform
-    k_dft_x<<<blocks_for(lines * M), TB, 0, st>>>(w.dz, w.a, lines, n, M);
-    k_dft_outer<<<blocks_for((int64_t)C * n * 2 * M * M), TB, 0, st>>>(w.a, w.b, (int64_t)C * n, n, M, M, n);
-    k_dft_outer<<<blocks_for((int64_t)C * s.K), TB, 0, st>>>(w.b, w.c, C, n, 2 * M * M, M, n);
-    k_mix_bwd<<<blocks_for((int64_t)s.K * C), TB, 0, st>>>(w.c, w.shat + (int64_t)l * C * s.K, P + s.off_R(l), w.d,
-                                                            grad + s.off_R(l), C, s.K, M, 1.f / (float)V);
-    k_idft_outer<<<blocks_for((int64_t)C * n * 2 * M * M), TB, 0, st>>>(w.d, w.b, C, 2 * M * M, M, n);
-    k_idft_outer<<<blocks_for((int64_t)C * n * n * M), TB, 0, st>>>(w.b, w.a, (int64_t)C * n, M, M, n);
-    k_idft_x<<<blocks_for(lines * n), TB, 0, st>>>(w.a, w.dv2, lines, n, M, 1.f, 1.f, 1);
-    cudaMemcpyAsync(w.dv, w.dv2, sizeof(float) * CV, cudaMemcpyDeviceToDevice, st);
+    dft3(s, w, dz, w.c, st);
+    k_mix_bwd<<<warps_grid, TB, 0, st>>>(w.c, w.shat + (int64_t)l * C * s.K, P + s.off_R(l), w.d, grad + s.off_R(l),
+                                         C, s.K, M, 1.f / (float)V);
+    idft3(s, w, w.d, dv2, nullptr, w.tab.ixa, 0, st);
+    float* t = dv;
+    dv = dv2;
+    dv2 = t;
   }
   // lift
-  k_wgrad<<<gw, TB, 0, st>>>(w.dv, C, x, 4, V, grad + s.off_P(), grad + s.off_p());
+  k_wgrad<<<gw, TB, 0, st>>>(dv, C, x, 4, V, grad + s.off_P(), grad + s.off_p());
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -605,8 +929,7 @@ int mond_fno_adam(int64_t count, float* p, float* g, float* m, float* v, float l
 int mond_fno_coarsen(int N, int n, int ncomp, const float* fine, const float* fine2, float* coarse,
                      const float* scale, void* stream) {
   if (!fine || !coarse || n <= 0 || N % n || ncomp < 1) return -1;
-  const int64_t tot = (int64_t)n * n * n * ncomp;
-  k_coarsen<<<blocks_for(tot), TB, 0, (cudaStream_t)stream>>>(N, n, ncomp, fine, fine2, coarse, scale);
+  launch_coarsen(N, n, ncomp, fine, fine2, coarse, scale, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -615,7 +938,7 @@ int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* sca
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t V = (int64_t)n * n * n;
   // coarse g_N into the x buffer's first 3 planes, its sum of squares into the scale slot's neighbour
-  k_coarsen<<<blocks_for(3 * V), TB, 0, st>>>(N, n, 3, gN, nullptr, x, nullptr);
+  launch_coarsen(N, n, 3, gN, nullptr, x, nullptr, st);
   double* acc = reinterpret_cast<double*>(scale_out + 2);  // scale_out must have room for 2 + 2 floats
   cudaMemsetAsync(acc, 0, sizeof(double), st);
   k_sumsq<<<grid_stride(3 * V), TB, 0, st>>>(x, 3 * V, acc);
@@ -625,7 +948,11 @@ int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* sca
 
 int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* stream) {
   if (!y || !scale || !H || n <= 0 || N % n) return -1;
-  k_output<<<grid_stride(3LL * N * N * N), TB, 0, (cudaStream_t)stream>>>(N, n, y, scale, H);
+  if (N % OUT_ROWS) return -1;
+  const int threads = N < 256 ? ((N + 31) / 32) * 32 : 256;
+  const int ny_max = OUT_ROWS / (N / n) + 3;
+  k_output<<<(unsigned)(3 * N * N / OUT_ROWS), threads, sizeof(float) * 2 * ny_max * n, (cudaStream_t)stream>>>(
+      N, n, y, scale, H);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

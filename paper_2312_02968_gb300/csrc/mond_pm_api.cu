@@ -204,11 +204,12 @@ __global__ void k_dep_sum(int64_t n3, const uint64_t* dep, unsigned long long* o
 void mond_pm_set_create_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
 enum KClass {
-  KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_Y_FWD, KC_Y_INV,
+  KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_X_NU_REAL, KC_Y_FWD, KC_Y_INV,
   KC_Z_NEWTON, KC_Z_CURL, KC_Z_DIV, KC_Z_FINAL, KC_Z_SMOOTH, KC_BIN, KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_COUNT
 };
 const char* const kKName[KC_COUNT] = {"xpass_rho", "xpass_nu_first", "xpass_nu", "xpass_mu", "xpass_inv",
-                                      "xpass_fwd", "ypass_fwd", "ypass_inv", "zpass_newton", "zpass_curl",
+                                      "xpass_fwd", "xpass_nu_real", "ypass_fwd", "ypass_inv", "zpass_newton",
+                                      "zpass_curl",
                                       "zpass_div", "zpass_final", "zpass_smooth", "bin", "deposit",
                                       "gather_push", "other"};
 
@@ -237,6 +238,7 @@ struct mond_pm {
   const float* mass = nullptr;
   int kacc = 0;
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false, density_given = false;
+  bool gn_valid = false;  // w.gN holds the Newton field of the current density
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   // TMA views of the spectral buffers: y-pass tiles (3-D), z-pass tiles with
   // the component as a dimension (4-D; W with 1 or 3 components per box, A
@@ -336,6 +338,7 @@ cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
     case passes::X_MU: bytes = 6 * S + 3 * R; break;
     case passes::X_INV: bytes = a.ncomp * (S + R * (a.real_out2 ? 2 : 1)); break;
     case passes::X_FWD: bytes = a.ncomp * (S + R); break;
+    case passes::X_NU_REAL: bytes = 3 * S + 3 * R + (a.H0 ? 3 * R : 0); break;
   }
   Timed tm(h, KC_X_RHO + mode, bytes);
   switch (h->nf) {
@@ -558,6 +561,7 @@ int do_deposit(mond_pm* h) {
   h->have_dep = true;
   h->have_solve = false;
   h->density_given = false;
+  h->gn_valid = false;
   return MOND_OK;
 }
 
@@ -606,38 +610,43 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   const int nout = h->keep_phi ? 4 : 3;
   float2* W = h->w.W;
   float2* A = h->w.A;
-  passes::XArgs x{};
-  x.ncomp = 1;
-  x.spec = W;
-  x.dep = h->w.dep;
-  x.rho_out = h->w.rho;
-  x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
-  if (h->density_given) {
-    // density set by mond_pm_set_density: forward x-transform of the FP32 plane
-    passes::XArgs xf{};
-    xf.ncomp = 1;
-    xf.spec = W;
-    xf.real_in = h->w.rho;
-    PK(xpass(h, passes::X_FWD, xf));
-  } else {
-    PK(xpass(h, passes::X_RHO, x));
+  // the Newton field is reused when the density has not changed since the last solve
+  const bool reuse = h->gn_valid && K > 0;
+  if (!reuse) {
+    passes::XArgs x{};
+    x.ncomp = 1;
+    x.spec = W;
+    x.dep = h->w.dep;
+    x.rho_out = h->w.rho;
+    x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
+    if (h->density_given) {
+      // density set by mond_pm_set_density: forward x-transform of the FP32 plane
+      passes::XArgs xf{};
+      xf.ncomp = 1;
+      xf.spec = W;
+      xf.real_in = h->w.rho;
+      PK(xpass(h, passes::X_FWD, xf));
+    } else {
+      PK(xpass(h, passes::X_RHO, x));
+    }
+    PK(ypass(h, -1, W, 1));
+    if (K == 0) {
+      PK(zpass(h, passes::Z_NEWTON, W, A, nout));
+      PK(ypass(h, +1, A, nout));
+      passes::XArgs xi{};
+      xi.ncomp = nout;
+      xi.spec = A;
+      xi.real_out = h->w.acc;
+      PK(xpass(h, passes::X_INV, xi));
+      CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
+      h->last_iters = 0;
+      h->have_solve = true;
+      h->gn_valid = true;
+      return MOND_OK;
+    }
+    PK(zpass(h, passes::Z_NEWTON, W, W, 3));
+    PK(ypass(h, +1, W, 3));
   }
-  PK(ypass(h, -1, W, 1));
-  if (K == 0) {
-    PK(zpass(h, passes::Z_NEWTON, W, A, nout));
-    PK(ypass(h, +1, A, nout));
-    passes::XArgs xi{};
-    xi.ncomp = nout;
-    xi.spec = A;
-    xi.real_out = h->w.acc;
-    PK(xpass(h, passes::X_INV, xi));
-    CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
-    h->last_iters = 0;
-    h->have_solve = true;
-    return MOND_OK;
-  }
-  PK(zpass(h, passes::Z_NEWTON, W, W, 3));
-  PK(ypass(h, +1, W, 3));
   const float* H0 = nullptr;
   if (warm == MOND_WARM_GUESS) {
     // project the guess onto its divergence-free part: H state = P_div(guess)
@@ -655,6 +664,8 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     xi.real_out = h->w.Hs;
     PK(xpass(h, passes::X_INV, xi));
     H0 = h->w.Hs;
+  } else if (warm == MOND_WARM_GUESS_RAW) {
+    H0 = Hguess;
   } else if (warm == MOND_WARM_PREV) {
     H0 = h->w.Hs;
   } else if (K == 1 || h->track_dh) {
@@ -665,8 +676,10 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   xn.ncomp = 3;
   xn.spec = W;
   xn.gN_out = h->w.gN;
+  xn.gN = h->w.gN;
   xn.H0 = H0;
-  PK(xpass(h, passes::X_NU_FIRST, xn));
+  PK(xpass(h, reuse ? passes::X_NU_REAL : passes::X_NU_FIRST, xn));
+  h->gn_valid = true;
   for (int j = 1; j <= K; j++) {
     PK(ypass(h, -1, W, 3));
     const bool last = (j == K);
@@ -903,6 +916,7 @@ int mond_pm_set_density(mond_pm_t h, const float* rho) {
   if (!h || !rho) return MOND_EINVAL;
   CK(cudaMemcpyAsync(h->w.rho, rho, sizeof(float) * h->n3, cudaMemcpyDeviceToDevice, h->st));
   h->density_given = true;
+  h->gn_valid = false;
   h->have_dep = true;
   h->have_solve = false;
   return MOND_OK;
@@ -912,8 +926,9 @@ int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess)
   if (!h) return MOND_EINVAL;
   if (!h->have_dep) return fail(h, MOND_ESTATE, "solve_field before deposit");
   if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
-  if (warm < 0 || warm > 2) return fail(h, MOND_EINVAL, "bad warm mode %d", warm);
-  if (warm == MOND_WARM_GUESS && !H_guess) return fail(h, MOND_EINVAL, "MOND_WARM_GUESS needs H_guess");
+  if (warm < 0 || warm > 3) return fail(h, MOND_EINVAL, "bad warm mode %d", warm);
+  if ((warm == MOND_WARM_GUESS || warm == MOND_WARM_GUESS_RAW) && !H_guess)
+    return fail(h, MOND_EINVAL, "a guess warm start needs H_guess");
   if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
   return do_solve(h, n_iter, warm, H_guess);
 }

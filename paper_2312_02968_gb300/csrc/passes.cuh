@@ -44,7 +44,8 @@ enum XMode {
   X_NU = 2,        // C2R H (optionally store, track dH), F = g_N + H, g_M = nu(F) F, R2C
   X_MU = 3,        // C2R g_M, F = mu(g_M) g_M, H = F - g_N, R2C
   X_INV = 4,       // C2R -> real planes
-  X_FWD = 5        // real planes -> R2C
+  X_FWD = 5,       // real planes -> R2C
+  X_NU_REAL = 6    // stored g_N (real) + H0, g_M = nu(F) F, R2C (reuses the last Newton solve)
 };
 
 // z-pass modes
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
   const int nc = (MODE == X_RHO) ? 1 : a.ncomp;
 
   constexpr bool INV = (MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_INV);
-  constexpr bool FWD = (MODE == X_RHO || MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_FWD);
+  constexpr bool FWD = (MODE == X_RHO || MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_FWD ||
+                        MODE == X_NU_REAL);
 
   if constexpr (INV) {
     for (int c = 0; c < nc; c++) x_load_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
@@ -264,12 +266,25 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
     } else {
       // three components, two samples each
       float v[3][2], gn[3][2];
-      for (int c = 0; c < 3; c++) {
-        float2 t = p0[c * TILE];
-        v[c][0] = t.x;
-        v[c][1] = t.y;
+      if constexpr (MODE != X_NU_REAL) {
+        for (int c = 0; c < 3; c++) {
+          float2 t = p0[c * TILE];
+          v[c][0] = t.x;
+          v[c][1] = t.y;
+        }
       }
-      if constexpr (MODE == X_NU_FIRST) {
+      if constexpr (MODE == X_NU_REAL) {
+        // F = g_N + H0 from the stored Newton field
+        for (int c = 0; c < 3; c++) {
+          float2 t = *reinterpret_cast<const float2*>(a.gN + (int64_t)c * N * N * N + ri);
+          float2 h0 = a.H0 ? *reinterpret_cast<const float2*>(a.H0 + (int64_t)c * N * N * N + ri)
+                           : make_float2(0.f, 0.f);
+          gn[c][0] = t.x;
+          gn[c][1] = t.y;
+          v[c][0] = t.x + h0.x;
+          v[c][1] = t.y + h0.y;
+        }
+      } else if constexpr (MODE == X_NU_FIRST) {
         // input is g_N; store it; F = g_N + H0
         for (int c = 0; c < 3; c++) {
           *reinterpret_cast<float2*>(a.gN_out + (int64_t)c * N * N * N + ri) = make_float2(v[c][0], v[c][1]);

@@ -53,6 +53,7 @@ cudaError_t CAT(mond_xpass_, MOND_N)(int mode, const passes::XArgs& a, cudaStrea
     case X_MU: return launch_x<X_MU>(a, st);
     case X_INV: return launch_x<X_INV>(a, st);
     case X_FWD: return launch_x<X_FWD>(a, st);
+    case X_NU_REAL: return launch_x<X_NU_REAL>(a, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -232,6 +232,9 @@ class GuessSolver:
         upsample(self.y, h.nf, net.n, self.scale, self.H, h.stream)
         return self.H
 
-    def solve(self, n_iter: int = 1):
+    def solve(self, n_iter: int = 1, project: bool = False):
+        """predict() then n_iter iterations from the guess (projected onto its
+        divergence-free part first when project is set); the Newton field of
+        predict() is reused by the solve."""
         self.predict()
-        self.h.solve_field(n_iter, B.WARM_GUESS, self.H)
+        self.h.solve_field(n_iter, B.WARM_GUESS if project else B.WARM_GUESS_RAW, self.H)

@@ -175,7 +175,7 @@ def test_solve_padded_grid_two_body(B):
     assert rel(g, g_ref) < 10 * tol  # the two self-fields cancel to about 1/10 of the ball terms
 
 
-@pytest.mark.parametrize("warm", ["prev", "guess"])
+@pytest.mark.parametrize("warm", ["prev", "guess", "guess_raw"])
 def test_warm_start_matches_oracle(B, warm):
     n, sigma, mu = 32, 1.5, 0
     p = W.isothermal(n, 1.0, 3000, 3.0, 12.0, seed=21)
@@ -188,11 +188,37 @@ def test_warm_start_matches_oracle(B, warm):
     else:
         rng = np.random.default_rng(3)
         guess = (1e-3 * rng.standard_normal((3, n, n, n))).astype(np.float32)
-        h.solve_field(1, B.WARM_GUESS, torch.from_numpy(guess).cuda())
-        H0 = oracle.project_div(guess.astype(np.float64), 1.0)
+        if warm == "guess":
+            h.solve_field(1, B.WARM_GUESS, torch.from_numpy(guess).cuda())
+            H0 = oracle.project_div(guess.astype(np.float64), 1.0)
+        else:
+            h.solve_field(1, B.WARM_GUESS_RAW, torch.from_numpy(guess).cuda())
+            H0 = guess.astype(np.float64)
     ref = oracle_fields(p, n, sigma, mu, 1, H0=H0, finish=True)
     assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
     assert rel(h.get_field(B.FIELD_H).cpu().numpy(), ref["H"], scale=ref["gN"]) < TOL
+
+
+def test_newton_field_reused_within_one_density(B):
+    """A second solve on the same density starts from the stored g_N and gives
+    the same acceleration bit for bit; a density uploaded with set_density
+    equal to the deposit's gives the same result up to the rounding of a
+    differently compiled x-transform (the compiler may contract a*b+c
+    differently in the two kernels)."""
+    n, sigma = 32, 1.5
+    p = W.isothermal(n, 1.0, 4000, 3.0, 12.0, seed=23)
+    h, _ = make(B, n, 1, p, sigma, mu=2)
+    h.deposit()
+    h.solve_field(4)
+    a1 = h.get_field(B.FIELD_ACC).cpu().numpy()
+    h.solve_field(4)
+    a2 = h.get_field(B.FIELD_ACC).cpu().numpy()
+    rho = h.get_field(B.FIELD_RHO).clone()
+    h.set_density(rho)
+    h.solve_field(4)
+    a3 = h.get_field(B.FIELD_ACC).cpu().numpy()
+    assert np.array_equal(a1, a2)
+    assert rel(a3, a1) < 1e-6
 
 
 # ---------------------------------------------------------------------------
