@@ -83,10 +83,14 @@ enum {
 enum {
   MOND_OPT_KEEP_PHI = 1,  /* value 1: also form the potential phi in the final pass */
   MOND_OPT_TRACK_DH = 2,  /* value 1: record ||H_j - H_{j-1}|| / ||g_N|| per iteration (costs one reduction) */
-  MOND_OPT_USE_GRAPH = 3, /* value 1: replay mond_pm_step as a captured CUDA graph (default 0) */
+  MOND_OPT_USE_GRAPH = 3, /* value 1: mond_pm_step runs as a CUDA graph, captured on first use and again
+                             when an argument, option or binding changes; needs a non-default stream and
+                             is bypassed while MOND_OPT_TIMING is on (default 0) */
   MOND_OPT_TIMING = 4,    /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
-  MOND_OPT_PIPELINED = 5  /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
+  MOND_OPT_PIPELINED = 5, /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
                              0: one tile per CTA with plain loads (same results) */
+  MOND_OPT_CHUNK = 6      /* particles per deposit/gather work item: a power of two in 256..16384
+                             (default 2048; same results) */
 };
 
 /* Per kernel class: launches, device time between the events around each
@@ -191,8 +195,46 @@ int mond_pm_half_kick(mond_pm_t h, double dt);
 /* Force at the particles only (Eq. gi) into g_out (device float32 [N][3]). */
 int mond_pm_gather(mond_pm_t h, float* g_out);
 
-/* One time step: deposit, solve_field(n_iter, warm, NULL), gather_push(dt). */
+/* One time step: deposit, solve_field(n_iter, warm, NULL), gather_push(dt).
+ * warm: MOND_WARM_NONE or MOND_WARM_PREV. */
 int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm);
+
+/* ---- batches of independent systems -------------------------------------
+ * A batch steps many handles (grids of any supported size, each with its own
+ * particles) as one CUDA graph: a fork from the batch stream to every
+ * handle's stream, one mond_pm_step of each system on its own stream, and a
+ * join back. The graph is captured on the first call and again whenever a
+ * step argument, an option or a particle binding of any member changes.
+ * Ownership: the handles stay owned by the caller and must outlive the batch;
+ * each needs its own non-default stream, distinct from the batch stream. */
+typedef struct mond_pm_batch* mond_pm_batch_t;
+
+/* Create a batch of n handles; stream: the batch's own non-default stream.
+ * Errors: MOND_EINVAL (default streams, repeated handles or streams); the
+ * text is in mond_pm_last_error(NULL). */
+int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_batch_t* out);
+
+/* Enqueue n_steps graph launches of one step (deposit, solve_field(n_iter,
+ * warm NONE or PREV), gather_push(dt)) of every member on the batch stream.
+ * Does not synchronise. */
+int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, int warm);
+
+/* Wait for the batch stream and return the first latched device error of the
+ * members. */
+int mond_pm_batch_sync(mond_pm_batch_t b);
+
+/* Kernel launches replayed by the batch's graph launches so far. */
+int64_t mond_pm_batch_kernel_launches(mond_pm_batch_t b);
+
+/* Synchronise and release the batch (not its handles). */
+int mond_pm_batch_destroy(mond_pm_batch_t b);
+
+/* Autotuner: time `trials` steps of length zero (which leave the particles
+ * exactly as they are; the H state is reset) for each work-item size in
+ * {512, 1024, 2048, 4096} and each pass variant (MOND_OPT_PIPELINED 0/1) on
+ * the handle's stream, keep the fastest and report it (either out pointer may
+ * be NULL). Synchronises. */
+int mond_pm_autotune(mond_pm_t h, int n_iter, int trials, int64_t* chosen_chunk, int* chosen_pipelined);
 
 /* One time step through host memory: copies cell/offset/vel of the N bound
  * particles from the host arrays (pinned memory recommended) to the bound

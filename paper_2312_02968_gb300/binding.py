@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libmondpm.so")
 MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
 WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW = 0, 1, 2, 3
 FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
-OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED = 1, 2, 3, 4, 5
+OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK = 1, 2, 3, 4, 5, 6
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
 
@@ -65,6 +65,12 @@ SIGNATURES = {
     "mond_pm_kernel_launches": (_I64, [_P]),
     "mond_pm_kernel_stats": (_I, [_P, ctypes.POINTER(KStat), _I, ctypes.POINTER(_I)]),
     "mond_pm_deposit_noalloc": (_I, [ctypes.c_int32, _D, _D, _I64, _P, _P, _P, _P, _P]),
+    "mond_pm_batch_create": (_I, [_I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
+    "mond_pm_batch_step": (_I, [_P, _D, _I, _I, _I]),
+    "mond_pm_batch_sync": (_I, [_P]),
+    "mond_pm_batch_kernel_launches": (_I64, [_P]),
+    "mond_pm_batch_destroy": (_I, [_P]),
+    "mond_pm_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I)]),
 }
 
 
@@ -276,3 +282,54 @@ class MondPM:
         self._check(lib().mond_pm_kernel_stats(self.h, arr, 32, ctypes.byref(cnt)))
         return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "ms": float(arr[i].ms),
                  "bytes": float(arr[i].bytes)} for i in range(min(cnt.value, 32))]
+
+
+def autotune(h: MondPM, n_iter: int = 4, trials: int = 3):
+    """Pick the work-item size and pass variant of one handle by timing
+    zero-length steps (mond_pm_autotune); returns (chunk, pipelined)."""
+    c = ctypes.c_int64()
+    p = ctypes.c_int()
+    h._check(lib().mond_pm_autotune(h.h, int(n_iter), int(trials), ctypes.byref(c), ctypes.byref(p)))
+    return int(c.value), int(p.value)
+
+
+class Batch:
+    """Independent systems stepped together as one CUDA graph per step
+    (mond_pm_batch_*). Each handle needs its own stream; the batch has one
+    more. The handles stay owned by the caller."""
+
+    def __init__(self, handles, stream=None):
+        import torch
+
+        self.handles = list(handles)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (_P * len(self.handles))(*[h.h for h in self.handles])
+        out = _P()
+        rc = lib().mond_pm_batch_create(len(self.handles), arr, _P(self.stream.cuda_stream), ctypes.byref(out))
+        if rc != 0:
+            raise MondError(rc, lib().mond_pm_last_error(None).decode())
+        self.b = out
+
+    def step(self, dt: float, n_steps: int = 1, n_iter: int = 4, warm: int = WARM_NONE):
+        rc = lib().mond_pm_batch_step(self.b, float(dt), int(n_steps), int(n_iter), int(warm))
+        if rc != 0:
+            raise MondError(rc, " / ".join(lib().mond_pm_last_error(h.h).decode() for h in self.handles[:1]))
+
+    def sync(self):
+        rc = lib().mond_pm_batch_sync(self.b)
+        if rc != 0:
+            raise MondError(rc, "device error in a batch member")
+
+    def kernel_launches(self) -> int:
+        return int(lib().mond_pm_batch_kernel_launches(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().mond_pm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

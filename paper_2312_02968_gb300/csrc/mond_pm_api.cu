@@ -240,6 +240,21 @@ struct mond_pm {
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false, density_given = false;
   bool gn_valid = false;  // w.gN holds the Newton field of the current density
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
+  int chunk = parts::CHUNK;  // particles per deposit/gather work item
+  // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
+  // mond_pm_step for the key below, replayed with one cudaGraphLaunch
+  cudaGraphExec_t gexec = nullptr;
+  struct GraphKey {
+    double dt;
+    int n_iter, warm, keep_phi, track_dh, pipelined, chunk;
+    int64_t N;
+    const void* cell;
+    bool operator==(const GraphKey& o) const {
+      return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
+             track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk && N == o.N && cell == o.cell;
+    }
+  } gkey{};
+  int64_t glaunches = 0;
   // TMA views of the spectral buffers: y-pass tiles (3-D), z-pass tiles with
   // the component as a dimension (4-D; W with 1 or 3 components per box, A
   // with 3 or 4)
@@ -464,6 +479,7 @@ int do_bin(mond_pm* h) {
   b.bsum = h->w.bsum;
   b.tile_start = h->w.tile_start;
   b.chunk_start = h->w.chunk_start;
+  b.chunk = h->chunk;
   b.perm = h->w.perm;
   b.status = h->w.status;
   const int64_t M = h->n3 + 1;
@@ -539,6 +555,7 @@ int do_deposit(mond_pm* h) {
   d.perm = h->w.perm;
   d.tile_start = h->w.tile_start;
   d.chunk_start = h->w.chunk_start;
+  d.chunk = h->chunk;
   d.lut = h->w.lut;
   d.ball = h->w.ball;
   d.ball_lin = h->w.ball_lin;
@@ -578,6 +595,7 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.perm = h->w.perm;
   g.tile_start = h->w.tile_start;
   g.chunk_start = h->w.chunk_start;
+  g.chunk = h->chunk;
   g.acc = h->w.acc;
   g.ball = h->w.ball;
   g.ball_hlin = h->w.ball_hlin;
@@ -856,6 +874,7 @@ int mond_pm_destroy(mond_pm_t h) {
   if (!h) return MOND_EINVAL;
   cudaStreamSynchronize(h->st);
   collect_timing(h);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (auto e : h->evpool) cudaEventDestroy(e);
   delete h;
   return MOND_OK;
@@ -867,6 +886,11 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_KEEP_PHI: h->keep_phi = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_TRACK_DH: h->track_dh = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_USE_GRAPH: h->use_graph = value ? 1 : 0; return MOND_OK;
+    case MOND_OPT_CHUNK:
+      if (value < 256 || value > 16384 || (value & (value - 1)))
+        return fail(h, MOND_EINVAL, "chunk must be a power of two in 256..16384");
+      h->chunk = (int)value;
+      return MOND_OK;
     case MOND_OPT_PIPELINED:
       h->pipelined = value ? 1 : 0;
       return MOND_OK;
@@ -983,13 +1007,249 @@ int mond_pm_gather(mond_pm_t h, float* g_out) {
   return do_gather(h, g_out, 0.0, 0, 0);
 }
 
-int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
-  if (!h) return MOND_EINVAL;
+namespace {
+
+int step_direct(mond_pm_t h, double dt, int n_iter, int warm) {
   int rc = mond_pm_deposit(h);
   if (rc) return rc;
   rc = mond_pm_solve_field(h, n_iter, warm, nullptr);
   if (rc) return rc;
   return mond_pm_gather_push(h, dt);
+}
+
+bool capturable(cudaStream_t st) { return st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread; }
+
+// Arguments a step would reject, checked before a capture starts.
+int step_checks(mond_pm_t h, int n_iter, int warm) {
+  if (!h->cell && h->N > 0) return fail(h, MOND_ESTATE, "no particles bound");
+  if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
+  if (warm != MOND_WARM_NONE && warm != MOND_WARM_PREV) return fail(h, MOND_EINVAL, "step takes warm NONE or PREV");
+  if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
+  return MOND_OK;
+}
+
+// Enqueue the step on h->st while h->st is being captured into a graph.
+int capture_into(mond_pm_t h, double dt, int n_iter, int warm) { return step_direct(h, dt, n_iter, warm); }
+
+int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
+  if (!capturable(h->st)) return fail(h, MOND_ESTATE, "a captured step needs a non-default stream");
+  int rc = step_checks(h, n_iter, warm);
+  if (rc) return rc;
+  const mond_pm::GraphKey key{dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->N, h->cell};
+  if (!h->gexec || !(key == h->gkey)) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    const int64_t l0 = h->launches;
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+    rc = capture_into(h, dt, n_iter, warm);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->st, &g);  // always ends the capture
+    h->glaunches = h->launches - l0;
+    h->launches = l0;
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc ? rc : fail(h, MOND_ECUDA, "step capture: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->gexec = nullptr;
+      return fail(h, MOND_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    }
+    h->gkey = key;
+  }
+  CK(cudaGraphLaunch(h->gexec, h->st));
+  h->launches += h->glaunches;
+  return MOND_OK;
+}
+
+}  // namespace
+
+int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
+  if (!h) return MOND_EINVAL;
+  if (h->use_graph && !h->timing) return step_graph(h, dt, n_iter, warm);
+  return step_direct(h, dt, n_iter, warm);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent systems
+// ---------------------------------------------------------------------------
+struct mond_pm_batch {
+  std::vector<mond_pm_t> hs;
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec = nullptr;
+  double dt = 0;
+  int n_iter = -1, warm = -1;
+  std::vector<mond_pm::GraphKey> keys;
+  int64_t glaunches = 0, launches = 0;
+};
+
+int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_batch_t* out) {
+  if (!out || n < 1 || !handles) return MOND_EINVAL;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!capturable(st)) {
+    mond_pm_set_create_error("batch: a non-default stream is required");
+    return MOND_EINVAL;
+  }
+  for (int i = 0; i < n; i++) {
+    if (!handles[i] || !capturable(handles[i]->st) || handles[i]->st == st) {
+      mond_pm_set_create_error("batch: every handle needs its own non-default stream");
+      return MOND_EINVAL;
+    }
+    for (int j = 0; j < i; j++)
+      if (handles[j] == handles[i] || handles[j]->st == handles[i]->st) {
+        mond_pm_set_create_error("batch: handles and their streams must be distinct");
+        return MOND_EINVAL;
+      }
+  }
+  auto* b = new mond_pm_batch;
+  b->hs.assign(handles, handles + n);
+  b->st = st;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  b->join.assign(n, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    mond_pm_batch_destroy(b);
+    mond_pm_set_create_error("batch: event creation failed");
+    return MOND_ECUDA;
+  }
+  *out = b;
+  return MOND_OK;
+}
+
+int mond_pm_batch_destroy(mond_pm_batch_t b) {
+  if (!b) return MOND_EINVAL;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  delete b;
+  return MOND_OK;
+}
+
+int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, int warm) {
+  if (!b || n_steps < 0) return MOND_EINVAL;
+  const int n = (int)b->hs.size();
+  for (auto h : b->hs) {
+    const int rc = step_checks(h, n_iter, warm);
+    if (rc) return rc;
+  }
+  std::vector<mond_pm::GraphKey> keys;
+  for (auto h : b->hs)
+    keys.push_back({dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->N, h->cell});
+  bool same = b->gexec && keys.size() == b->keys.size();
+  for (size_t i = 0; same && i < keys.size(); i++) same = keys[i] == b->keys[i];
+  if (!same) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    // one graph: fork from the batch stream to every handle's stream, one step
+    // of each system on its own stream, join back
+    std::vector<int64_t> l0(n);
+    for (int i = 0; i < n; i++) l0[i] = b->hs[i]->launches;
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(b->hs[0], MOND_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+    int rc = MOND_OK;
+    e = cudaEventRecord(b->fork, b->st);
+    for (int i = 0; i < n && !rc && e == cudaSuccess; i++) {
+      mond_pm_t h = b->hs[i];
+      e = cudaStreamWaitEvent(h->st, b->fork, 0);
+      const int timing = h->timing;
+      h->timing = 0;  // no event timing inside a graph
+      if (e == cudaSuccess) rc = capture_into(h, dt, n_iter, warm);
+      h->timing = timing;
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], h->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->st, &g);
+    b->glaunches = 0;
+    for (int i = 0; i < n; i++) {
+      b->glaunches += b->hs[i]->launches - l0[i];
+      b->hs[i]->launches = l0[i];
+    }
+    if (rc || e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc) return rc;
+      return fail(b->hs[0], MOND_ECUDA, "batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->gexec = nullptr;
+      return fail(b->hs[0], MOND_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    b->keys = keys;
+  }
+  for (int k = 0; k < n_steps; k++) {
+    const cudaError_t e = cudaGraphLaunch(b->gexec, b->st);
+    if (e != cudaSuccess) return fail(b->hs[0], MOND_ECUDA, "batch graph launch: %s", cudaGetErrorString(e));
+  }
+  b->launches += b->glaunches * n_steps;
+  return MOND_OK;
+}
+
+int64_t mond_pm_batch_kernel_launches(mond_pm_batch_t b) { return b ? b->launches : -1; }
+
+int mond_pm_batch_sync(mond_pm_batch_t b) {
+  if (!b) return MOND_EINVAL;
+  const cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return fail(b->hs[0], MOND_ECUDA, "batch sync: %s", cudaGetErrorString(e));
+  for (auto h : b->hs) {
+    const int rc = read_status(h);
+    if (rc) return rc;
+  }
+  return MOND_OK;
+}
+
+// Per-handle choice of the work-item size and the pass variant: each candidate
+// is timed over a few steps of length zero (deposit, solve, gather and a push
+// that moves nothing), so the particle state is left exactly as it was.
+int mond_pm_autotune(mond_pm_t h, int n_iter, int trials, int64_t* chosen_chunk, int* chosen_pipelined) {
+  if (!h || trials < 1) return MOND_EINVAL;
+  int rc = step_checks(h, n_iter, MOND_WARM_NONE);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int timing = h->timing;
+  h->timing = 0;
+  float best = 1e30f;
+  int best_chunk = h->chunk, best_pipe = h->pipelined;
+  const int chunks[] = {512, 1024, 2048, 4096};
+  for (int pipe = 0; pipe < 2 && !rc; pipe++)
+    for (int c : chunks) {
+      h->pipelined = pipe;
+      h->chunk = c;
+      rc = step_direct(h, 0.0, n_iter, MOND_WARM_NONE);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, h->st);
+      for (int t = 0; t < trials && !rc; t++) rc = step_direct(h, 0.0, n_iter, MOND_WARM_NONE);
+      cudaEventRecord(e1, h->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!rc && ms < best) {
+        best = ms;
+        best_chunk = c;
+        best_pipe = pipe;
+      }
+    }
+  h->timing = timing;
+  h->chunk = best_chunk;
+  h->pipelined = best_pipe;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (chosen_chunk) *chosen_chunk = best_chunk;
+  if (chosen_pipelined) *chosen_pipelined = best_pipe;
+  return rc ? rc : read_status(h);
 }
 
 int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cell_host, float* offset_host,

@@ -10,7 +10,7 @@ namespace parts {
 constexpr int TILE = 8;       // mesh tile side: work items never span two tiles
 constexpr int DEP_NT = 256;   // threads per deposit CTA
 constexpr int GAT_NT = 256;   // threads per gather CTA
-constexpr int CHUNK = 2048;   // particles per work item
+constexpr int CHUNK = 2048;   // default particles per work item (runtime: the args' chunk)
 constexpr int QHALF = 32768;  // offset quantisation: q = round(offset * 2^16) + 32768
 constexpr int SCAN_B = 8192;  // elements per block of the key scan
 
@@ -34,6 +34,7 @@ struct BinArgs {
   int* bsum;         // per-block sums of the scan
   int* tile_start;   // ntile + 1
   int* chunk_start;  // ntile + 1
+  int chunk;         // particles per work item
   uint32_t* perm;
   uint32_t* status;
 };
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_tile_chunks(BinArgs a) {
   int s = 0;
   for (int t = t0; t < t1; t++) {
     int c = a.cstart[(int64_t)(t + 1) * 512] - a.cstart[(int64_t)t * 512];
-    s += (c + CHUNK - 1) / CHUNK;
+    s += (c + a.chunk - 1) / a.chunk;
   }
   int tot;
   int base = block_excl_scan(s, wsum, &tot);
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(1024) k_tile_chunks(BinArgs a) {
     int ts = a.cstart[(int64_t)t * 512], te = a.cstart[(int64_t)(t + 1) * 512];
     a.tile_start[t] = ts;
     a.chunk_start[t] = base;
-    base += (te - ts + CHUNK - 1) / CHUNK;
+    base += (te - ts + a.chunk - 1) / a.chunk;
   }
   if (threadIdx.x == 0) {
     a.tile_start[T] = a.cstart[a.ncell];
@@ -181,6 +182,7 @@ struct DepArgs {
   const uint32_t* perm;
   const int* tile_start;
   const int* chunk_start;
+  int chunk;  // particles per work item
   const uint32_t* lut;      // (65537) x (2r+1) words, row q + 32768
   const uint32_t* ball;     // packed (dx+r) | (dy+r) << 8 | (dz+r) << 16
   const int32_t* ball_lin;  // per tap: ((dz-r) n + (dy-r)) n + (dx-r)
@@ -362,8 +364,8 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
     if (it >= nitems) break;
     const int t = find_tile(a.chunk_start, a.ntile, it);
     const int ts = __ldg(a.tile_start + t), te = __ldg(a.tile_start + t + 1);
-    const int p0 = ts + (it - __ldg(a.chunk_start + t)) * CHUNK;
-    const int p1 = min(te, p0 + CHUNK);
+    const int p0 = ts + (it - __ldg(a.chunk_start + t)) * a.chunk;
+    const int p1 = min(te, p0 + a.chunk);
     const int tx = t % a.ntx, ty = (t / a.ntx) % a.ntx, tz = t / (a.ntx * a.ntx);
     const int ox = tx * TILE - a.r, oy = ty * TILE - a.r, oz = tz * TILE - a.r;
     const int len = (p1 - p0 + nw - 1) / nw;
@@ -409,6 +411,7 @@ struct GatArgs {
   const uint32_t* perm;
   const int* tile_start;
   const int* chunk_start;
+  int chunk;  // particles per work item
   const float* acc;       // 3 real planes
   const uint32_t* ball;
   const int32_t* ball_hlin;  // per tap: offset inside a tile plus its reach
@@ -536,8 +539,8 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
     if (it >= nitems) break;
     const int t = find_tile(a.chunk_start, a.ntile, it);
     const int ts = __ldg(a.tile_start + t), te = __ldg(a.tile_start + t + 1);
-    const int p0 = ts + (it - __ldg(a.chunk_start + t)) * CHUNK;
-    const int p1 = min(te, p0 + CHUNK);
+    const int p0 = ts + (it - __ldg(a.chunk_start + t)) * a.chunk;
+    const int p1 = min(te, p0 + a.chunk);
     const int tx = t % a.ntx, ty = (t / a.ntx) % a.ntx, tz = t / (a.ntx * a.ntx);
     const int ox = tx * TILE - a.r, oy = ty * TILE - a.r, oz = tz * TILE - a.r;
     const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
