@@ -198,6 +198,123 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args, dev):
+    """Learned warm start (sphere mixtures, 256^3, standard mu, sigma 1 px,
+    G = a0 = 1): train the FNO on solver-made pairs, then time and score
+    plain and surrogate-seeded solves on 1e7-particle mixtures."""
+    import torch
+
+    from paper_2312_02968_gb300 import binding as B
+    from paper_2312_02968_gb300 import surrogate as S
+    from paper_2312_02968_gb300 import train_surrogate as T
+
+    st = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    prev = torch.cuda.current_stream(dev)
+    torch.cuda.set_stream(st)
+    try:
+        h = B.MondPM(256, 1, 256.0, 1.0, 1.0, B.MU_STANDARD, 1.0, 10_000_000, stream=st)
+        net = S.FNO(*S.DEFAULT_SHAPE, seed=7, device=dev, stream=st)
+        tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 1e-3, seed0=1000, log=None)
+        ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000)
+        h.close()
+    finally:
+        torch.cuda.synchronize()
+        torch.cuda.set_stream(prev)
+    plain4 = ev["plain4"]
+    best = min((k for k in ev if k.startswith("guess")), key=lambda k: ev[k]["force_err_median"])
+    meets = [k for k in ev if ev[k]["force_err_median"] <= 1e-4]
+    fastest_meeting = min(meets, key=lambda k: ev[k]["ms_per_solve"]) if meets else None
+    return {"workload": "sphere mixtures (1-8 Plummer/Hernquist), 1e7 particles, 256^3, standard mu, sigma 1 px",
+            "fno": {"grid": 64, "width": 32, "modes": 16, "layers": 4, "weights": "bf16", "accumulate": "f32"},
+            "train": {k: tr[k] for k in ("pairs", "epochs", "batch", "lr", "s_pairs", "s_train")} |
+                     {"loss_first": tr["loss"][0], "loss_last": tr["loss"][-1]},
+            "solves": ev, "ref": "particle forces of the mean of iterates 40 and 41",
+            "guess1_vs_plain4_speed": plain4["ms_per_solve"] / ev["guess1"]["ms_per_solve"],
+            "best_guess": best, "fastest_at_1e-4": fastest_meeting}
+
+
+def run_ensemble(args, dev):
+    """Batched ensemble: independent systems with sides drawn from
+    {64, 96, 128, 192} and 1e4-1e6 particles (isothermal, deep mu, b = side/32;
+    or Plummer, standard mu, a = side/16), sigma 1 px, 4 iterations, stepped
+    together as one CUDA graph per step after per-system autotuning."""
+    import numpy as np
+    import torch
+
+    from paper_2312_02968_gb300 import binding as B
+    from paper_2312_02968_gb300 import workloads as W
+
+    rng = np.random.default_rng(7)
+    hs, keep, Ns, sides = [], [], [], []
+    t0 = time.time()
+    for _ in range(args.ensemble_systems):
+        n = int(rng.choice([64, 96, 128, 192]))
+        N = int(round(math.exp(rng.uniform(math.log(1e4), math.log(1e6)))))
+        kind = int(rng.integers(0, 2))
+        seed = int(rng.integers(1 << 30))
+        if kind == 0:
+            p, mu = W.isothermal(n, 1.0, N, n / 32, 0.4 * n, seed=seed), B.MU_DEEP
+        else:
+            p, mu = W.plummer(n, 1.0, N, n / 16, 0.4 * n, seed=seed), B.MU_STANDARD
+        st = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(st):
+            h = B.MondPM(n, 1, float(n), 1.0, 1.0, mu, 1.0, N, stream=st)
+            t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+        torch.cuda.synchronize()
+        h.bind_particles(*t)
+        hs.append(h)
+        keep.append(t)
+        Ns.append(N)
+        sides.append(n)
+    t_gen = time.time() - t0
+    t0 = time.time()
+    tuned = [B.autotune(h, 4, 2) for h in hs]
+    t_tune = time.time() - t0
+    batch = B.Batch(hs)
+    dt = 0.25
+    batch.step(dt, n_steps=2, n_iter=4)
+    batch.sync()
+    l0 = batch.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(batch.stream)
+    batch.step(dt, n_steps=args.ensemble_steps, n_iter=4)
+    e1.record(batch.stream)
+    e1.synchronize()
+    batch.sync()
+    ms = e0.elapsed_time(e1)
+    launches = batch.kernel_launches() - l0
+    sec = ms / 1000.0
+    # the same systems stepped one after another on one stream, for comparison
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    serial_steps = 2
+    torch.cuda.synchronize()
+    s0.record()
+    for h in hs:
+        for _ in range(serial_steps):
+            h.step(dt, 4, B.WARM_NONE)
+        # each handle runs on its own stream: wait before the next one starts
+        h.sync()
+    s1.record()
+    s1.synchronize()
+    serial_sps = len(hs) * serial_steps / (s0.elapsed_time(s1) / 1000.0)
+    batch.close()
+    for h in hs:
+        h.close()
+    chunks = {}
+    for c, pp in tuned:
+        key = f"chunk{c}_pipe{pp}"
+        chunks[key] = chunks.get(key, 0) + 1
+    return {"systems": len(hs), "sides": {str(k): sides.count(k) for k in sorted(set(sides))},
+            "particles": int(sum(Ns)), "steps": args.ensemble_steps, "ms": ms,
+            "system_steps_per_s": len(hs) * args.ensemble_steps / sec,
+            "particle_steps_per_s": sum(Ns) * args.ensemble_steps / sec,
+            "one_by_one_system_steps_per_s": serial_sps, "graph_launches_per_step": 1,
+            "kernel_launches": launches, "autotuned": chunks, "s_generate": t_gen, "s_autotune": t_tune}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +324,12 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the timed steps directly, not as a CUDA graph")
+    ap.add_argument("--learned-pairs", type=int, default=384, help="training pairs of the learned warm start (0: skip)")
+    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-eval", type=int, default=2, help="evaluation systems (1e7 particles each)")
+    ap.add_argument("--ensemble-systems", type=int, default=64, help="systems of the batched ensemble (0: skip)")
+    ap.add_argument("--ensemble-steps", type=int, default=20)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -248,18 +371,19 @@ def main():
     n, pad, N = WL["n"], WL["pad"], WL["N"]
     t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")}
     init = {k: v.clone() for k, v in t.items()}
-    h = B.MondPM(n, pad, WL["box"], WL["a0"], WL["G"], WL["mu"], WL["sigma"], N)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)  # torch's own copies below run in order with the handle's work
+    h = B.MondPM(n, pad, WL["box"], WL["a0"], WL["G"], WL["mu"], WL["sigma"], N, stream=stream)
     h.bind_particles(t["cell"], t["offset"], t["vel"], t["mass"])
-    stream = h.stream
     K, dt = WL["K"], WL["dt"]
+    h.set_option(B.OPT_USE_GRAPH, 0 if args.no_graph else 1)
 
     for _ in range(args.warmup):
         h.step(dt, K, B.WARM_NONE)
     h.sync()
 
-    # ---- timed region: plain 4-iteration steps --------------------------------
-    h.set_option(B.OPT_TIMING, 1)
-    h.kernel_stats()
+    # ---- timed region: plain 4-iteration steps (one CUDA graph per step) -------
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
@@ -275,6 +399,20 @@ def main():
     barrier()
     launches = h.kernel_launches() - l0
     ms = e0.elapsed_time(e1)
+    h.sync()
+
+    # ---- the same steps with every launch bracketed by CUDA events --------------
+    # (per-kernel durations for the roofline; direct launches, so a little slower)
+    h.set_option(B.OPT_TIMING, 1)
+    h.kernel_stats()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(args.steps):
+        h.step(dt, K, B.WARM_NONE)
+    k1.record(stream)
+    k1.synchronize()
+    ms_timed_mode = k0.elapsed_time(k1)
     stats = h.kernel_stats()
     h.set_option(B.OPT_TIMING, 0)
     h.sync()
@@ -347,6 +485,12 @@ def main():
         e2e_s = float(tt.item())
     e2e_value = world * args.steps / e2e_s
 
+    learned = ensemble = None
+    if rank == 0 and args.learned_pairs > 0:
+        learned = run_learned(args, dev)
+    if rank == 0 and args.ensemble_systems > 0:
+        ensemble = run_ensemble(args, dev)
+
     if rank == 0:
         peak, peak_src = load_peaks()
         hbm = [s for s in stats if s["name"].startswith(("xpass", "ypass", "zpass"))]
@@ -380,7 +524,9 @@ def main():
                 "accuracy": acc_info,
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 36 * N,
                         "d2h_bytes_per_step": 36 * N},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern}
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern,
+                "ms_per_step_event_timed": ms_timed_mode / args.steps,
+                "learned": learned, "ensemble": ensemble}
         if cpu:
             line["cpu_baseline"] = {"value": 1.0 / cpu["t_step"], "unit": "solves/s", "cores": cpu["cores"],
                                     "kind": "oracle",

@@ -205,13 +205,16 @@ int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm);
  * handle's stream, one mond_pm_step of each system on its own stream, and a
  * join back. The graph is captured on the first call and again whenever a
  * step argument, an option or a particle binding of any member changes.
- * Ownership: the handles stay owned by the caller and must outlive the batch;
- * each needs its own non-default stream, distinct from the batch stream. */
+ * The launches of each member are captured from a stream the batch owns for
+ * it, so the members are independent branches of the graph whatever streams
+ * the handles use; replays run on the batch stream, so a caller that also
+ * drives a member directly on its own stream synchronises in between.
+ * Ownership: the handles stay owned by the caller and must outlive the batch. */
 typedef struct mond_pm_batch* mond_pm_batch_t;
 
-/* Create a batch of n handles; stream: the batch's own non-default stream.
- * Errors: MOND_EINVAL (default streams, repeated handles or streams); the
- * text is in mond_pm_last_error(NULL). */
+/* Create a batch of n distinct handles; stream: the batch's non-default
+ * stream. Errors: MOND_EINVAL (a default stream, a null or repeated handle),
+ * MOND_ECUDA; the text is in mond_pm_last_error(NULL). */
 int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_batch_t* out);
 
 /* Enqueue n_steps graph launches of one step (deposit, solve_field(n_iter,

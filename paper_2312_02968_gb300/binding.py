@@ -295,8 +295,8 @@ def autotune(h: MondPM, n_iter: int = 4, trials: int = 3):
 
 class Batch:
     """Independent systems stepped together as one CUDA graph per step
-    (mond_pm_batch_*). Each handle needs its own stream; the batch has one
-    more. The handles stay owned by the caller."""
+    (mond_pm_batch_*), replayed on the batch's stream. The handles stay owned
+    by the caller; one that is also driven directly is synchronised first."""
 
     def __init__(self, handles, stream=None):
         import torch

@@ -1079,6 +1079,7 @@ int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
 struct mond_pm_batch {
   std::vector<mond_pm_t> hs;
   cudaStream_t st = nullptr;
+  std::vector<cudaStream_t> cs;  // one capture stream per member: independent graph branches
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   cudaGraphExec_t gexec = nullptr;
@@ -1097,13 +1098,13 @@ int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_
     return MOND_EINVAL;
   }
   for (int i = 0; i < n; i++) {
-    if (!handles[i] || !capturable(handles[i]->st) || handles[i]->st == st) {
-      mond_pm_set_create_error("batch: every handle needs its own non-default stream");
+    if (!handles[i]) {
+      mond_pm_set_create_error("batch: null handle");
       return MOND_EINVAL;
     }
     for (int j = 0; j < i; j++)
-      if (handles[j] == handles[i] || handles[j]->st == handles[i]->st) {
-        mond_pm_set_create_error("batch: handles and their streams must be distinct");
+      if (handles[j] == handles[i]) {
+        mond_pm_set_create_error("batch: repeated handle");
         return MOND_EINVAL;
       }
   }
@@ -1112,7 +1113,9 @@ int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_
   b->st = st;
   cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   b->join.assign(n, nullptr);
+  b->cs.assign(n, nullptr);
   for (int i = 0; i < n && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; i++) e = cudaStreamCreateWithFlags(&b->cs[i], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     mond_pm_batch_destroy(b);
     mond_pm_set_create_error("batch: event creation failed");
@@ -1129,6 +1132,8 @@ int mond_pm_batch_destroy(mond_pm_batch_t b) {
   if (b->fork) cudaEventDestroy(b->fork);
   for (auto e : b->join)
     if (e) cudaEventDestroy(e);
+  for (auto c : b->cs)
+    if (c) cudaStreamDestroy(c);
   delete b;
   return MOND_OK;
 }
@@ -1159,13 +1164,18 @@ int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, in
     int rc = MOND_OK;
     e = cudaEventRecord(b->fork, b->st);
     for (int i = 0; i < n && !rc && e == cudaSuccess; i++) {
+      // the member's launches are captured from the batch's own stream for it;
+      // a graph keeps only their order, so replays run independent branches
       mond_pm_t h = b->hs[i];
-      e = cudaStreamWaitEvent(h->st, b->fork, 0);
+      cudaStream_t own = h->st;
       const int timing = h->timing;
+      e = cudaStreamWaitEvent(b->cs[i], b->fork, 0);
+      h->st = b->cs[i];
       h->timing = 0;  // no event timing inside a graph
       if (e == cudaSuccess) rc = capture_into(h, dt, n_iter, warm);
       h->timing = timing;
-      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], h->st);
+      h->st = own;
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->cs[i]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join[i], 0);
     }
     cudaGraph_t g = nullptr;

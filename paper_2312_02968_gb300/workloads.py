@@ -110,6 +110,24 @@ def isothermal(n_f: int, s: float, N: int, b_px: float, r_max_px: float, seed: i
     return _pack(pos, vel, mass, n_f)
 
 
+def plummer(n_f: int, s: float, N: int, a_px: float, r_max_px: float, seed: int, M: float = 1.0):
+    """N equal-mass particles of a Plummer sphere of scale radius a_px pixels
+    centred on the domain, truncated at r_max_px (textbook inverse cumulative
+    mass M(r)/M = r^3/(r^2+a^2)^{3/2}); velocities zero (a cold start)."""
+    rng = np.random.default_rng(seed)
+    got = np.zeros((0, 3))
+    while got.shape[0] < N:
+        k = int((N - got.shape[0]) * 1.2) + 16
+        eta = np.clip(rng.uniform(0.0, 1.0, k), 1e-12, 1 - 1e-12)
+        r = a_px / np.sqrt(eta ** (-2.0 / 3.0) - 1.0)
+        u = rng.uniform(-1.0, 1.0, k)
+        ph = rng.uniform(0.0, 2 * math.pi, k)
+        su = np.sqrt(1 - u * u)
+        p = np.stack([su * np.cos(ph), su * np.sin(ph), u], 1) * r[:, None]
+        got = np.concatenate([got, p[r <= r_max_px]])
+    return _pack(got[:N], np.zeros((N, 3)), np.full(N, M / N), n_f)
+
+
 def mixture_spheres(n_f: int, seed: int, n_spheres=None):
     """Parameters of a mixture of 1-8 Plummer (kind 0) or Hernquist (kind 1)
     spheres: masses log-uniform over [1e-2, 1], scale radii uniform over
