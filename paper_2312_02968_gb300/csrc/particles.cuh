@@ -135,24 +135,31 @@ __global__ void k_bin_scatter(BinArgs a) {
   a.perm[a.cstart[k] + old - 1] = (uint32_t)i;
 }
 
-// Tile ranges and the exclusive scan of work chunks per tile (single CTA).
+// Tile ranges and work-item counts per tile, one thread per tile (the tile
+// starts sit 512 cells apart in the cell scan, so the reads are spread out).
+__global__ void k_tile_counts(BinArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.ntile) return;
+  const int ts = a.cstart[(int64_t)t * 512], te = a.cstart[(int64_t)(t + 1) * 512];
+  a.tile_start[t] = ts;
+  a.chunk_start[t] = (te - ts + a.chunk - 1) / a.chunk;
+}
+
+// Exclusive scan of the per-tile work-item counts in place (single CTA; each
+// thread owns a contiguous run of tiles).
 __global__ void __launch_bounds__(1024) k_tile_chunks(BinArgs a) {
   __shared__ int wsum[32];
   const int T = a.ntile;
   const int per = (T + 1023) / 1024;
   const int t0 = threadIdx.x * per, t1 = min(T, t0 + per);
   int s = 0;
-  for (int t = t0; t < t1; t++) {
-    int c = a.cstart[(int64_t)(t + 1) * 512] - a.cstart[(int64_t)t * 512];
-    s += (c + a.chunk - 1) / a.chunk;
-  }
+  for (int t = t0; t < t1; t++) s += a.chunk_start[t];
   int tot;
   int base = block_excl_scan(s, wsum, &tot);
   for (int t = t0; t < t1; t++) {
-    int ts = a.cstart[(int64_t)t * 512], te = a.cstart[(int64_t)(t + 1) * 512];
-    a.tile_start[t] = ts;
+    const int c = a.chunk_start[t];
     a.chunk_start[t] = base;
-    base += (te - ts + a.chunk - 1) / a.chunk;
+    base += c;
   }
   if (threadIdx.x == 0) {
     a.tile_start[T] = a.cstart[a.ncell];
@@ -232,6 +239,26 @@ struct LaneSlots {
   }
 };
 
+// The per-particle inputs a lane needs (index, cell, the offsets of its
+// axis-weight slots, mass bits), fetched one particle ahead so that their
+// global-memory latency overlaps the previous particle's taps.
+struct PartIn {
+  uint32_t i;
+  int c0, c1, c2;
+  float o[2];
+  uint32_t mb;
+  __device__ __forceinline__ void fetch(uint32_t idx, const int32_t* cell, const float* off, const float* mass,
+                                        const LaneSlots& ls) {
+    i = idx;
+    c0 = cell[3 * idx];
+    c1 = cell[3 * idx + 1];
+    c2 = cell[3 * idx + 2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) o[k] = ls.wl[k] != 0xFFFFFFFFu ? off[3 * idx + (ls.wl[k] >> 8)] : 0.f;
+    mb = mass ? __float_as_uint(__ldg(mass + idx)) : 0u;
+  }
+};
+
 // One warp deposits the particles [q0, q1): per particle the lanes build the
 // mass-folded x weights and the y.z row weights, then each lane evaluates the
 // taps t = lane + 32 j with one exact 32x32->64 product and a round-half-up
@@ -260,10 +287,15 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
                                               const TapRegs<TPL>& tr, DepWarp* sw) {
   const int lane = threadIdx.x & 31;
   const int w = 2 * a.r + 1;
+  if (q0 >= q1) return;
+  PartIn cur, nxt;
+  cur.fetch(__ldg(a.perm + q0), a.cell, a.off, a.mass, ls);
+  uint32_t i_next = q0 + 1 < q1 ? __ldg(a.perm + q0 + 1) : 0u;
   for (int p = q0; p < q1; p++) {
-    const uint32_t i = __ldg(a.perm + p);
-    const int c0 = __ldg(a.cell + 3 * i), c1 = __ldg(a.cell + 3 * i + 1), c2 = __ldg(a.cell + 3 * i + 2);
-    const uint32_t mb = __float_as_uint(__ldg(a.mass + i));
+    if (p + 1 < q1) nxt.fetch(i_next, a.cell, a.off, a.mass, ls);
+    if (p + 2 < q1) i_next = __ldg(a.perm + p + 2);
+    const int c0 = cur.c0, c1 = cur.c1, c2 = cur.c2;
+    const uint32_t mb = cur.mb;
     uint32_t msig;
     int e2;
     mass_parts(mb, &msig, &e2);
@@ -273,7 +305,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
     for (int k = 0; k < 2; k++) {
       if (ls.wl[k] != 0xFFFFFFFFu) {
         const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
-        const int q = __float2int_rn(__ldg(a.off + 3 * i + ax) * 65536.0f) + QHALF;
+        const int q = __float2int_rn(cur.o[k] * 65536.0f) + QHALF;
         sw->W[ax][j] = __ldg(a.lut + (int64_t)q * w + j);
       }
     }
@@ -322,6 +354,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
       }
     }
     __syncwarp();
+    cur = nxt;
   }
 }
 
@@ -436,17 +469,25 @@ struct GatWarp {
 // staged components, a warp sum gives Eq. gi, and lanes 0..2 kick and drift.
 template <int TPL>
 __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
-                                             const float* sa, int hv, const uint32_t* spk, const int32_t* shlin,
+                                             const float4* sa, const uint32_t* spk, const int32_t* shlin,
                                              const LaneSlots& ls, const TapRegs<TPL>& tr, GatWarp* sw) {
   const int lane = threadIdx.x & 31;
+  if (q0 >= q1) return;
+  // the cell and offset of particle i are rewritten (drift) only by this
+  // warp, after their last use, so reading them one particle ahead is safe
+  PartIn cur, nxt;
+  cur.fetch(__ldg(a.perm + q0), a.cell, a.off, nullptr, ls);
+  uint32_t i_next = q0 + 1 < q1 ? __ldg(a.perm + q0 + 1) : 0u;
   for (int p = q0; p < q1; p++) {
-    const uint32_t i = __ldg(a.perm + p);
-    const int c0 = a.cell[3 * i], c1 = a.cell[3 * i + 1], c2 = a.cell[3 * i + 2];
+    if (p + 1 < q1) nxt.fetch(i_next, a.cell, a.off, nullptr, ls);
+    if (p + 2 < q1) i_next = __ldg(a.perm + p + 2);
+    const uint32_t i = cur.i;
+    const int c0 = cur.c0, c1 = cur.c1, c2 = cur.c2;
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       if (ls.wl[k] != 0xFFFFFFFFu) {
         const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
-        const float u = (float)(j - a.r) - a.off[3 * i + ax];
+        const float u = (float)(j - a.r) - cur.o[k];
         sw->W[ax][j] = expf(-u * u * a.inv2s2) * a.gnorm;
       }
     }
@@ -462,20 +503,20 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
       for (int j = 0; j < TPL; j++) {
         if (tr.pk[j] != 0xFFFFFFFFu) {
           const float wgt = sw->WYZ[tr.pk[j] & 0xFF] * sw->W[0][tr.pk[j] >> 8];
-          const int idx = hbase + tr.hl[j];
-          gx = fmaf(wgt, sa[idx], gx);
-          gy = fmaf(wgt, sa[hv + idx], gy);
-          gz = fmaf(wgt, sa[2 * hv + idx], gz);
+          const float4 m = sa[hbase + tr.hl[j]];
+          gx = fmaf(wgt, m.x, gx);
+          gy = fmaf(wgt, m.y, gy);
+          gz = fmaf(wgt, m.z, gz);
         }
       }
     } else {
       for (int t = lane; t < a.nb; t += 32) {
         const uint32_t pk = spk[t];
         const float wgt = sw->WYZ[pk & 0xFF] * sw->W[0][pk >> 8];
-        const int idx = hbase + shlin[t];
-        gx = fmaf(wgt, sa[idx], gx);
-        gy = fmaf(wgt, sa[hv + idx], gy);
-        gz = fmaf(wgt, sa[2 * hv + idx], gz);
+        const float4 m = sa[hbase + shlin[t]];
+        gx = fmaf(wgt, m.x, gx);
+        gy = fmaf(wgt, m.y, gy);
+        gz = fmaf(wgt, m.z, gz);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -501,6 +542,7 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
       }
     }
     __syncwarp();
+    cur = nxt;
   }
 }
 
@@ -509,14 +551,14 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
 // wrap) in shared memory, one row per warp step, and gather from it.
 template <int TPL>
 __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
-  extern __shared__ float gsm[];
+  extern __shared__ __align__(16) float gsm[];
   __shared__ GatWarp sw[GAT_NT / 32];
   __shared__ int s_item;
   const int hw = TILE + 2 * a.r;
   const int hv = hw * hw * hw;
   const int w = 2 * a.r + 1;
-  float* sa = gsm;  // 3 x hv
-  uint32_t* spk = reinterpret_cast<uint32_t*>(gsm + 3 * hv);
+  float4* sa = reinterpret_cast<float4*>(gsm);  // hv cells, the three components interleaved
+  uint32_t* spk = reinterpret_cast<uint32_t*>(gsm + 4 * hv);
   int32_t* shlin = reinterpret_cast<int32_t*>(spk + a.nb);
   for (int t = threadIdx.x; t < a.nb; t += blockDim.x) {
     const uint32_t q = a.ball[t];
@@ -555,16 +597,14 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
       for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
         int gx = ox + lx;
         if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
-        const int k = row * hw + lx;
-        sa[k] = __ldg(a.acc + rbase + gx);
-        sa[hv + k] = __ldg(a.acc + n3 + rbase + gx);
-        sa[2 * hv + k] = __ldg(a.acc + 2 * n3 + rbase + gx);
+        sa[row * hw + lx] = make_float4(__ldg(a.acc + rbase + gx), __ldg(a.acc + n3 + rbase + gx),
+                                        __ldg(a.acc + 2 * n3 + rbase + gx), 0.f);
       }
     }
     __syncthreads();
     const int len = (p1 - p0 + nw - 1) / nw;
     const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
-    gather_range<TPL>(a, q0, q1, ox, oy, oz, hw, sa, hv, spk, shlin, ls, tr, sw + warp);
+    gather_range<TPL>(a, q0, q1, ox, oy, oz, hw, sa, spk, shlin, ls, tr, sw + warp);
   }
 }
 
