@@ -247,6 +247,17 @@ struct PartIn {
   int c0, c1, c2;
   float o[2];
   uint32_t mb;
+  uint32_t lw[2];  // deposit: the axis-table words of this lane's slots
+  // deposit: request the table words for the fetched offsets (q = round(2^16 o))
+  __device__ __forceinline__ void fetch_lut(const uint32_t* lut, int w, const LaneSlots& ls) {
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      if (ls.wl[k] != 0xFFFFFFFFu) {
+        const int q = __float2int_rn(o[k] * 65536.0f) + QHALF;
+        lw[k] = __ldg(lut + (int64_t)q * w + (ls.wl[k] & 0xFF));
+      }
+    }
+  }
   __device__ __forceinline__ void fetch(uint32_t idx, const int32_t* cell, const float* off, const float* mass,
                                         const LaneSlots& ls) {
     i = idx;
@@ -288,12 +299,17 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
   const int lane = threadIdx.x & 31;
   const int w = 2 * a.r + 1;
   if (q0 >= q1) return;
-  PartIn cur, nxt;
+  // three-stage software pipeline: particle p is deposited while the table
+  // words of p + 1 and the inputs of p + 2 are in flight
+  PartIn cur, nxt, nn;
   cur.fetch(__ldg(a.perm + q0), a.cell, a.off, a.mass, ls);
-  uint32_t i_next = q0 + 1 < q1 ? __ldg(a.perm + q0 + 1) : 0u;
+  cur.fetch_lut(a.lut, w, ls);
+  if (q0 + 1 < q1) nxt.fetch(__ldg(a.perm + q0 + 1), a.cell, a.off, a.mass, ls);
+  uint32_t i_nn = q0 + 2 < q1 ? __ldg(a.perm + q0 + 2) : 0u;
   for (int p = q0; p < q1; p++) {
-    if (p + 1 < q1) nxt.fetch(i_next, a.cell, a.off, a.mass, ls);
-    if (p + 2 < q1) i_next = __ldg(a.perm + p + 2);
+    if (p + 2 < q1) nn.fetch(i_nn, a.cell, a.off, a.mass, ls);
+    if (p + 3 < q1) i_nn = __ldg(a.perm + p + 3);
+    if (p + 1 < q1) nxt.fetch_lut(a.lut, w, ls);
     const int c0 = cur.c0, c1 = cur.c1, c2 = cur.c2;
     const uint32_t mb = cur.mb;
     uint32_t msig;
@@ -302,13 +318,8 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
     const bool neg = (mb >> 31) != 0;
     const int sh = 40 - a.kacc - e2;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-      if (ls.wl[k] != 0xFFFFFFFFu) {
-        const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
-        const int q = __float2int_rn(cur.o[k] * 65536.0f) + QHALF;
-        sw->W[ax][j] = __ldg(a.lut + (int64_t)q * w + j);
-      }
-    }
+    for (int k = 0; k < 2; k++)
+      if (ls.wl[k] != 0xFFFFFFFFu) sw->W[ls.wl[k] >> 8][ls.wl[k] & 0xFF] = cur.lw[k];
     __syncwarp();
     if (lane < w) sw->MX[lane] = fold_x(sw->W[0][lane], msig);
 #pragma unroll
@@ -355,6 +366,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
     }
     __syncwarp();
     cur = nxt;
+    nxt = nn;
   }
 }
 
