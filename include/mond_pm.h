@@ -89,7 +89,7 @@ enum {
   MOND_OPT_TIMING = 4,    /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
   MOND_OPT_PIPELINED = 5, /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
                              0: one tile per CTA with plain loads (same results) */
-  MOND_OPT_CHUNK = 6      /* particles per deposit/gather work item: a power of two in 256..16384
+  MOND_OPT_CHUNK = 6      /* particles per deposit/gather work item: a power of two in 256..4096
                              (default 2048; same results) */
 };
 

@@ -526,7 +526,7 @@ int taps_per_lane(int nb) {
 
 size_t dep_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(uint32_t) * 2 * (size_t)hw * hw * hw + sizeof(uint32_t) * 3 * h->nb;
+  return sizeof(uint32_t) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * 3 * h->nb;
 }
 size_t gat_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
@@ -889,8 +889,8 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_TRACK_DH: h->track_dh = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_USE_GRAPH: h->use_graph = value ? 1 : 0; return MOND_OK;
     case MOND_OPT_CHUNK:
-      if (value < 256 || value > 16384 || (value & (value - 1)))
-        return fail(h, MOND_EINVAL, "chunk must be a power of two in 256..16384");
+      if (value < 256 || value > 4096 || (value & (value - 1)))
+        return fail(h, MOND_EINVAL, "chunk must be a power of two in 256..4096");
       h->chunk = (int)value;
       return MOND_OK;
     case MOND_OPT_PIPELINED:

@@ -207,13 +207,17 @@ struct DepWarp {
   uint32_t R[15 * 15];
 };
 
-// 64-bit add into a shared accumulator held as two 32-bit words: the low
-// word's carry goes to the high word, so the pair sums exactly modulo 2^64.
-__device__ __forceinline__ void sadd64(uint32_t* lo, uint32_t* hi, int idx, uint64_t v) {
-  uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
-  uint32_t old = atomicAdd(lo + idx, vl);
-  vh += (old + vl < old) ? 1u : 0u;
-  if (vh) atomicAdd(hi + idx, vh);
+// 64-bit add into a shared accumulator held as three 32-bit words of 20-bit
+// digits, value = s0 + s1 2^20 + s2 2^40 (mod 2^64). The adds need no return
+// value (no carry chain); s0 and s1 take at most 4096 addends of < 2^20 each
+// without overflow (a work item holds at most 4096 particles and a particle
+// adds to a cell once), and s2 may wrap freely because s2 2^40 is only needed
+// modulo 2^64.
+__device__ __forceinline__ void sadd3(uint32_t* s0, uint32_t* s1, uint32_t* s2, int idx, uint64_t v) {
+  const uint32_t d0 = (uint32_t)v & 0xFFFFFu, d1 = (uint32_t)(v >> 20) & 0xFFFFFu, d2 = (uint32_t)(v >> 40);
+  atomicAdd(s0 + idx, d0);
+  if (d1) atomicAdd(s1 + idx, d1);
+  if (d2) atomicAdd(s2 + idx, d2);
 }
 
 __device__ __forceinline__ bool ball_inside(int c0, int c1, int c2, int r, int n) {
@@ -293,7 +297,7 @@ struct TapRegs {
 
 template <bool DENSE, int TPL>
 __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
-                                              uint32_t* slo, uint32_t* shi, const uint32_t* spk,
+                                              uint32_t* sd, int hv, const uint32_t* spk,
                                               const int32_t* slin, const int32_t* shlin, const LaneSlots& ls,
                                               const TapRegs<TPL>& tr, DepWarp* sw) {
   const int lane = threadIdx.x & 31;
@@ -334,7 +338,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
       for (int j = 0; j < TPL; j++) {
         if (tr.pk[j] != 0xFFFFFFFFu) {
           const uint64_t v = ((uint64_t)sw->R[tr.pk[j] & 0xFF] * sw->MX[tr.pk[j] >> 8] + rnd) >> sh;
-          sadd64(slo, shi, hbase + tr.hl[j], v);
+          sadd3(sd, sd + hv, sd + 2 * hv, hbase + tr.hl[j], v);
         }
       }
     } else {
@@ -346,7 +350,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
         if (neg) v = 0ull - v;
         if (v == 0ull) continue;
         if constexpr (DENSE) {
-          sadd64(slo, shi, hbase + shlin[t], v);
+          sadd3(sd, sd + hv, sd + 2 * hv, hbase + shlin[t], v);
         } else {
           int64_t gi;
           if (inside) {
@@ -383,9 +387,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
   const int hw = TILE + 2 * a.r;
   const int hv = hw * hw * hw;
   const int w = 2 * a.r + 1;
-  uint32_t* slo = dsm;
-  uint32_t* shi = dsm + hv;
-  uint32_t* spk = dsm + 2 * hv;
+  uint32_t* spk = dsm + 3 * hv;  // dsm[0, 3 hv): the digit planes of the tile accumulator
   int32_t* slin = reinterpret_cast<int32_t*>(spk + a.nb);
   int32_t* shlin = slin + a.nb;
   for (int t = threadIdx.x; t < a.nb; t += blockDim.x) {
@@ -417,9 +419,9 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
     const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
     const bool dense = (int64_t)(p1 - p0) * a.nb >= 2 * (int64_t)hv;
     if (dense) {
-      for (int k = threadIdx.x; k < 2 * hv; k += blockDim.x) dsm[k] = 0u;
+      for (int k = threadIdx.x; k < 3 * hv; k += blockDim.x) dsm[k] = 0u;
       __syncthreads();
-      deposit_range<true, TPL>(a, q0, q1, ox, oy, oz, hw, slo, shi, spk, slin, shlin, ls, tr, sw + warp);
+      deposit_range<true, TPL>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, tr, sw + warp);
       __syncthreads();
       const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
       // one halo row (fixed ly, lz) per warp step, lanes over x
@@ -432,7 +434,8 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
         }
         for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
           const int k = row * hw + lx;
-          const unsigned long long v = ((unsigned long long)shi[k] << 32) | slo[k];
+          const unsigned long long v = (unsigned long long)dsm[k] + ((unsigned long long)dsm[hv + k] << 20) +
+                                       ((unsigned long long)dsm[2 * hv + k] << 40);
           if (v == 0ull) continue;
           int gx = ox + lx;
           if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
         }
       }
     } else {
-      deposit_range<false, TPL>(a, q0, q1, ox, oy, oz, hw, slo, shi, spk, slin, shlin, ls, tr, sw + warp);
+      deposit_range<false, TPL>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, tr, sw + warp);
     }
   }
 }

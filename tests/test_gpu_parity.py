@@ -81,6 +81,26 @@ def test_deposit_dense_cluster_bit_exact(B):
     assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
 
 
+@pytest.mark.parametrize("chunk", [256, 4096])
+def test_deposit_dense_cells_signed_masses_bit_exact(B, chunk):
+    """Work items of up to 4096 particles piled into a few cells, masses of
+    both signs and spread exponents: the shared tile's digit planes must sum
+    exactly modulo 2^64."""
+    n = 32
+    rng = np.random.default_rng(17)
+    N = 12000
+    pos = rng.normal(0.0, 0.6, size=(N, 3))
+    cell, off = W.to_cells(pos, n)
+    mass = (rng.choice([-1.0, 1.0], N) * np.exp(rng.uniform(-6, 0, N)) / N).astype(np.float32)
+    p = {"cell": cell, "offset": off, "vel": np.zeros((N, 3), np.float32), "mass": mass}
+    h, _ = make(B, n, 1, p, 1.0)
+    h.set_option(B.OPT_CHUNK, chunk)
+    h.deposit()
+    acc, ka = h.get_deposit_acc()
+    ref, ka_ref, _ = oracle.deposit_fixed(n, 1.0, p["cell"], p["offset"], p["mass"])
+    assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+
+
 def test_deposit_edge_cases(B):
     n = 16
     # empty set
