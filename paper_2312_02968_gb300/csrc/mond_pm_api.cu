@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,6 +33,7 @@ struct Workspace {
   uint32_t* ball;
   int32_t* ball_lin;   // per tap: linear mesh offset of an interior ball
   int32_t* ball_hlin;  // per tap: linear offset inside a tile plus its reach
+  int32_t* rows;       // gather rows of the ball: [k] halo offset of the row centre, [nrows + k] wyz index | L << 16
   uint64_t* dep;
   float2* W;         // 3 spectral planes
   float2* A;         // 4 spectral planes
@@ -93,6 +95,7 @@ size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
   t.ball = (uint32_t*)take(sizeof(uint32_t) * nb);
   t.ball_lin = (int32_t*)take(sizeof(int32_t) * nb);
   t.ball_hlin = (int32_t*)take(sizeof(int32_t) * nb);
+  t.rows = (int32_t*)take(sizeof(int32_t) * 2 * (2 * r + 1) * (2 * r + 1));
   t.dep = (uint64_t*)take(sizeof(uint64_t) * n3);
   t.W = (float2*)take(sizeof(float2) * 3 * plane);
   t.A = (float2*)take(sizeof(float2) * 4 * plane);
@@ -222,7 +225,7 @@ struct TimedLaunch {
 struct mond_pm {
   int n, npad, nf;
   double box, s, a0, G, sigma;
-  int mu_kind, r, nb;
+  int mu_kind, r, nb, nrows = 0;
   int64_t maxp;
   cudaStream_t st;
   Workspace w;
@@ -530,7 +533,7 @@ size_t dep_smem(mond_pm* h) {
 }
 size_t gat_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(float) * 4 * (size_t)hw * hw * hw + sizeof(uint32_t) * 2 * h->nb;
+  return sizeof(float) * 4 * (size_t)hw * hw * hw;
 }
 
 template <typename K>
@@ -601,6 +604,8 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.acc = h->w.acc;
   g.ball = h->w.ball;
   g.ball_hlin = h->w.ball_hlin;
+  g.rows = h->w.rows;
+  g.nrows = h->nrows;
   g.g_out = g_out;
   g.dt = (float)dt;
   g.dt_over_s = (float)(dt / h->s);
@@ -615,11 +620,13 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   {
     // algorithmic bytes: the acceleration mesh once, particles read and written
     Timed tm(h, KC_GATHER, 3.0 * real_bytes(h) + 64.0 * h->N);
-    const int tpl = taps_per_lane(h->nb);
-    if (tpl == 3) CK(launch_smem(parts::k_gather_push<3>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
-    else if (tpl == 8) CK(launch_smem(parts::k_gather_push<8>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
-    else if (tpl == 28) CK(launch_smem(parts::k_gather_push<28>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
-    else CK(launch_smem(parts::k_gather_push<0>, h->sms * 4, parts::GAT_NT, sm, h->st, &g));
+    switch (h->r) {
+#define GATHER_R(R) \
+  case R: CK(launch_smem(parts::k_gather_push<R>, h->sms * 4, parts::GAT_NT, sm, h->st, &g)); break;
+      GATHER_R(2) GATHER_R(3) GATHER_R(4) GATHER_R(5) GATHER_R(6) GATHER_R(7)
+#undef GATHER_R
+      default: return fail(h, MOND_EINVAL, "no gather for reach %d", h->r);
+    }
   }
   CK(cudaGetLastError());
   return MOND_OK;
@@ -820,6 +827,24 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
     blin[t] = ((dz - h->r) * n + (dy - h->r)) * n + (dx - h->r);
     bhlin[t] = (dz * hw + dy) * hw + dx;
   }
+  // rows (dy, dz) of the ball for the gather, each with its x extent L
+  // (dx in [-L, L]); sorted by decreasing L and dealt to lanes round-robin
+  std::vector<std::pair<int, int>> rowv;  // (L, dy/dz code)
+  for (int dz = -h->r; dz <= h->r; dz++)
+    for (int dy = -h->r; dy <= h->r; dy++) {
+      int L = -1;
+      for (int dx = 0; dx <= h->r; dx++)
+        if ((double)(dx * dx + dy * dy + dz * dz) < lim) L = dx;
+      if (L >= 0) rowv.push_back({L, (dz + h->r) * 64 + (dy + h->r)});
+    }
+  std::stable_sort(rowv.begin(), rowv.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  h->nrows = (int)rowv.size();
+  std::vector<int32_t> rowt(2 * rowv.size());
+  for (size_t k = 0; k < rowv.size(); k++) {
+    const int dz = rowv[k].second / 64, dy = rowv[k].second % 64;  // both shifted by r
+    rowt[k] = (dz * hw + dy) * hw + h->r;
+    rowt[rowv.size() + k] = (dy * (2 * h->r + 1) + dz) | (rowv[k].first << 16);
+  }
   // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))
   const int lw = 2 * h->r + 1;
   std::vector<uint32_t> lut((size_t)65537 * lw);
@@ -856,6 +881,7 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
   e = e ? e : cudaMemcpyAsync(h->w.ball, ball.data(), sizeof(uint32_t) * ball.size(), cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.ball_lin, blin.data(), sizeof(int32_t) * h->nb, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.ball_hlin, bhlin.data(), sizeof(int32_t) * h->nb, cudaMemcpyHostToDevice, h->st);
+  e = e ? e : cudaMemcpyAsync(h->w.rows, rowt.data(), sizeof(int32_t) * rowt.size(), cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.kv, kv.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);
   e = e ? e : cudaMemcpyAsync(h->w.kp, kp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st);

@@ -463,6 +463,8 @@ struct GatArgs {
   const float* acc;       // 3 real planes
   const uint32_t* ball;
   const int32_t* ball_hlin;  // per tap: offset inside a tile plus its reach
+  const int32_t* rows;    // [k] halo offset of row k's centre, [nrows + k] wyz index | L << 16
+  int nrows;              // rows (dy, dz) of the ball
   float* g_out;           // optional [N][3] force output
   float dt;               // kick time step
   float dt_over_s;        // drift: offset += v dt / s
@@ -478,14 +480,18 @@ struct GatWarp {
   float WYZ[15 * 15];
 };
 
-// One warp gathers the particles [q0, q1) from the staged tile: per particle
-// the lanes build the x weights and the y.z row weights (FP32 exp), then each
-// lane sums its taps t = lane + 32 j as w = WYZ[row] W[x] times the three
-// staged components, a warp sum gives Eq. gi, and lanes 0..2 kick and drift.
-template <int TPL>
-__device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
-                                             const float4* sa, const uint32_t* spk, const int32_t* shlin,
-                                             const LaneSlots& ls, const TapRegs<TPL>& tr, GatWarp* sw) {
+// One warp gathers the particles [q0, q1) from the staged tile, row by row:
+// the ball is cut into rows (dy, dz), each spanning dx in [-L, L]; a lane owns
+// up to RPL rows (fixed per kernel). Per particle the lanes build the x weights
+// and the y.z row weights (FP32 exp); a lane then sums each of its rows with
+// the x weights held in registers, scales the row sum by its y.z weight, and a
+// warp sum gives Eq. gi. Lanes 0..2 kick and drift.
+template <int R>
+__device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
+                                            const float4* sa, const LaneSlots& ls, const int* roff,
+                                            const uint32_t* rinfo, GatWarp* sw) {
+  constexpr int W2 = 2 * R + 1;
+  constexpr int RPL = (W2 * W2 + 31) / 32;
   const int lane = threadIdx.x & 31;
   if (q0 >= q1) return;
   // the cell and offset of particle i are rewritten (drift) only by this
@@ -502,7 +508,7 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
     for (int k = 0; k < 2; k++) {
       if (ls.wl[k] != 0xFFFFFFFFu) {
         const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
-        const float u = (float)(j - a.r) - cur.o[k];
+        const float u = (float)(j - R) - cur.o[k];
         sw->W[ax][j] = expf(-u * u * a.inv2s2) * a.gnorm;
       }
     }
@@ -511,27 +517,30 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
     for (int k = 0; k < 8; k++)
       if (ls.rl[k] != 0xFFFFFFFFu) sw->WYZ[lane + 32 * k] = sw->W[1][ls.rl[k] >> 8] * sw->W[2][ls.rl[k] & 0xFF];
     __syncwarp();
-    const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if constexpr (TPL > 0) {
+    float wx[W2];
 #pragma unroll
-      for (int j = 0; j < TPL; j++) {
-        if (tr.pk[j] != 0xFFFFFFFFu) {
-          const float wgt = sw->WYZ[tr.pk[j] & 0xFF] * sw->W[0][tr.pk[j] >> 8];
-          const float4 m = sa[hbase + tr.hl[j]];
-          gx = fmaf(wgt, m.x, gx);
-          gy = fmaf(wgt, m.y, gy);
-          gz = fmaf(wgt, m.z, gz);
+    for (int t = 0; t < W2; t++) wx[t] = sw->W[0][t];
+    const int hbase = ((c2 - oz - R) * hw + (c1 - oy - R)) * hw + (c0 - ox - R);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int k = 0; k < RPL; k++) {
+      if (rinfo[k] != 0xFFFFFFFFu) {
+        const int L = (int)(rinfo[k] >> 16);
+        const float wyz = sw->WYZ[rinfo[k] & 0xFFFF];
+        const float4* row = sa + hbase + roff[k];  // dx = 0
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int t = -R; t <= R; t++) {
+          if ((t < 0 ? -t : t) <= L) {
+            const float4 m = row[t];
+            sx = fmaf(wx[t + R], m.x, sx);
+            sy = fmaf(wx[t + R], m.y, sy);
+            sz = fmaf(wx[t + R], m.z, sz);
+          }
         }
-      }
-    } else {
-      for (int t = lane; t < a.nb; t += 32) {
-        const uint32_t pk = spk[t];
-        const float wgt = sw->WYZ[pk & 0xFF] * sw->W[0][pk >> 8];
-        const float4 m = sa[hbase + shlin[t]];
-        gx = fmaf(wgt, m.x, gx);
-        gy = fmaf(wgt, m.y, gy);
-        gz = fmaf(wgt, m.z, gz);
+        gx = fmaf(wyz, sx, gx);
+        gy = fmaf(wyz, sy, gy);
+        gz = fmaf(wyz, sz, gz);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -563,28 +572,28 @@ __device__ __forceinline__ void gather_range(const GatArgs& a, int q0, int q1, i
 
 // Persistent gather: CTAs take work items (chunks of one tile) from a
 // counter, stage the acceleration mesh over the tile plus its reach (periodic
-// wrap) in shared memory, one row per warp step, and gather from it.
-template <int TPL>
+// wrap) in shared memory, one row per warp step, and gather from it. R is the
+// reach of the ball (r of the handle).
+template <int R>
 __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
+  constexpr int W2 = 2 * R + 1;
+  constexpr int RPL = (W2 * W2 + 31) / 32;
   extern __shared__ __align__(16) float gsm[];
   __shared__ GatWarp sw[GAT_NT / 32];
   __shared__ int s_item;
-  const int hw = TILE + 2 * a.r;
-  const int hv = hw * hw * hw;
-  const int w = 2 * a.r + 1;
-  float4* sa = reinterpret_cast<float4*>(gsm);  // hv cells, the three components interleaved
-  uint32_t* spk = reinterpret_cast<uint32_t*>(gsm + 4 * hv);
-  int32_t* shlin = reinterpret_cast<int32_t*>(spk + a.nb);
-  for (int t = threadIdx.x; t < a.nb; t += blockDim.x) {
-    const uint32_t q = a.ball[t];
-    spk[t] = (((q >> 8) & 0xFF) * w + ((q >> 16) & 0xFF)) | ((q & 0xFF) << 8);
-    shlin[t] = a.ball_hlin[t];
-  }
-  __syncthreads();
+  const int hw = TILE + 2 * R;
+  float4* sa = reinterpret_cast<float4*>(gsm);  // hw^3 cells, the three components interleaved
+  const int lane = threadIdx.x & 31;
   LaneSlots ls;
-  ls.init(threadIdx.x & 31, w);
-  TapRegs<TPL> tr;
-  tr.load(spk, shlin, a.nb, threadIdx.x & 31);
+  ls.init(lane, W2);
+  int roff[RPL];
+  uint32_t rinfo[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; k++) {
+    const int idx = lane + 32 * k;
+    roff[k] = idx < a.nrows ? __ldg(a.rows + idx) : 0;
+    rinfo[k] = idx < a.nrows ? (uint32_t)__ldg(a.rows + a.nrows + idx) : 0xFFFFFFFFu;
+  }
   const int nitems = __ldg(a.chunk_start + a.ntile);
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t n3 = (int64_t)a.n * a.n * a.n;
@@ -599,7 +608,7 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
     const int p0 = ts + (it - __ldg(a.chunk_start + t)) * a.chunk;
     const int p1 = min(te, p0 + a.chunk);
     const int tx = t % a.ntx, ty = (t / a.ntx) % a.ntx, tz = t / (a.ntx * a.ntx);
-    const int ox = tx * TILE - a.r, oy = ty * TILE - a.r, oz = tz * TILE - a.r;
+    const int ox = tx * TILE - R, oy = ty * TILE - R, oz = tz * TILE - R;
     const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
     for (int row = warp; row < hw * hw; row += nw) {
       const int ly = row % hw, lz = row / hw;
@@ -609,7 +618,7 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
         gz += gz < 0 ? a.n : (gz >= a.n ? -a.n : 0);
       }
       const int64_t rbase = ((int64_t)gz * a.n + gy) * a.n;
-      for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
+      for (int lx = lane; lx < hw; lx += 32) {
         int gx = ox + lx;
         if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
         sa[row * hw + lx] = make_float4(__ldg(a.acc + rbase + gx), __ldg(a.acc + n3 + rbase + gx),
@@ -619,7 +628,7 @@ __global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
     __syncthreads();
     const int len = (p1 - p0 + nw - 1) / nw;
     const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
-    gather_range<TPL>(a, q0, q1, ox, oy, oz, hw, sa, spk, shlin, ls, tr, sw + warp);
+    gather_rows<R>(a, q0, q1, ox, oy, oz, hw, sa, ls, roff, rinfo, sw + warp);
   }
 }
 
