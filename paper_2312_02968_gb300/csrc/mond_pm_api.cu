@@ -522,11 +522,6 @@ int do_bin(mond_pm* h) {
 // taps per lane kept in registers: the smallest instantiated width covering
 // the ball, 0 when it is too wide (the kernels then read the taps from shared
 // memory)
-int taps_per_lane(int nb) {
-  const int need = (nb + 31) / 32;
-  return need <= 3 ? 3 : need <= 8 ? 8 : need <= 28 ? 28 : 0;
-}
-
 size_t dep_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
   return sizeof(uint32_t) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * 3 * h->nb;
@@ -565,6 +560,8 @@ int do_deposit(mond_pm* h) {
   d.ball = h->w.ball;
   d.ball_lin = h->w.ball_lin;
   d.ball_hlin = h->w.ball_hlin;
+  d.rows = h->w.rows;
+  d.nrows = h->nrows;
   d.dep = h->w.dep;
   d.kacc = h->kacc;
   d.work_counter = h->w.counters;
@@ -573,11 +570,13 @@ int do_deposit(mond_pm* h) {
   {
     // algorithmic bytes: particle reads (perm, cell, offset, mass) and one int64 write per touched cell
     Timed tm(h, KC_DEPOSIT, 32.0 * h->N + 8.0 * h->n3);
-    const int tpl = taps_per_lane(h->nb);
-    if (tpl == 3) CK(launch_smem(parts::k_deposit<3>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
-    else if (tpl == 8) CK(launch_smem(parts::k_deposit<8>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
-    else if (tpl == 28) CK(launch_smem(parts::k_deposit<28>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
-    else CK(launch_smem(parts::k_deposit<0>, h->sms * 4, parts::DEP_NT, sm, h->st, &d));
+    switch (h->r) {
+#define DEPOSIT_R(R) \
+  case R: CK(launch_smem(parts::k_deposit<R>, h->sms * 4, parts::DEP_NT, sm, h->st, &d)); break;
+      DEPOSIT_R(2) DEPOSIT_R(3) DEPOSIT_R(4) DEPOSIT_R(5) DEPOSIT_R(6) DEPOSIT_R(7)
+#undef DEPOSIT_R
+      default: return fail(h, MOND_EINVAL, "no deposit for reach %d", h->r);
+    }
   }
   CK(cudaGetLastError());
   h->have_dep = true;

@@ -194,6 +194,8 @@ struct DepArgs {
   const uint32_t* ball;     // packed (dx+r) | (dy+r) << 8 | (dz+r) << 16
   const int32_t* ball_lin;  // per tap: ((dz-r) n + (dy-r)) n + (dx-r)
   const int32_t* ball_hlin; // per tap: ((dz+r') hw + (dy+r')) hw + (dx+r') with packed offsets
+  const int32_t* rows;      // [k] tile offset of row k's centre, [nrows + k] R index | L << 16
+  int nrows;                // rows (dy, dz) of the ball
   uint64_t* dep;
   int kacc;
   int* work_counter;  // persistent-grid work queue (zeroed before launch)
@@ -275,31 +277,20 @@ struct PartIn {
 };
 
 // One warp deposits the particles [q0, q1): per particle the lanes build the
-// mass-folded x weights and the y.z row weights, then each lane evaluates the
-// taps t = lane + 32 j with one exact 32x32->64 product and a round-half-up
-// shift, and adds the result to the shared tile (dense items) or to the global
-// accumulator (sparse items). Integer addition makes the order immaterial.
-// The taps a lane owns (t = lane + 32 j), held in registers when TPL > 0:
-// pk = y.z row index | x index << 8, and the tap's offset in the staged tile.
-template <int TPL>
-struct TapRegs {
-  uint32_t pk[TPL > 0 ? TPL : 1];
-  int32_t hl[TPL > 0 ? TPL : 1];
-  __device__ __forceinline__ void load(const uint32_t* spk, const int32_t* shlin, int nb, int lane) {
-#pragma unroll
-    for (int j = 0; j < TPL; j++) {
-      const int t = lane + 32 * j;
-      pk[j] = t < nb ? spk[t] : 0xFFFFFFFFu;
-      hl[j] = t < nb ? shlin[t] : 0;
-    }
-  }
-};
+// mass-folded x weights and the y.z row weights. Dense work items go row by
+// row through the ball (a lane owns up to RPL rows (dy, dz), the x weights in
+// registers): one exact 32x32->64 product and a round-half-up shift per tap,
+// added to the shared tile. Other items and rare rounding cases take the
+// generic per-tap loop into the shared tile or the global accumulator.
+// Integer addition makes the order immaterial.
 
-template <bool DENSE, int TPL>
+template <bool DENSE, int R>
 __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
                                               uint32_t* sd, int hv, const uint32_t* spk,
                                               const int32_t* slin, const int32_t* shlin, const LaneSlots& ls,
-                                              const TapRegs<TPL>& tr, DepWarp* sw) {
+                                              const int* roff, const uint32_t* rinfo, DepWarp* sw) {
+  constexpr int W2 = 2 * R + 1;
+  constexpr int RPL = (W2 * W2 + 31) / 32;
   const int lane = threadIdx.x & 31;
   const int w = 2 * a.r + 1;
   if (q0 >= q1) return;
@@ -331,14 +322,24 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
       if (ls.rl[k] != 0xFFFFFFFFu) sw->R[lane + 32 * k] = row_yz(sw->W[1][ls.rl[k] >> 8], sw->W[2][ls.rl[k] & 0xFF]);
     __syncwarp();
     const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
-    if (DENSE && TPL > 0 && sh > 0 && sh < 64 && !neg) {
-      // common case: exact product, round-half-up shift, split shared add
+    if (DENSE && sh > 0 && sh < 64 && !neg) {
+      // common case, row by row: the lane's rows (dy, dz) of the ball with the
+      // mass-folded x weights in registers; exact product, round-half-up
+      // shift, digit-plane shared add
       const uint64_t rnd = 1ull << (sh - 1);
+      uint32_t mx[W2];
 #pragma unroll
-      for (int j = 0; j < TPL; j++) {
-        if (tr.pk[j] != 0xFFFFFFFFu) {
-          const uint64_t v = ((uint64_t)sw->R[tr.pk[j] & 0xFF] * sw->MX[tr.pk[j] >> 8] + rnd) >> sh;
-          sadd3(sd, sd + hv, sd + 2 * hv, hbase + tr.hl[j], v);
+      for (int t = 0; t < W2; t++) mx[t] = sw->MX[t];
+#pragma unroll
+      for (int k = 0; k < RPL; k++) {
+        if (rinfo[k] != 0xFFFFFFFFu) {
+          const int L = (int)(rinfo[k] >> 16);
+          const uint64_t rw = sw->R[rinfo[k] & 0xFFFF];
+          const int base = hbase + roff[k];  // dx = 0
+#pragma unroll
+          for (int t = -R; t <= R; t++) {
+            if ((t < 0 ? -t : t) <= L) sadd3(sd, sd + hv, sd + 2 * hv, base + t, (rw * mx[t + R] + rnd) >> sh);
+          }
         }
       }
     } else {
@@ -379,7 +380,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
 // of the chunk. Dense items accumulate into a shared copy of the tile plus its
 // reach and add it to the global accumulator once; sparse items add to the
 // global accumulator directly.
-template <int TPL>
+template <int R>
 __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
   extern __shared__ uint32_t dsm[];
   __shared__ DepWarp sw[DEP_NT / 32];
@@ -399,8 +400,15 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
   __syncthreads();
   LaneSlots ls;
   ls.init(threadIdx.x & 31, w);
-  TapRegs<TPL> tr;
-  tr.load(spk, shlin, a.nb, threadIdx.x & 31);
+  constexpr int RPL = ((2 * R + 1) * (2 * R + 1) + 31) / 32;
+  int roff[RPL];
+  uint32_t rinfo[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; k++) {
+    const int idx = (threadIdx.x & 31) + 32 * k;
+    roff[k] = idx < a.nrows ? __ldg(a.rows + idx) : 0;
+    rinfo[k] = idx < a.nrows ? (uint32_t)__ldg(a.rows + a.nrows + idx) : 0xFFFFFFFFu;
+  }
   const int nitems = __ldg(a.chunk_start + a.ntile);
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   while (true) {
@@ -421,7 +429,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
     if (dense) {
       for (int k = threadIdx.x; k < 3 * hv; k += blockDim.x) dsm[k] = 0u;
       __syncthreads();
-      deposit_range<true, TPL>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, tr, sw + warp);
+      deposit_range<true, R>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
       __syncthreads();
       const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
       // one halo row (fixed ly, lz) per warp step, lanes over x
@@ -443,7 +451,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
         }
       }
     } else {
-      deposit_range<false, TPL>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, tr, sw + warp);
+      deposit_range<false, R>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
     }
   }
 }
