@@ -33,7 +33,7 @@ struct Workspace {
   uint32_t* ball;
   int32_t* ball_lin;   // per tap: linear mesh offset of an interior ball
   int32_t* ball_hlin;  // per tap: linear offset inside a tile plus its reach
-  int32_t* rows;       // gather rows of the ball: [k] halo offset of the row centre, [nrows + k] wyz index | L << 16
+  int32_t* rows;       // rows of the ball: [k] halo offset of the row centre, [nrows + k] dy | dz << 8 | L << 16
   uint64_t* dep;
   float2* W;         // 3 spectral planes
   float2* A;         // 4 spectral planes
@@ -842,7 +842,7 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
   for (size_t k = 0; k < rowv.size(); k++) {
     const int dz = rowv[k].second / 64, dy = rowv[k].second % 64;  // both shifted by r
     rowt[k] = (dz * hw + dy) * hw + h->r;
-    rowt[rowv.size() + k] = (dy * (2 * h->r + 1) + dz) | (rowv[k].first << 16);
+    rowt[rowv.size() + k] = dy | (dz << 8) | (rowv[k].first << 16);
   }
   // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))
   const int lw = 2 * h->r + 1;

@@ -194,7 +194,7 @@ struct DepArgs {
   const uint32_t* ball;     // packed (dx+r) | (dy+r) << 8 | (dz+r) << 16
   const int32_t* ball_lin;  // per tap: ((dz-r) n + (dy-r)) n + (dx-r)
   const int32_t* ball_hlin; // per tap: ((dz+r') hw + (dy+r')) hw + (dx+r') with packed offsets
-  const int32_t* rows;      // [k] tile offset of row k's centre, [nrows + k] R index | L << 16
+  const int32_t* rows;      // [k] tile offset of row k's centre, [nrows + k] dy | dz << 8 | L << 16 (shifted by r)
   int nrows;                // rows (dy, dz) of the ball
   uint64_t* dep;
   int kacc;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
       for (int k = 0; k < RPL; k++) {
         if (rinfo[k] != 0xFFFFFFFFu) {
           const int L = (int)(rinfo[k] >> 16);
-          const uint64_t rw = sw->R[rinfo[k] & 0xFFFF];
+          const uint64_t rw = sw->R[(rinfo[k] & 0xFF) * W2 + ((rinfo[k] >> 8) & 0xFF)];
           const int base = hbase + roff[k];  // dx = 0
 #pragma unroll
           for (int t = -R; t <= R; t++) {
@@ -471,7 +471,7 @@ struct GatArgs {
   const float* acc;       // 3 real planes
   const uint32_t* ball;
   const int32_t* ball_hlin;  // per tap: offset inside a tile plus its reach
-  const int32_t* rows;    // [k] halo offset of row k's centre, [nrows + k] wyz index | L << 16
+  const int32_t* rows;    // [k] halo offset of row k's centre, [nrows + k] dy | dz << 8 | L << 16 (shifted by r)
   int nrows;              // rows (dy, dz) of the ball
   float* g_out;           // optional [N][3] force output
   float dt;               // kick time step
@@ -484,16 +484,17 @@ struct GatArgs {
 };
 
 struct GatWarp {
-  float W[3][16];
-  float WYZ[15 * 15];
+  float W[2][3][16];  // axis weights of the two particles in flight
 };
 
-// One warp gathers the particles [q0, q1) from the staged tile, row by row:
-// the ball is cut into rows (dy, dz), each spanning dx in [-L, L]; a lane owns
-// up to RPL rows (fixed per kernel). Per particle the lanes build the x weights
-// and the y.z row weights (FP32 exp); a lane then sums each of its rows with
-// the x weights held in registers, scales the row sum by its y.z weight, and a
-// warp sum gives Eq. gi. Lanes 0..2 kick and drift.
+// One warp gathers the particles [q0, q1) from the staged tile, two at a time
+// and row by row: the ball is cut into rows (dy, dz), each spanning dx in
+// [-L, L]; a lane owns up to RPL rows (fixed per kernel). Per pair the lanes
+// build the axis weights (FP32 exp); a lane sums each of its rows with the x
+// weights in registers and scales the row sums by the y.z weights. When both
+// particles sit in the same cell (most of them, in dense regions) each staged
+// value is read once for both. Warp sums give Eq. gi; lanes 0..2 kick and
+// drift the first particle, lanes 3..5 the second.
 template <int R>
 __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
                                             const float4* sa, const LaneSlots& ls, const int* roff,
@@ -502,79 +503,115 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
   constexpr int RPL = (W2 * W2 + 31) / 32;
   const int lane = threadIdx.x & 31;
   if (q0 >= q1) return;
-  // the cell and offset of particle i are rewritten (drift) only by this
-  // warp, after their last use, so reading them one particle ahead is safe
-  PartIn cur, nxt;
-  cur.fetch(__ldg(a.perm + q0), a.cell, a.off, nullptr, ls);
-  uint32_t i_next = q0 + 1 < q1 ? __ldg(a.perm + q0 + 1) : 0u;
-  for (int p = q0; p < q1; p++) {
-    if (p + 1 < q1) nxt.fetch(i_next, a.cell, a.off, nullptr, ls);
-    if (p + 2 < q1) i_next = __ldg(a.perm + p + 2);
-    const uint32_t i = cur.i;
-    const int c0 = cur.c0, c1 = cur.c1, c2 = cur.c2;
+  // the cell and offset of a particle are rewritten (drift) only by this warp,
+  // after their last use, so reading them ahead is safe
+  PartIn pa, pb, na, nb;
+  pa.fetch(__ldg(a.perm + q0), a.cell, a.off, nullptr, ls);
+  if (q0 + 1 < q1) pb.fetch(__ldg(a.perm + q0 + 1), a.cell, a.off, nullptr, ls);
+  uint32_t ia = q0 + 2 < q1 ? __ldg(a.perm + q0 + 2) : 0u, ib = q0 + 3 < q1 ? __ldg(a.perm + q0 + 3) : 0u;
+  for (int p = q0; p < q1; p += 2) {
+    const bool two = p + 1 < q1;
+    if (p + 2 < q1) na.fetch(ia, a.cell, a.off, nullptr, ls);
+    if (p + 3 < q1) nb.fetch(ib, a.cell, a.off, nullptr, ls);
+    if (p + 4 < q1) ia = __ldg(a.perm + p + 4);
+    if (p + 5 < q1) ib = __ldg(a.perm + p + 5);
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       if (ls.wl[k] != 0xFFFFFFFFu) {
         const int ax = ls.wl[k] >> 8, j = ls.wl[k] & 0xFF;
-        const float u = (float)(j - R) - cur.o[k];
-        sw->W[ax][j] = expf(-u * u * a.inv2s2) * a.gnorm;
+        const float ua = (float)(j - R) - pa.o[k];
+        sw->W[0][ax][j] = expf(-ua * ua * a.inv2s2) * a.gnorm;
+        const float ub = (float)(j - R) - pb.o[k];
+        sw->W[1][ax][j] = two ? expf(-ub * ub * a.inv2s2) * a.gnorm : 0.f;
       }
     }
     __syncwarp();
+    float wxa[W2], wxb[W2];
 #pragma unroll
-    for (int k = 0; k < 8; k++)
-      if (ls.rl[k] != 0xFFFFFFFFu) sw->WYZ[lane + 32 * k] = sw->W[1][ls.rl[k] >> 8] * sw->W[2][ls.rl[k] & 0xFF];
-    __syncwarp();
-    float wx[W2];
-#pragma unroll
-    for (int t = 0; t < W2; t++) wx[t] = sw->W[0][t];
-    const int hbase = ((c2 - oz - R) * hw + (c1 - oy - R)) * hw + (c0 - ox - R);
-    float gx = 0.f, gy = 0.f, gz = 0.f;
+    for (int t = 0; t < W2; t++) {
+      wxa[t] = sw->W[0][0][t];
+      wxb[t] = sw->W[1][0][t];
+    }
+    const bool same = !two || (pb.c0 == pa.c0 && pb.c1 == pa.c1 && pb.c2 == pa.c2);
+    const int ha = ((pa.c2 - oz - R) * hw + (pa.c1 - oy - R)) * hw + (pa.c0 - ox - R);
+    const int hb = two ? ((pb.c2 - oz - R) * hw + (pb.c1 - oy - R)) * hw + (pb.c0 - ox - R) : ha;
+    float gax = 0.f, gay = 0.f, gaz = 0.f, gbx = 0.f, gby = 0.f, gbz = 0.f;
 #pragma unroll
     for (int k = 0; k < RPL; k++) {
       if (rinfo[k] != 0xFFFFFFFFu) {
-        const int L = (int)(rinfo[k] >> 16);
-        const float wyz = sw->WYZ[rinfo[k] & 0xFFFF];
-        const float4* row = sa + hbase + roff[k];  // dx = 0
-        float sx = 0.f, sy = 0.f, sz = 0.f;
+        const int L = (int)(rinfo[k] >> 16), dy = rinfo[k] & 0xFF, dz = (rinfo[k] >> 8) & 0xFF;
+        const float wyza = sw->W[0][1][dy] * sw->W[0][2][dz];
+        const float wyzb = sw->W[1][1][dy] * sw->W[1][2][dz];
+        float sax = 0.f, say = 0.f, saz = 0.f, sbx = 0.f, sby = 0.f, sbz = 0.f;
+        const float4* ra = sa + ha + roff[k];  // dx = 0
+        if (same) {
 #pragma unroll
-        for (int t = -R; t <= R; t++) {
-          if ((t < 0 ? -t : t) <= L) {
-            const float4 m = row[t];
-            sx = fmaf(wx[t + R], m.x, sx);
-            sy = fmaf(wx[t + R], m.y, sy);
-            sz = fmaf(wx[t + R], m.z, sz);
+          for (int t = -R; t <= R; t++) {
+            if ((t < 0 ? -t : t) <= L) {
+              const float4 m = ra[t];
+              sax = fmaf(wxa[t + R], m.x, sax);
+              say = fmaf(wxa[t + R], m.y, say);
+              saz = fmaf(wxa[t + R], m.z, saz);
+              sbx = fmaf(wxb[t + R], m.x, sbx);
+              sby = fmaf(wxb[t + R], m.y, sby);
+              sbz = fmaf(wxb[t + R], m.z, sbz);
+            }
+          }
+        } else {
+          const float4* rb = sa + hb + roff[k];
+#pragma unroll
+          for (int t = -R; t <= R; t++) {
+            if ((t < 0 ? -t : t) <= L) {
+              const float4 m = ra[t], n = rb[t];
+              sax = fmaf(wxa[t + R], m.x, sax);
+              say = fmaf(wxa[t + R], m.y, say);
+              saz = fmaf(wxa[t + R], m.z, saz);
+              sbx = fmaf(wxb[t + R], n.x, sbx);
+              sby = fmaf(wxb[t + R], n.y, sby);
+              sbz = fmaf(wxb[t + R], n.z, sbz);
+            }
           }
         }
-        gx = fmaf(wyz, sx, gx);
-        gy = fmaf(wyz, sy, gy);
-        gz = fmaf(wyz, sz, gz);
+        gax = fmaf(wyza, sax, gax);
+        gay = fmaf(wyza, say, gay);
+        gaz = fmaf(wyza, saz, gaz);
+        gbx = fmaf(wyzb, sbx, gbx);
+        gby = fmaf(wyzb, sby, gby);
+        gbz = fmaf(wyzb, sbz, gbz);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      gx += __shfl_xor_sync(0xffffffffu, gx, o);
-      gy += __shfl_xor_sync(0xffffffffu, gy, o);
-      gz += __shfl_xor_sync(0xffffffffu, gz, o);
+      gax += __shfl_xor_sync(0xffffffffu, gax, o);
+      gay += __shfl_xor_sync(0xffffffffu, gay, o);
+      gaz += __shfl_xor_sync(0xffffffffu, gaz, o);
+      gbx += __shfl_xor_sync(0xffffffffu, gbx, o);
+      gby += __shfl_xor_sync(0xffffffffu, gby, o);
+      gbz += __shfl_xor_sync(0xffffffffu, gbz, o);
     }
-    if (lane < 3) {
-      const float g = lane == 0 ? gx : (lane == 1 ? gy : gz);
-      if (a.g_out) a.g_out[3 * i + lane] = g;
+    if (lane < 3 || (two && lane < 6)) {
+      const bool first = lane < 3;
+      const int ax = first ? lane : lane - 3;
+      const PartIn& q = first ? pa : pb;
+      const uint32_t i = q.i;
+      const float g = first ? (ax == 0 ? gax : (ax == 1 ? gay : gaz)) : (ax == 0 ? gbx : (ax == 1 ? gby : gbz));
+      if (a.g_out) a.g_out[3 * i + ax] = g;
       if (!isfinite(g)) set_status(a.status, ST_NAN);
       if (a.do_kick) {
-        const float v = a.vel[3 * i + lane] + g * a.dt;
-        a.vel[3 * i + lane] = v;
+        const float v = a.vel[3 * i + ax] + g * a.dt;
+        a.vel[3 * i + ax] = v;
         if (a.do_drift) {
-          const float o = a.off[3 * i + lane] + v * a.dt_over_s;
+          const float o = a.off[3 * i + ax] + v * a.dt_over_s;
           const float sh = floorf(o + 0.5f);
-          int c = (lane == 0 ? c0 : (lane == 1 ? c1 : c2)) + (int)sh;
+          int c = (ax == 0 ? q.c0 : (ax == 1 ? q.c1 : q.c2)) + (int)sh;
           c += c < 0 ? a.n : (c >= a.n ? -a.n : 0);
-          a.off[3 * i + lane] = o - sh;
-          a.cell[3 * i + lane] = c;
+          a.off[3 * i + ax] = o - sh;
+          a.cell[3 * i + ax] = c;
         }
       }
     }
     __syncwarp();
-    cur = nxt;
+    pa = na;
+    pb = nb;
   }
 }
 
@@ -583,7 +620,7 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
 // wrap) in shared memory, one row per warp step, and gather from it. R is the
 // reach of the ball (r of the handle).
 template <int R>
-__global__ void __launch_bounds__(GAT_NT) k_gather_push(GatArgs a) {
+__global__ void __launch_bounds__(GAT_NT, 2) k_gather_push(GatArgs a) {
   constexpr int W2 = 2 * R + 1;
   constexpr int RPL = (W2 * W2 + 31) / 32;
   extern __shared__ __align__(16) float gsm[];
