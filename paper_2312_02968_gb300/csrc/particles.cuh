@@ -218,7 +218,7 @@ struct DepWarp {
 __device__ __forceinline__ void sadd3(uint32_t* s0, uint32_t* s1, uint32_t* s2, int idx, uint64_t v) {
   const uint32_t d0 = (uint32_t)v & 0xFFFFFu, d1 = (uint32_t)(v >> 20) & 0xFFFFFu, d2 = (uint32_t)(v >> 40);
   atomicAdd(s0 + idx, d0);
-  if (d1) atomicAdd(s1 + idx, d1);
+  atomicAdd(s1 + idx, d1);  // unconditional: a zero add is cheaper than a divergent branch
   if (d2) atomicAdd(s2 + idx, d2);
 }
 
