@@ -214,7 +214,8 @@ def run_learned(args, dev):
     torch.cuda.set_stream(st)
     try:
         h = B.MondPM(256, 1, 256.0, 1.0, 1.0, B.MU_STANDARD, 1.0, 10_000_000, stream=st)
-        net = S.FNO(*S.DEFAULT_SHAPE, seed=7, device=dev, stream=st)
+        shape = tuple(int(v) for v in args.learned_fno.split(","))
+        net = S.FNO(*shape, seed=7, device=dev, stream=st)
         tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 1e-3, seed0=1000, log=None)
         ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000)
         h.close()
@@ -226,7 +227,8 @@ def run_learned(args, dev):
     meets = [k for k in ev if ev[k]["force_err_median"] <= 1e-4]
     fastest_meeting = min(meets, key=lambda k: ev[k]["ms_per_solve"]) if meets else None
     return {"workload": "sphere mixtures (1-8 Plummer/Hernquist), 1e7 particles, 256^3, standard mu, sigma 1 px",
-            "fno": {"grid": 64, "width": 32, "modes": 16, "layers": 4, "weights": "bf16", "accumulate": "f32"},
+            "fno": {"grid": shape[0], "width": shape[1], "modes": shape[2], "layers": shape[3], "weights": "bf16",
+                    "accumulate": "f32"},
             "train": {k: tr[k] for k in ("pairs", "epochs", "batch", "lr", "s_pairs", "s_train")} |
                      {"loss_first": tr["loss"][0], "loss_last": tr["loss"][-1]},
             "solves": ev, "ref": "particle forces of the mean of iterates 40 and 41",
@@ -328,6 +330,7 @@ def main():
     ap.add_argument("--learned-pairs", type=int, default=384, help="training pairs of the learned warm start (0: skip)")
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--learned-eval", type=int, default=2, help="evaluation systems (1e7 particles each)")
+    ap.add_argument("--learned-fno", default="32,32,16,4", help="network grid side, width, modes, layers")
     ap.add_argument("--ensemble-systems", type=int, default=64, help="systems of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20)
     args = ap.parse_args()

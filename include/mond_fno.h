@@ -69,9 +69,12 @@ int mond_fno_loss(int64_t count, const float* y, const float* t, float* dy, floa
                   void* stream);
 
 /* Adam step on all parameters: params -= lr mhat / (sqrt(vhat) + eps);
- * m, v float32 moments; step = 1, 2, ...; grad is cleared afterwards. */
+ * m, v float32 moments; step = 1, 2, ...; grad is cleared afterwards. When
+ * clip_norm > 0 the gradient is first scaled by min(1, clip_norm / |grad|);
+ * a gradient with a non-finite norm is dropped (parameters and moments keep
+ * their values). scratch: one device double. */
 int mond_fno_adam(int64_t count, float* params, float* grad, float* m, float* v, float lr, float beta1, float beta2,
-                  float eps, int step, void* stream);
+                  float eps, int step, float clip_norm, double* scratch, void* stream);
 
 /* Network input from a fine Newtonian field: g_N [3][N^3] (N = f n) is
  * averaged over f^3 blocks to the coarse grid and normalised: x [4][n^3].

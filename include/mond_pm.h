@@ -167,8 +167,9 @@ int mond_pm_set_density(mond_pm_t h, const float* rho);
  * (H = 0), MOND_WARM_PREV (H of the previous solve), MOND_WARM_GUESS
  * (H_guess: device float32, 3 planes; it is projected onto its
  * divergence-free part first) or MOND_WARM_GUESS_RAW (H_guess used as
- * given). With a warm start the last iteration also completes the H update
- * so the next solve can start from it. The Newtonian field is computed once
+ * given, once: the H state is left as it was). With MOND_WARM_PREV or
+ * MOND_WARM_GUESS the last iteration also completes the H update so the next
+ * solve can start from it. The Newtonian field is computed once
  * per density: a solve on the density of the previous solve (no deposit or
  * mond_pm_set_density in between) starts from the stored g_N.
  * 0 <= n_iter <= 64. */

@@ -88,7 +88,7 @@ SIGNATURES.update({
     "mond_fno_forward": (_I, [FnoShape, _P, _P, _P, _P, _P]),
     "mond_fno_backward": (_I, [FnoShape, _P, _P, _P, _P, _P, _P]),
     "mond_fno_loss": (_I, [_I64, _P, _P, _P, _F, _P, _P]),
-    "mond_fno_adam": (_I, [_I64, _P, _P, _P, _P, _F, _F, _F, _F, _I, _P]),
+    "mond_fno_adam": (_I, [_I64, _P, _P, _P, _P, _F, _F, _F, _F, _I, _F, _P, _P]),
     "mond_fno_input": (_I, [_I, _I, _F, _P, _P, _P, _P]),
     "mond_fno_output": (_I, [_I, _I, _P, _P, _P, _P]),
     "mond_fno_coarsen": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),

@@ -573,9 +573,19 @@ __global__ void k_loss(const float* y, const float* t, float* dy, int64_t n, con
 }
 
 __global__ void k_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float c1, float c2, float clip, const double* sumsq) {
+  float scale = 1.f;
+  if (sumsq) {
+    const double norm = sqrt(*sumsq);
+    if (!isfinite(norm)) {  // drop the step, keep parameters and moments
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = 0.f;
+      return;
+    }
+    if (clip > 0.f && norm > clip) scale = (float)(clip / norm);
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = g[i] * scale;
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -919,10 +929,13 @@ int mond_fno_loss(int64_t count, const float* y, const float* t, float* dy, floa
 }
 
 int mond_fno_adam(int64_t count, float* p, float* g, float* m, float* v, float lr, float b1, float b2, float eps,
-                  int step, void* stream) {
-  if (!p || !g || !m || !v || count <= 0 || step < 1) return -1;
+                  int step, float clip_norm, double* scratch, void* stream) {
+  if (!p || !g || !m || !v || count <= 0 || step < 1 || !scratch) return -1;
+  cudaStream_t st = (cudaStream_t)stream;
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-  k_adam<<<grid_stride(count), TB, 0, (cudaStream_t)stream>>>(count, p, g, m, v, lr, b1, b2, eps, c1, c2);
+  cudaMemsetAsync(scratch, 0, sizeof(double), st);
+  k_sumsq<<<grid_stride(count), TB, 0, st>>>(g, count, scratch);
+  k_adam<<<grid_stride(count), TB, 0, st>>>(count, p, g, m, v, lr, b1, b2, eps, c1, c2, clip_norm, scratch);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

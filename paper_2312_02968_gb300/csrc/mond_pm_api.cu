@@ -717,7 +717,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       xi.spec = A;
       xi.real_out = h->w.acc;
       PK(xpass(h, passes::X_INV, xi));
-      if (warm == MOND_WARM_NONE) break;
+      if (warm == MOND_WARM_NONE || warm == MOND_WARM_GUESS_RAW) break;  // no H state to carry on
     }
     PK(zpass(h, passes::Z_CURL, W, W, 3));
     PK(ypass(h, +1, W, 3));

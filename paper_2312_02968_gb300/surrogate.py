@@ -59,6 +59,7 @@ class FNO:
         self.ws = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device=self.device)
         self.ws_ptr = ctypes.c_void_p((self.ws.data_ptr() + 255) & ~255)
         self.loss_acc = torch.zeros(2, dtype=torch.float64, device=self.device)
+        self.adam_scratch = torch.zeros(1, dtype=torch.float64, device=self.device)
         self.steps = 0
         self.init(seed)
 
@@ -92,15 +93,18 @@ class FNO:
         _check(lib().mond_fno_loss(int(y.numel()), _p(y), _p(t), _p(dy), float(weight), _p(self.loss_acc),
                                    self._st), "loss")
 
-    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, clip=0.0):
+        """One Adam step; clip > 0 caps the gradient norm; a non-finite
+        gradient is dropped."""
         self.steps += 1
         _check(lib().mond_fno_adam(self.count, _p(self.params), _p(self.grad), _p(self.m), _p(self.v), float(lr),
-                                   float(b1), float(b2), float(eps), self.steps, self._st), "adam")
+                                   float(b1), float(b2), float(eps), self.steps, float(clip), _p(self.adam_scratch),
+                                   self._st), "adam")
         self.cast()
 
     # ----------------------------------------------------------- training
     def train(self, xs, ts, epochs: int, batch: int, lr: float, seed: int = 0, lr_final: float | None = None,
-              log=None):
+              log=None, clip: float = 5.0):
         """Adam on the relative squared error over pairs xs [P, 4, n^3], ts
         [P, 3, n^3] (device); cosine-decayed learning rate. Returns the mean
         loss of each epoch."""
@@ -123,7 +127,7 @@ class FNO:
                     self.loss(y, ts[i], dy, 1.0 / batch)
                     self.backward(xs[i], dy)
                 cur = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / max(1, total - 1)))
-                self.adam(cur)
+                self.adam(cur, clip=clip)
                 it += 1
             hist.append(float(self.loss_acc[0].item()) / nb)
             if log:

@@ -216,7 +216,8 @@ def test_warm_start_matches_oracle(B, warm):
             H0 = guess.astype(np.float64)
     ref = oracle_fields(p, n, sigma, mu, 1, H0=H0, finish=True)
     assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
-    assert rel(h.get_field(B.FIELD_H).cpu().numpy(), ref["H"], scale=ref["gN"]) < TOL
+    if warm != "guess_raw":  # a raw guess is used once and leaves no H state
+        assert rel(h.get_field(B.FIELD_H).cpu().numpy(), ref["H"], scale=ref["gN"]) < TOL
 
 
 def test_newton_field_reused_within_one_density(B):
