@@ -216,7 +216,7 @@ def run_learned(args, dev):
         h = B.MondPM(256, 1, 256.0, 1.0, 1.0, B.MU_STANDARD, 1.0, 10_000_000, stream=st)
         shape = tuple(int(v) for v in args.learned_fno.split(","))
         net = S.FNO(*shape, seed=7, device=dev, stream=st)
-        tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 1e-3, seed0=1000, log=None)
+        tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 7e-4, seed0=1000, log=None)
         ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000)
         h.close()
     finally:
@@ -327,8 +327,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps directly, not as a CUDA graph")
-    ap.add_argument("--learned-pairs", type=int, default=384, help="training pairs of the learned warm start (0: skip)")
-    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-pairs", type=int, default=1024, help="training pairs of the learned warm start (0: skip)")
+    ap.add_argument("--learned-epochs", type=int, default=12)
     ap.add_argument("--learned-eval", type=int, default=2, help="evaluation systems (1e7 particles each)")
     ap.add_argument("--learned-fno", default="32,32,16,4", help="network grid side, width, modes, layers")
     ap.add_argument("--ensemble-systems", type=int, default=64, help="systems of the batched ensemble (0: skip)")
