@@ -524,11 +524,11 @@ int do_bin(mond_pm* h) {
 // memory)
 size_t dep_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(uint32_t) * 3 * (size_t)hw * hw * hw + sizeof(uint32_t) * 3 * h->nb;
+  return sizeof(uint32_t) * 3 * (size_t)hw * hw * (hw + 1) + sizeof(uint32_t) * 3 * h->nb;
 }
 size_t gat_smem(mond_pm* h) {
   int hw = parts::TILE + 2 * h->r;
-  return sizeof(float) * 4 * (size_t)hw * hw * hw;
+  return sizeof(float) * 4 * (size_t)hw * hw * (hw + 1);
 }
 
 template <typename K>
@@ -824,7 +824,7 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
   for (int t = 0; t < h->nb; t++) {
     int dx = ball[t] & 0xFF, dy = (ball[t] >> 8) & 0xFF, dz = (ball[t] >> 16) & 0xFF;
     blin[t] = ((dz - h->r) * n + (dy - h->r)) * n + (dx - h->r);
-    bhlin[t] = (dz * hw + dy) * hw + dx;
+    bhlin[t] = (dz * hw + dy) * (hw + 1) + dx;  // tiles are staged with an odd x pitch hw + 1
   }
   // rows (dy, dz) of the ball for the gather, each with its x extent L
   // (dx in [-L, L]); sorted by decreasing L and dealt to lanes round-robin
@@ -841,7 +841,7 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
   std::vector<int32_t> rowt(2 * rowv.size());
   for (size_t k = 0; k < rowv.size(); k++) {
     const int dz = rowv[k].second / 64, dy = rowv[k].second % 64;  // both shifted by r
-    rowt[k] = (dz * hw + dy) * hw + h->r;
+    rowt[k] = (dz * hw + dy) * (hw + 1) + h->r;
     rowt[rowv.size() + k] = dy | (dz << 8) | (rowv[k].first << 16);
   }
   // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))

@@ -285,7 +285,7 @@ struct PartIn {
 // Integer addition makes the order immaterial.
 
 template <bool DENSE, int R>
-__device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
+__device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, int ox, int oy, int oz, int hw, int px,
                                               uint32_t* sd, int hv, const uint32_t* spk,
                                               const int32_t* slin, const int32_t* shlin, const LaneSlots& ls,
                                               const int* roff, const uint32_t* rinfo, DepWarp* sw) {
@@ -321,7 +321,7 @@ __device__ __forceinline__ void deposit_range(const DepArgs& a, int q0, int q1, 
     for (int k = 0; k < 8; k++)
       if (ls.rl[k] != 0xFFFFFFFFu) sw->R[lane + 32 * k] = row_yz(sw->W[1][ls.rl[k] >> 8], sw->W[2][ls.rl[k] & 0xFF]);
     __syncwarp();
-    const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * hw + (c0 - ox - a.r);
+    const int hbase = ((c2 - oz - a.r) * hw + (c1 - oy - a.r)) * px + (c0 - ox - a.r);
     if (DENSE && sh > 0 && sh < 64 && !neg) {
       // common case, row by row: the lane's rows (dy, dz) of the ball with the
       // mass-folded x weights in registers; exact product, round-half-up
@@ -386,7 +386,8 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
   __shared__ DepWarp sw[DEP_NT / 32];
   __shared__ int s_item;
   const int hw = TILE + 2 * a.r;
-  const int hv = hw * hw * hw;
+  const int px = hw + 1;  // odd x pitch of the staged tile: rows of different lanes spread over the banks
+  const int hv = hw * hw * px;
   const int w = 2 * a.r + 1;
   uint32_t* spk = dsm + 3 * hv;  // dsm[0, 3 hv): the digit planes of the tile accumulator
   int32_t* slin = reinterpret_cast<int32_t*>(spk + a.nb);
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
     if (dense) {
       for (int k = threadIdx.x; k < 3 * hv; k += blockDim.x) dsm[k] = 0u;
       __syncthreads();
-      deposit_range<true, R>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
+      deposit_range<true, R>(a, q0, q1, ox, oy, oz, hw, px, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
       __syncthreads();
       const bool inside = ox >= 0 && oy >= 0 && oz >= 0 && ox + hw <= a.n && oy + hw <= a.n && oz + hw <= a.n;
       // one halo row (fixed ly, lz) per warp step, lanes over x
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
           gz += gz < 0 ? a.n : (gz >= a.n ? -a.n : 0);
         }
         for (int lx = threadIdx.x & 31; lx < hw; lx += 32) {
-          const int k = row * hw + lx;
+          const int k = row * px + lx;
           const unsigned long long v = (unsigned long long)dsm[k] + ((unsigned long long)dsm[hv + k] << 20) +
                                        ((unsigned long long)dsm[2 * hv + k] << 40);
           if (v == 0ull) continue;
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit(DepArgs a) {
         }
       }
     } else {
-      deposit_range<false, R>(a, q0, q1, ox, oy, oz, hw, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
+      deposit_range<false, R>(a, q0, q1, ox, oy, oz, hw, px, dsm, hv, spk, slin, shlin, ls, roff, rinfo, sw + warp);
     }
   }
 }
@@ -496,7 +497,7 @@ struct GatWarp {
 // value is read once for both. Warp sums give Eq. gi; lanes 0..2 kick and
 // drift the first particle, lanes 3..5 the second.
 template <int R>
-__device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw,
+__device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw, int px,
                                             const float4* sa, const LaneSlots& ls, const int* roff,
                                             const uint32_t* rinfo, GatWarp* sw) {
   constexpr int W2 = 2 * R + 1;
@@ -533,8 +534,8 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
       wxb[t] = sw->W[1][0][t];
     }
     const bool same = !two || (pb.c0 == pa.c0 && pb.c1 == pa.c1 && pb.c2 == pa.c2);
-    const int ha = ((pa.c2 - oz - R) * hw + (pa.c1 - oy - R)) * hw + (pa.c0 - ox - R);
-    const int hb = two ? ((pb.c2 - oz - R) * hw + (pb.c1 - oy - R)) * hw + (pb.c0 - ox - R) : ha;
+    const int ha = ((pa.c2 - oz - R) * hw + (pa.c1 - oy - R)) * px + (pa.c0 - ox - R);
+    const int hb = two ? ((pb.c2 - oz - R) * hw + (pb.c1 - oy - R)) * px + (pb.c0 - ox - R) : ha;
     float gax = 0.f, gay = 0.f, gaz = 0.f, gbx = 0.f, gby = 0.f, gbz = 0.f;
 #pragma unroll
     for (int k = 0; k < RPL; k++) {
@@ -627,6 +628,7 @@ __global__ void __launch_bounds__(GAT_NT, 2) k_gather_push(GatArgs a) {
   __shared__ GatWarp sw[GAT_NT / 32];
   __shared__ int s_item;
   const int hw = TILE + 2 * R;
+  const int px = hw + 1;  // odd x pitch of the staged tile: rows of different lanes spread over the banks
   float4* sa = reinterpret_cast<float4*>(gsm);  // hw^3 cells, the three components interleaved
   const int lane = threadIdx.x & 31;
   LaneSlots ls;
@@ -666,14 +668,14 @@ __global__ void __launch_bounds__(GAT_NT, 2) k_gather_push(GatArgs a) {
       for (int lx = lane; lx < hw; lx += 32) {
         int gx = ox + lx;
         if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
-        sa[row * hw + lx] = make_float4(__ldg(a.acc + rbase + gx), __ldg(a.acc + n3 + rbase + gx),
+        sa[row * px + lx] = make_float4(__ldg(a.acc + rbase + gx), __ldg(a.acc + n3 + rbase + gx),
                                         __ldg(a.acc + 2 * n3 + rbase + gx), 0.f);
       }
     }
     __syncthreads();
     const int len = (p1 - p0 + nw - 1) / nw;
     const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
-    gather_rows<R>(a, q0, q1, ox, oy, oz, hw, sa, ls, roff, rinfo, sw + warp);
+    gather_rows<R>(a, q0, q1, ox, oy, oz, hw, px, sa, ls, roff, rinfo, sw + warp);
   }
 }
 
