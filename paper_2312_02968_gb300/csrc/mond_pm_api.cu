@@ -33,7 +33,8 @@ struct Workspace {
   uint32_t* ball;
   int32_t* ball_lin;   // per tap: linear mesh offset of an interior ball
   int32_t* ball_hlin;  // per tap: linear offset inside a tile plus its reach
-  int32_t* rows;       // rows of the ball: [k] halo offset of the row centre, [nrows + k] dy | dz << 8 | L << 16
+  int32_t* rows;       // rows of the ball, two orders (deposit, gather) of nrows each:
+                       // [k] tile offset of the row centre, [nrows + k] dy | dz << 8 | L << 16
   uint64_t* dep;
   float2* W;         // 3 spectral planes
   float2* A;         // 4 spectral planes
@@ -95,7 +96,7 @@ size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
   t.ball = (uint32_t*)take(sizeof(uint32_t) * nb);
   t.ball_lin = (int32_t*)take(sizeof(int32_t) * nb);
   t.ball_hlin = (int32_t*)take(sizeof(int32_t) * nb);
-  t.rows = (int32_t*)take(sizeof(int32_t) * 2 * (2 * r + 1) * (2 * r + 1));
+  t.rows = (int32_t*)take(sizeof(int32_t) * 4 * (2 * r + 1) * (2 * r + 1));
   t.dep = (uint64_t*)take(sizeof(uint64_t) * n3);
   t.W = (float2*)take(sizeof(float2) * 3 * plane);
   t.A = (float2*)take(sizeof(float2) * 4 * plane);
@@ -603,7 +604,7 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.acc = h->w.acc;
   g.ball = h->w.ball;
   g.ball_hlin = h->w.ball_hlin;
-  g.rows = h->w.rows;
+  g.rows = h->w.rows + 2 * h->nrows;  // the gather's order
   g.nrows = h->nrows;
   g.g_out = g_out;
   g.dt = (float)dt;
@@ -826,23 +827,52 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
     blin[t] = ((dz - h->r) * n + (dy - h->r)) * n + (dx - h->r);
     bhlin[t] = (dz * hw + dy) * (hw + 1) + dx;  // tiles are staged with an odd x pitch hw + 1
   }
-  // rows (dy, dz) of the ball for the gather, each with its x extent L
-  // (dx in [-L, L]); sorted by decreasing L and dealt to lanes round-robin
-  std::vector<std::pair<int, int>> rowv;  // (L, dy/dz code)
+  // rows (dy, dz) of the ball, each with its x extent L (dx in [-L, L]), for
+  // the row-wise deposit and gather: row k + 32 j goes to lane k. Two orders:
+  // the deposit's by decreasing L (lanes of a group have rows of similar
+  // length, so fewer predicated-off atomics); the gather's picks the 32 rows
+  // of each group with distinct tile offsets modulo 32 words where possible,
+  // so that the lanes' 16-byte loads at a given dx spread over the banks.
+  struct BallRow {
+    int L, dy, dz, off;  // dy, dz shifted by r; off = tile offset of dx = 0
+  };
+  std::vector<BallRow> all;
   for (int dz = -h->r; dz <= h->r; dz++)
     for (int dy = -h->r; dy <= h->r; dy++) {
       int L = -1;
       for (int dx = 0; dx <= h->r; dx++)
         if ((double)(dx * dx + dy * dy + dz * dz) < lim) L = dx;
-      if (L >= 0) rowv.push_back({L, (dz + h->r) * 64 + (dy + h->r)});
+      if (L < 0) continue;
+      all.push_back({L, dy + h->r, dz + h->r, ((dz + h->r) * hw + (dy + h->r)) * (hw + 1) + h->r});
     }
-  std::stable_sort(rowv.begin(), rowv.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-  h->nrows = (int)rowv.size();
-  std::vector<int32_t> rowt(2 * rowv.size());
-  for (size_t k = 0; k < rowv.size(); k++) {
-    const int dz = rowv[k].second / 64, dy = rowv[k].second % 64;  // both shifted by r
-    rowt[k] = (dz * hw + dy) * (hw + 1) + h->r;
-    rowt[rowv.size() + k] = dy | (dz << 8) | (rowv[k].first << 16);
+  const int nrows = (int)all.size();
+  std::vector<BallRow> dep_order = all;
+  std::stable_sort(dep_order.begin(), dep_order.end(), [](const BallRow& a, const BallRow& b) { return a.L > b.L; });
+  std::vector<std::vector<BallRow>> bucket(32);
+  for (const auto& b : all) bucket[b.off % 32].push_back(b);
+  std::vector<BallRow> gat_order;
+  while ((int)gat_order.size() < nrows) {
+    int taken = 0;  // one group: a row from each non-empty residue class in turn, then any
+    for (int b = 0; b < 32 && taken < 32; b++)
+      if (!bucket[b].empty()) {
+        gat_order.push_back(bucket[b].back());
+        bucket[b].pop_back();
+        taken++;
+      }
+    for (int b = 0; b < 32 && taken < 32; b++)
+      while (!bucket[b].empty() && taken < 32) {
+        gat_order.push_back(bucket[b].back());
+        bucket[b].pop_back();
+        taken++;
+      }
+  }
+  h->nrows = nrows;
+  std::vector<int32_t> rowt(4 * nrows);  // deposit: [0, 2n), gather: [2n, 4n)
+  for (int k = 0; k < nrows; k++) {
+    rowt[k] = dep_order[k].off;
+    rowt[nrows + k] = dep_order[k].dy | (dep_order[k].dz << 8) | (dep_order[k].L << 16);
+    rowt[2 * nrows + k] = gat_order[k].off;
+    rowt[3 * nrows + k] = gat_order[k].dy | (gat_order[k].dz << 8) | (gat_order[k].L << 16);
   }
   // per-axis lookup table of the Gaussian (Sect. 3.1): round(2^24 g1((j - r) - q/2^16))
   const int lw = 2 * h->r + 1;
