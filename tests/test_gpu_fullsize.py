@@ -84,3 +84,43 @@ def test_fullsize_graph_step_sample(setup):
     pos = t[0].cpu().numpy()[idx] + t[1].cpu().numpy()[idx].astype(np.float64)
     d = np.abs(((pos - pos_ref) + N_MESH / 2) % N_MESH - N_MESH / 2)
     assert d.max() < 1e-4
+
+
+def test_ring_config_at_512_against_eq_ringforce():
+    """The largest supported mesh with the ring configuration of Sect. 4.2
+    (central mass 1, 1e5 ring particles of total mass 0.1 at 64 px, sigma
+    1 px, deep mu, K = 4): the ring particles' mean radial acceleration
+    against Eq. ringforce, the tangential part against zero and the central
+    body's force against the self-force level (properties the oracle pins at
+    smaller sizes)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2312_02968_gb300 import binding as B
+
+    n, N, m0, ring_mass, r2 = 512, 100_000, 1.0, 0.1, 64.0
+    p, meta = W.ring(n, 1.0, N, m0, ring_mass, r2)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        h = B.MondPM(n, 1, float(n), 1.0, 1.0, B.MU_DEEP, 1.0, N + 1, stream=st)
+        t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+    torch.cuda.synchronize()
+    h.bind_particles(*t)
+    h.deposit()
+    h.solve_field(4)
+    gt = h.gather()
+    h.sync()
+    g = gt.cpu().numpy().astype(np.float64)
+    m, M = meta["m"], meta["M"]
+    F2 = 2.0 / (3 * N * r2) * (M ** 1.5 - m0 ** 1.5 - N * m ** 1.5)
+    pos = (p["cell"][1:] - n / 2 + p["offset"][1:]).astype(np.float64)
+    rhat = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    radial = -(g[1:] * rhat).sum(1)
+    tang = np.linalg.norm(g[1:] + radial[:, None] * rhat, axis=1)
+    assert abs(np.mean(radial) / (F2 / m) - 1) < 0.05
+    assert np.mean(tang) < 0.02 * np.mean(radial)
+    # the ring's pulls on the central body cancel; what is left is the mesh
+    # self-force, about 1.08e-3 sqrt(G m0 a0)/s for sigma = 1 px (Sect. 4)
+    assert np.linalg.norm(g[0]) < 2e-3
