@@ -82,10 +82,14 @@ int mond_fno_adam(int64_t count, float* params, float* grad, float* m, float* v,
  * RMS of the coarse g_N); scale_out[2..3] are scratch. */
 int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* scale_out, void* stream);
 
-/* Fine field from a coarse network output: H [3][N^3] = s * trilinear
- * upsampling (periodic, cell centred) of y [3][n^3]; s read from scale.
- * N must be a multiple of n and of 16. */
-int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* stream);
+/* Fine field from a coarse network output: H [3][N^3] = s * cubic-convolution
+ * upsampling (Keys, a = -1/2; periodic, cell centred; one axis at a time) of
+ * y [3][n^3]; s read from scale. N must be a multiple of n. scratch: device
+ * memory of mond_fno_output_scratch_bytes(N, n) bytes. */
+int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* scratch, void* stream);
+
+/* Scratch bytes mond_fno_output needs (0 if N is not a multiple of n). */
+size_t mond_fno_output_scratch_bytes(int N, int n);
 
 /* Means of f^3 blocks of a fine field: fine [ncomp][N^3] -> coarse
  * [ncomp][n^3]. When fine2 is not NULL the blocks of (fine + fine2)/2 are

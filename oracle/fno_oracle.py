@@ -24,8 +24,9 @@ Pins (tests/test_fno_oracle.py): the truncated transform against a brute-force
 DFT sum; the spectral layer as the identity on band-limited fields; gradients
 against central differences; bfloat16 rounding on hand-worked values and
 against torch's conversion; GELU against the erf form; Adam's first step in
-closed form; block means and trilinear upsampling on constant and linear
-fields; the sphere-mixture density against the closed-form enclosed masses.
+closed form; block means and cubic-convolution upsampling on constant,
+linear and quadratic fields; the sphere-mixture density against the
+closed-form enclosed masses.
 """
 from __future__ import annotations
 
@@ -247,25 +248,31 @@ def features(gN_fine: np.ndarray, n: int, a0: float):
     return x, s
 
 
+def cubic_weights(u):
+    """Cubic convolution (Keys, a = -1/2) weights of the taps -1, 0, 1, 2 at
+    fraction u in [0, 1); they sum to 1 and reproduce quadratics."""
+    u = np.asarray(u, np.float64)
+    return np.stack([((-u + 2) * u - 1) * u / 2, ((3 * u - 5) * u * u + 2) / 2, ((-3 * u + 4) * u + 1) * u / 2,
+                     (u - 1) * u * u / 2])
+
+
 def upsample(y: np.ndarray, N: int, scale: float) -> np.ndarray:
-    """Periodic trilinear interpolation of a cell-centred coarse field onto
-    the fine cell centres, times scale: [c][n]^3 -> [c][N]^3."""
+    """Periodic cubic-convolution interpolation of a cell-centred coarse field
+    onto the fine cell centres, times scale: [c][n]^3 -> [c][N]^3."""
     c, n = y.shape[0], y.shape[1]
     f = N // n
     u = (np.arange(N) + 0.5) / f - 0.5
     i0 = np.floor(u).astype(np.int64)
-    w = u - i0
+    w = cubic_weights(u - i0)  # [4][N]
     out = np.zeros((c, N, N, N))
-    for dz in (0, 1):
-        wz = (w if dz else 1 - w)[:, None, None]
-        iz = np.mod(i0 + dz, n)
-        for dy_ in (0, 1):
-            wy = (w if dy_ else 1 - w)[None, :, None]
-            iy = np.mod(i0 + dy_, n)
-            for dx in (0, 1):
-                wx = (w if dx else 1 - w)[None, None, :]
-                ix = np.mod(i0 + dx, n)
-                out += y[:, iz][:, :, iy][:, :, :, ix] * (wz * wy * wx)[None]
+    for a in range(4):
+        iz = np.mod(i0 + a - 1, n)
+        for b in range(4):
+            iy = np.mod(i0 + b - 1, n)
+            for d in range(4):
+                ix = np.mod(i0 + d - 1, n)
+                wt = w[a][:, None, None] * w[b][None, :, None] * w[d][None, None, :]
+                out += y[:, iz][:, :, iy][:, :, :, ix] * wt[None]
     return scale * out
 
 

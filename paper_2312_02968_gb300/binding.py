@@ -90,7 +90,8 @@ SIGNATURES.update({
     "mond_fno_loss": (_I, [_I64, _P, _P, _P, _F, _P, _P]),
     "mond_fno_adam": (_I, [_I64, _P, _P, _P, _P, _F, _F, _F, _F, _I, _F, _P, _P]),
     "mond_fno_input": (_I, [_I, _I, _F, _P, _P, _P, _P]),
-    "mond_fno_output": (_I, [_I, _I, _P, _P, _P, _P]),
+    "mond_fno_output": (_I, [_I, _I, _P, _P, _P, _P, _P]),
+    "mond_fno_output_scratch_bytes": (ctypes.c_size_t, [_I, _I]),
     "mond_fno_coarsen": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
     "mond_fno_mixture_density": (_I, [_I, _D, _I, _P, _P, _P, _P, _F, _P, _P]),
 })

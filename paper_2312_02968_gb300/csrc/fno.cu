@@ -673,46 +673,58 @@ __global__ void k_input(int n, float a0, const float* g, const double* sumsq, fl
   }
 }
 
-// Trilinear, periodic, cell-centred upsampling times the scale. A CTA covers
-// OUT_ROWS fine rows (c, Z, Y0..Y0+OUT_ROWS-1): the coarse rows they blend
-// (two z planes, ny rows each) are staged in shared memory, a thread owns an
-// x column and writes its rows coalesced.
-constexpr int OUT_ROWS = 16;
-__global__ void __launch_bounds__(256) k_output(int N, int n, const float* __restrict__ y,
-                                                const float* __restrict__ scale, float* __restrict__ H) {
-  extern __shared__ float sc[];  // [2][ny][n]
+// Cubic convolution weights (Keys, a = -1/2) of the taps -1, 0, 1, 2 at
+// fraction u in [0, 1).
+__device__ __forceinline__ void cubic_w(float u, float w[4]) {
+  w[0] = ((-u + 2.f) * u - 1.f) * u * 0.5f;
+  w[1] = ((3.f * u - 5.f) * u * u + 2.f) * 0.5f;
+  w[2] = ((-3.f * u + 4.f) * u + 1.f) * u * 0.5f;
+  w[3] = (u - 1.f) * u * u * 0.5f;
+}
+
+// Periodic cubic-convolution upsampling, one axis per kernel: the fine cell
+// centre X of the fine axis (f = N/n fine cells per coarse cell) sits at
+// coarse position (X + 1/2)/f - 1/2; the taps are the coarse cells x0 - 1 ..
+// x0 + 2 around it. Each kernel reads `in` with the axis of length n at
+// stride `stride` (elements) inside rows of `inner` elements, and writes the
+// axis of length N. One CTA per outer row; threads along the inner axis.
+__device__ __forceinline__ void up_taps(int X, int n, int f, int idx[4], float w[4]) {
+  const float fx = (X + 0.5f) / f - 0.5f;
+  const int x0 = (int)floorf(fx);
+  cubic_w(fx - x0, w);
+#pragma unroll
+  for (int k = 0; k < 4; k++) idx[k] = ((x0 - 1 + k) % n + n) % n;
+}
+
+// x: in [rows][n] -> out [rows][N]
+__global__ void k_up_x(int n, int N, const float* __restrict__ in, float* __restrict__ out) {
   const int f = N / n;
-  const int row0 = blockIdx.x * OUT_ROWS;  // (c N + Z) N + Y0, N % OUT_ROWS == 0
-  const int Z = (row0 / N) % N, c = row0 / (N * N), Y0 = row0 % N;
-  const float fz = (Z + 0.5f) / f - 0.5f;
-  const int z0 = (int)floorf(fz);
-  const float wz = fz - z0;
-  const int ylo = (int)floorf((Y0 + 0.5f) / f - 0.5f);
-  const int ny = (int)floorf((Y0 + OUT_ROWS - 0.5f) / f - 0.5f) - ylo + 2;
-  const float* yc = y + (int64_t)c * n * n * n;
-  for (int e = threadIdx.x; e < 2 * ny * n; e += blockDim.x) {
-    const int xx = e % n, j = (e / n) % ny, dz = e / (n * ny);
-    const int zz = (z0 + dz + n) % n, yy = ((ylo + j) % n + n) % n;
-    sc[e] = yc[((int64_t)zz * n + yy) * n + xx];
-  }
-  __syncthreads();
-  const float s = *scale;
+  const int64_t row = blockIdx.x;
   for (int X = threadIdx.x; X < N; X += blockDim.x) {
-    const float fx = (X + 0.5f) / f - 0.5f;
-    const int x0 = (int)floorf(fx);
-    const float wx = fx - x0;
-    const int xa = (x0 + n) % n, xb = (x0 + 1) % n;
-    for (int r = 0; r < OUT_ROWS; r++) {
-      const float fy = (Y0 + r + 0.5f) / f - 0.5f;
-      const int y0 = (int)floorf(fy);
-      const float wy = fy - y0;
-      const float* p0 = sc + (y0 - ylo) * n;  // dz = 0, rows y0 and y0 + 1
-      const float* p1 = p0 + ny * n;          // dz = 1
-      const float a00 = (1 - wx) * p0[xa] + wx * p0[xb], a01 = (1 - wx) * p0[n + xa] + wx * p0[n + xb];
-      const float a10 = (1 - wx) * p1[xa] + wx * p1[xb], a11 = (1 - wx) * p1[n + xa] + wx * p1[n + xb];
-      H[(int64_t)(row0 + r) * N + X] =
-          s * ((1 - wz) * ((1 - wy) * a00 + wy * a01) + wz * ((1 - wy) * a10 + wy * a11));
-    }
+    int idx[4];
+    float w[4];
+    up_taps(X, n, f, idx, w);
+    const float* r = in + row * n;
+    out[row * N + X] = w[0] * r[idx[0]] + w[1] * r[idx[1]] + w[2] * r[idx[2]] + w[3] * r[idx[3]];
+  }
+}
+
+// middle axis: in [outer][n][inner] -> out [outer][N][inner] (times scale when given)
+__global__ void k_up_mid(int n, int N, int inner, const float* __restrict__ in, float* __restrict__ out,
+                         const float* __restrict__ scale) {
+  const int f = N / n;
+  const int64_t orow = blockIdx.x;  // outer * N + Y
+  const int Y = (int)(orow % N);
+  const int64_t outer = orow / N;
+  int idx[4];
+  float w[4];
+  up_taps(Y, n, f, idx, w);
+  const float s = scale ? *scale : 1.f;
+  const float* base = in + outer * n * inner;
+  for (int X = threadIdx.x; X < inner; X += blockDim.x) {
+    const float v = w[0] * base[(int64_t)idx[0] * inner + X] + w[1] * base[(int64_t)idx[1] * inner + X] +
+                    w[2] * base[(int64_t)idx[2] * inner + X] + w[3] * base[(int64_t)idx[3] * inner + X];
+    out[orow * inner + X] = s * v;
   }
 }
 
@@ -959,13 +971,20 @@ int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* sca
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* stream) {
-  if (!y || !scale || !H || n <= 0 || N % n) return -1;
-  if (N % OUT_ROWS) return -1;
+size_t mond_fno_output_scratch_bytes(int N, int n) {
+  if (n <= 0 || N % n) return 0;
+  return sizeof(float) * 3 * ((size_t)n * n * N + (size_t)n * N * N);
+}
+
+int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* scratch, void* stream) {
+  if (!y || !scale || !H || !scratch || n <= 0 || N % n) return -1;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* t1 = (float*)scratch;              // [3 n n][N]   x upsampled
+  float* t2 = t1 + (size_t)3 * n * n * N;   // [3 n][N][N]  x, y upsampled
   const int threads = N < 256 ? ((N + 31) / 32) * 32 : 256;
-  const int ny_max = OUT_ROWS / (N / n) + 3;
-  k_output<<<(unsigned)(3 * N * N / OUT_ROWS), threads, sizeof(float) * 2 * ny_max * n, (cudaStream_t)stream>>>(
-      N, n, y, scale, H);
+  k_up_x<<<(unsigned)(3 * n * n), threads, 0, st>>>(n, N, y, t1);
+  k_up_mid<<<(unsigned)(3 * n * N), threads, 0, st>>>(n, N, N, t1, t2, nullptr);
+  k_up_mid<<<(unsigned)(3 * N), threads, 0, st>>>(n, N, N * N, t2, H, scale);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -1060,7 +1060,8 @@ int mond_pm_half_kick(mond_pm_t h, double dt) {
 int mond_pm_gather(mond_pm_t h, float* g_out) {
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "gather before solve_field");
-  if (!g_out) return fail(h, MOND_EINVAL, "g_out is NULL");
+  if (!g_out && h->N > 0) return fail(h, MOND_EINVAL, "g_out is NULL");
+  if (h->N == 0) return MOND_OK;
   return do_gather(h, g_out, 0.0, 0, 0);
 }
 

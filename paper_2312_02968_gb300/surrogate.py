@@ -142,8 +142,16 @@ def features(gN, N: int, n: int, a0: float, x, scale, stream):
            "input")
 
 
-def upsample(y, N: int, n: int, scale, H, stream):
-    _check(lib().mond_fno_output(N, n, _p(y), _p(scale), _p(H), ctypes.c_void_p(stream.cuda_stream)), "output")
+def upsample(y, N: int, n: int, scale, H, stream, scratch=None):
+    """H [3, N^3] = scale * cubic upsampling of y [3, n^3]; scratch: a device
+    uint8 tensor of at least mond_fno_output_scratch_bytes(N, n) bytes (made
+    here when not given)."""
+    if scratch is None:
+        import torch
+
+        scratch = torch.empty(int(lib().mond_fno_output_scratch_bytes(N, n)), dtype=torch.uint8, device=H.device)
+    _check(lib().mond_fno_output(N, n, _p(y), _p(scale), _p(H), _p(scratch), ctypes.c_void_p(stream.cuda_stream)),
+           "output")
 
 
 def coarsen(fine, N: int, n: int, ncomp: int, coarse, scale, stream, fine2=None):
@@ -225,6 +233,8 @@ class GuessSolver:
         self.y = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
         self.scale = torch.empty(4, dtype=torch.float32, device=dev)
         self.H = torch.empty((3, nf, nf, nf), dtype=torch.float32, device=dev)
+        self.up_scratch = torch.empty(int(lib().mond_fno_output_scratch_bytes(nf, n)), dtype=torch.uint8,
+                                      device=dev)
         self.gN = h.field_ptr(B.FIELD_GN)
 
     def predict(self):
@@ -233,7 +243,7 @@ class GuessSolver:
         h.solve_field(0, B.WARM_NONE)
         features(self.gN, h.nf, net.n, self.a0, self.x, self.scale, h.stream)
         net.forward(self.x, self.y)
-        upsample(self.y, h.nf, net.n, self.scale, self.H, h.stream)
+        upsample(self.y, h.nf, net.n, self.scale, self.H, h.stream, self.up_scratch)
         return self.H
 
     def solve(self, n_iter: int = 1, project: bool = False):

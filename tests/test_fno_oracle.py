@@ -155,14 +155,20 @@ def test_coarsen_and_upsample():
     const = np.full((1, 4, 4, 4), 2.5)
     assert np.allclose(F.upsample(const, 16, 2.0), 5.0)
     # a field linear in x on the coarse cells interpolates linearly in between
+    # (away from the periodic seam)
     n, N = 8, 32
     lin = np.broadcast_to(np.arange(n, dtype=float)[None, None, None, :], (1, n, n, n)).copy()
     up = F.upsample(lin, N, 1.0)
     f = N // n
     X = np.arange(N)
     u = (X + 0.5) / f - 0.5
-    inner = (u >= 0) & (u <= n - 1)
+    inner = (u >= 1) & (u <= n - 2)  # all four taps on the same side of the seam
     assert np.allclose(up[0, 3, 5, inner], u[inner])
+    # and a quadratic one exactly (cubic convolution is third-order accurate)
+    quad = lin ** 2
+    upq = F.upsample(quad, N, 1.0)
+    assert np.allclose(upq[0, 3, 5, inner], u[inner] ** 2)
+    assert np.allclose(F.cubic_weights(np.linspace(0, 0.99, 7)).sum(0), 1.0)
 
 
 def test_mixture_density_masses():

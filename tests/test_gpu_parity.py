@@ -55,6 +55,7 @@ def make(B, n, pad, p, sigma, mu=0, box=None, a0=1.0, G=1.0, maxp=None):
 # deposit: bit-exact
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n,sigma,N,seed", [(16, 1.0, 1, 0), (16, 1.5, 37, 1), (32, 1.0, 5000, 2), (32, 2.0, 777, 3),
+                                            (32, 1.25, 6000, 7), (48, 1.75, 9000, 8),
                                             (48, 1.5, 20000, 4), (64, 1.0, 100000, 5), (32, 0.75, 3000, 6)])
 def test_deposit_bit_exact(B, n, sigma, N, seed):
     p = W.uniform_random(n, N, seed=seed)  # covers the periodic wrap at the faces
@@ -119,6 +120,20 @@ def test_deposit_edge_cases(B):
     acc, ka = h.get_deposit_acc()
     ref, ka_ref, _ = oracle.deposit_fixed(n, 1.0, cell, off, mass)
     assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+
+
+def test_empty_particle_set_steps(B):
+    """No particles: deposit, solve, gather and push run and leave the
+    (empty) state alone; the field of an empty density is zero."""
+    n = 32
+    p = W.uniform_random(n, 0, seed=0)
+    h, _ = make(B, n, 1, p, 1.5, maxp=8)
+    h.step(0.5, 4)
+    h.sync()
+    assert float(h.get_field(B.FIELD_ACC).abs().max()) == 0.0
+    h.deposit()  # a step leaves the field stale (the particles moved): solve again before a gather
+    h.solve_field(4)
+    assert h.gather().numel() == 0
 
 
 def test_deposit_invalid_particle_reported(B):
@@ -245,7 +260,7 @@ def test_newton_field_reused_within_one_density(B):
 # ---------------------------------------------------------------------------
 # gather, smoothing, push, diagnostics
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("sigma", [1.0, 1.5, 2.0])
+@pytest.mark.parametrize("sigma", [0.75, 1.0, 1.25, 1.5, 1.75, 2.0])  # reach r = 2 .. 7: every kernel variant
 def test_gather_matches_oracle(B, sigma):
     n = 32
     p = W.uniform_random(n, 3000, seed=int(10 * sigma))  # includes particles whose ball wraps
