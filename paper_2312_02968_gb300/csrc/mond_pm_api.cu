@@ -511,10 +511,14 @@ int do_bin(mond_pm* h) {
     parts::k_bin_scatter<<<nb, 256, 0, h->st>>>(b);
   }
   {
-    Timed tm(h, KC_BIN, 12.0 * h->ntile);
-    parts::k_tile_counts<<<(h->ntile + 255) / 256, 256, 0, h->st>>>(b);
-    h->launches++;  // the Timed scope counts the second launch
-    parts::k_tile_chunks<<<1, 1024, 0, h->st>>>(b);
+    // work items per tile, then their exclusive scan in place (chunk_start[T] = total)
+    Timed tm(h, KC_BIN, 16.0 * h->ntile);
+    const int T = h->ntile, nbt = (T + parts::SCAN_B - 1) / parts::SCAN_B;
+    parts::k_tile_counts<<<(T + 255) / 256, 256, 0, h->st>>>(b);
+    parts::k_scan_reduce<<<nbt, 1024, 0, h->st>>>(h->w.chunk_start, T, h->w.bsum);
+    parts::k_scan_blocks<<<1, 1024, 0, h->st>>>(h->w.bsum, nbt);
+    parts::k_scan_apply<<<nbt, 1024, 0, h->st>>>(h->w.chunk_start, T, h->w.bsum, h->w.chunk_start);
+    h->launches += 3;  // the Timed scope counts one of the four launches
   }
   CK(cudaGetLastError());
   return MOND_OK;

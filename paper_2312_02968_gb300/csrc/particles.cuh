@@ -108,20 +108,38 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int* bsum, int nblk) {
   }
 }
 
+// cnt and cstart may be the same array (each thread reads its run before
+// writing it); both 16-byte aligned.
 __global__ void __launch_bounds__(1024) k_scan_apply(const int* cnt, int64_t M, const int* bsum, int* cstart) {
   __shared__ int wsum[32];
   constexpr int PER = SCAN_B / 1024;
+  static_assert(PER == 8, "two int4 per thread");
   const int64_t b0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * PER;
   int v[PER], s = 0;
-  for (int k = 0; k < PER; k++) {
-    v[k] = (b0 + k < M) ? cnt[b0 + k] : 0;
-    s += v[k];
+  if (b0 + PER <= M) {
+    const int4 a = reinterpret_cast<const int4*>(cnt + b0)[0], b = reinterpret_cast<const int4*>(cnt + b0)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; k++) v[k] = (b0 + k < M) ? cnt[b0 + k] : 0;
   }
+#pragma unroll
+  for (int k = 0; k < PER; k++) s += v[k];
   int tot;
   int base = block_excl_scan(s, wsum, &tot) + bsum[blockIdx.x];
+  int o[PER];
+#pragma unroll
   for (int k = 0; k < PER; k++) {
-    if (b0 + k < M) cstart[b0 + k] = base;
+    o[k] = base;
     base += v[k];
+  }
+  if (b0 + PER <= M) {
+    reinterpret_cast<int4*>(cstart + b0)[0] = make_int4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<int4*>(cstart + b0)[1] = make_int4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; k++)
+      if (b0 + k < M) cstart[b0 + k] = o[k];
   }
   if (b0 <= M - 1 && M - 1 < b0 + PER) cstart[M] = base;  // the thread holding the last key writes the total
 }
@@ -136,35 +154,15 @@ __global__ void k_bin_scatter(BinArgs a) {
 }
 
 // Tile ranges and work-item counts per tile, one thread per tile (the tile
-// starts sit 512 cells apart in the cell scan, so the reads are spread out).
+// starts sit 512 cells apart in the cell scan, so the reads are spread out);
+// the counts are then scanned in place by the key-scan kernels.
 __global__ void k_tile_counts(BinArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) a.tile_start[a.ntile] = a.cstart[a.ncell];
   if (t >= a.ntile) return;
   const int ts = a.cstart[(int64_t)t * 512], te = a.cstart[(int64_t)(t + 1) * 512];
   a.tile_start[t] = ts;
   a.chunk_start[t] = (te - ts + a.chunk - 1) / a.chunk;
-}
-
-// Exclusive scan of the per-tile work-item counts in place (single CTA; each
-// thread owns a contiguous run of tiles).
-__global__ void __launch_bounds__(1024) k_tile_chunks(BinArgs a) {
-  __shared__ int wsum[32];
-  const int T = a.ntile;
-  const int per = (T + 1023) / 1024;
-  const int t0 = threadIdx.x * per, t1 = min(T, t0 + per);
-  int s = 0;
-  for (int t = t0; t < t1; t++) s += a.chunk_start[t];
-  int tot;
-  int base = block_excl_scan(s, wsum, &tot);
-  for (int t = t0; t < t1; t++) {
-    const int c = a.chunk_start[t];
-    a.chunk_start[t] = base;
-    base += c;
-  }
-  if (threadIdx.x == 0) {
-    a.tile_start[T] = a.cstart[a.ncell];
-    a.chunk_start[T] = tot;
-  }
 }
 
 // Work item w -> tile t with chunk_start[t] <= w < chunk_start[t + 1].
