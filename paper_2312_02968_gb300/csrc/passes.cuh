@@ -694,7 +694,11 @@ __device__ __forceinline__ void zop(float2* tile, int T, int i, int col, int row
 template <int MODE>
 constexpr int zthreads() { return 384; }
 
-template <int N, int MODE, int NTZ = zthreads<MODE>()>
+// SC: a separate scalar region per stage (needed only when phi is stored);
+// without it the Newton pass lands its scalar input in the last third of the
+// vector region and reads it into registers before the outputs overwrite it,
+// so that every mode runs with three-component stages (two CTAs per SM).
+template <int N, int MODE, bool SC, int NTZ = zthreads<MODE>()>
 __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
                                                    const __grid_constant__ tma::TensorMap out_map,
                                                    const __grid_constant__ tma::TensorMap phi_map, PipeZArgs a) {
@@ -702,14 +706,15 @@ __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma:
   constexpr int P = C::PZ;
   constexpr bool SCALAR = (MODE == Z_NEWTON || MODE == Z_FINAL);
   constexpr int VP = 3 * P;                     // vector row pitch
-  constexpr int SE = N * VP + (SCALAR ? N * P : 0);
+  constexpr int SE = N * VP + (SC ? N * P : 0);
+  constexpr int SOFF = SC ? N * VP : 2 * N * P;  // scalar region inside a stage
   extern __shared__ __align__(128) float2 psm[];
   __shared__ __align__(8) uint64_t bars[2];
   float2* tw = psm;
   float* kv = reinterpret_cast<float*>(psm + N);
   float* kp = kv + N;
   float2* stage0 = psm + 2 * N;
-  const bool phi = SCALAR && a.nout > 3;
+  const bool phi = SC && SCALAR && a.nout > 3;
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += NTZ) {
     tw[i] = a.tw[i];
@@ -722,7 +727,7 @@ __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma:
     if constexpr (MODE == Z_NEWTON) {
       tma::mbar_expect_tx(bar, N * P * 8);
       for (int b = 0; b < C::NBOX; b++)
-        tma::load_4d(dst + N * VP + b * C::BOX * P, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
+        tma::load_4d(dst + SOFF + b * C::BOX * P, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
       return N * P * 8;
     } else {
       tma::mbar_expect_tx(bar, 3 * N * P * 8);
@@ -733,12 +738,26 @@ __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma:
   auto compute = [&](int t, float2* st) {
     const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
     float2* sv = st;            // vector region
-    float2* ss = st + N * VP;   // scalar region
+    float2* ss = st + SOFF;     // scalar region
     if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(ss, P, 1, tw, 1, tid);
     else fftk::fft<N, -1, 3 * P, NTZ>(sv, VP, 1, tw, 1, tid);
     const float ky = kv[y], kpy = kp[y];
     const bool ny = (y == N / 2);
-    for (int i = tid; i < N * P; i += NTZ) {
+    constexpr int PPT = (N * P + NTZ - 1) / NTZ;
+    float2 rin[(MODE == Z_NEWTON && !SC) ? PPT : 1];
+    if constexpr (MODE == Z_NEWTON && !SC) {
+      // the scalar input shares its space with the outputs: read it all first
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        const int i = tid + k * NTZ;
+        if (i < N * P) rin[k] = ss[i];
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int i = tid + k * NTZ;
+      if (i >= N * P) break;
       const int row = i / P, cc = i % P, col = blk * P + cc;
       if (col > N / 2) continue;
       float2* v = sv + row * VP + cc;  // component c at v[c * P]
@@ -748,13 +767,15 @@ __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma:
       const float kk = kx * kx + ky * ky + kz * kz;
       const float A = kk > 0.f ? 1.0f / kk : 0.f;
       if constexpr (MODE == Z_NEWTON) {
-        const float2 r = *sc;
+        float2 r;
+        if constexpr (SC) r = *sc;
+        else r = rin[k];
         const float f = a.coef * A * a.norm;  // 4 pi G A / N^3
         const float2 ir = cmul_i<1>(r);
         v[0] = cscale(ir, f * kp[col]);
         v[P] = cscale(ir, f * kpy);
         v[2 * P] = cscale(ir, f * kp[row]);
-        *sc = cscale(r, -f);  // phi_N^ = -4 pi G A rho^
+        if constexpr (SC) *sc = cscale(r, -f);  // phi_N^ = -4 pi G A rho^
       } else if constexpr (MODE == Z_SMOOTH) {
         const float f = a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] * a.norm;
         for (int c = 0; c < 3; c++) v[c * P] = cscale(v[c * P], f);
@@ -771,7 +792,7 @@ __global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma:
           v[0] = cscale(aS, kp[col]);
           v[P] = cscale(aS, kpy);
           v[2 * P] = cscale(aS, kp[row]);
-          *sc = cmul_i<1>(aS);
+          if constexpr (SC) *sc = cmul_i<1>(aS);
         } else {
           // P_ab = k_a k_b A, off-diagonal terms dropped when exactly one of a, b is on its Nyquist plane
           for (int aa = 0; aa < 3; aa++) {

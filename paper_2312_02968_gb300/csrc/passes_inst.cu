@@ -95,20 +95,27 @@ cudaError_t launch_ypipe(const tma::TensorMap& map, const PipeYArgs& a, cudaStre
   return cudaGetLastError();
 }
 
-template <int MODE>
-cudaError_t launch_zpipe(const tma::TensorMap& in, const tma::TensorMap& out, const tma::TensorMap& phi,
-                         const PipeZArgs& a, cudaStream_t st) {
-  constexpr bool SCALAR = (MODE == Z_NEWTON || MODE == Z_FINAL);
-  const size_t stage = (size_t)N * PipeCfg<N>::PZ * (SCALAR ? 4 : 3);
+template <int MODE, bool SC>
+cudaError_t launch_zpipe_sc(const tma::TensorMap& in, const tma::TensorMap& out, const tma::TensorMap& phi,
+                            const PipeZArgs& a, cudaStream_t st) {
+  const size_t stage = (size_t)N * PipeCfg<N>::PZ * (SC ? 4 : 3);
   const size_t sm = sizeof(float2) * (2 * N + 2 * stage);
-  cudaError_t e = set_smem(k_zpass_pipe<N, MODE>, sm);
+  cudaError_t e = set_smem(k_zpass_pipe<N, MODE, SC>, sm);
   if (e != cudaSuccess) return e;
   static int grid = 0;
   constexpr int nt = zthreads<MODE>();
-  if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE>, sm, nt);
+  if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE, SC>, sm, nt);
   const int ntiles = PipeCfg<N>::NBLKZ * N;
-  k_zpass_pipe<N, MODE><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
+  k_zpass_pipe<N, MODE, SC><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
   return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_zpipe(const tma::TensorMap& in, const tma::TensorMap& out, const tma::TensorMap& phi,
+                         const PipeZArgs& a, cudaStream_t st) {
+  // a separate scalar region only when the potential is stored
+  if ((MODE == Z_NEWTON || MODE == Z_FINAL) && a.nout > 3) return launch_zpipe_sc<MODE, true>(in, out, phi, a, st);
+  return launch_zpipe_sc<MODE, false>(in, out, phi, a, st);
 }
 }  // namespace
 
