@@ -699,7 +699,7 @@ constexpr int zthreads() { return 384; }
 // vector region and reads it into registers before the outputs overwrite it,
 // so that every mode runs with three-component stages (two CTAs per SM).
 template <int N, int MODE, bool SC, int NTZ = zthreads<MODE>()>
-__global__ void __launch_bounds__(NTZ) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
+__global__ void __launch_bounds__(NTZ, 2) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
                                                    const __grid_constant__ tma::TensorMap out_map,
                                                    const __grid_constant__ tma::TensorMap phi_map, PipeZArgs a) {
   using C = PipeCfg<N>;
