@@ -236,25 +236,33 @@ def run_learned(args, dev):
             "best_guess": best, "fastest_at_1e-4": fastest_meeting}
 
 
-def run_ensemble(args, dev):
+def run_ensemble(args, dev, dist=None):
     """Batched ensemble: independent systems with sides drawn from
     {64, 96, 128, 192} and 1e4-1e6 particles (isothermal, deep mu, b = side/32;
     or Plummer, standard mu, a = side/16), sigma 1 px, 4 iterations, stepped
-    together as one CUDA graph per step after per-system autotuning."""
+    together as one CUDA graph per step after per-system autotuning. Under
+    several ranks the systems are dealt to the GPUs by estimated cost
+    (longest first); each rank steps its share, rank 0 gathers."""
     import numpy as np
     import torch
 
     from paper_2312_02968_gb300 import binding as B
+    from paper_2312_02968_gb300 import replicas as R
     from paper_2312_02968_gb300 import workloads as W
 
+    rank = dist.get_rank() if dist is not None else 0
+    world = dist.get_world_size() if dist is not None else 1
     rng = np.random.default_rng(7)
-    hs, keep, Ns, sides = [], [], [], []
-    t0 = time.time()
+    specs = []
     for _ in range(args.ensemble_systems):
         n = int(rng.choice([64, 96, 128, 192]))
         N = int(round(math.exp(rng.uniform(math.log(1e4), math.log(1e6)))))
-        kind = int(rng.integers(0, 2))
-        seed = int(rng.integers(1 << 30))
+        specs.append((n, N, int(rng.integers(0, 2)), int(rng.integers(1 << 30))))
+    mine = R.lpt_shard([R.system_cost(n, N) for n, N, _, _ in specs], world)[rank]
+    hs, keep, Ns, sides = [], [], [], []
+    t0 = time.time()
+    for i in mine:
+        n, N, kind, seed = specs[i]
         if kind == 0:
             p, mu = W.isothermal(n, 1.0, N, n / 32, 0.4 * n, seed=seed), B.MU_DEEP
         else:
@@ -278,6 +286,8 @@ def run_ensemble(args, dev):
     batch.step(dt, n_steps=2, n_iter=4)
     batch.sync()
     l0 = batch.kernel_launches()
+    if dist is not None:
+        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(batch.stream)
@@ -285,7 +295,7 @@ def run_ensemble(args, dev):
     e1.record(batch.stream)
     e1.synchronize()
     batch.sync()
-    ms = e0.elapsed_time(e1)
+    ms = R.max_over_ranks(e0.elapsed_time(e1), dist, dev)  # the slowest rank's share
     launches = batch.kernel_launches() - l0
     sec = ms / 1000.0
     # the same systems stepped one after another on one stream, for comparison
@@ -305,16 +315,25 @@ def run_ensemble(args, dev):
     batch.close()
     for h in hs:
         h.close()
-    chunks = {}
-    for c, pp in tuned:
-        key = f"chunk{c}_pipe{pp}"
-        chunks[key] = chunks.get(key, 0) + 1
-    return {"systems": len(hs), "sides": {str(k): sides.count(k) for k in sorted(set(sides))},
-            "particles": int(sum(Ns)), "steps": args.ensemble_steps, "ms": ms,
-            "system_steps_per_s": len(hs) * args.ensemble_steps / sec,
-            "particle_steps_per_s": sum(Ns) * args.ensemble_steps / sec,
-            "one_by_one_system_steps_per_s": serial_sps, "graph_launches_per_step": 1,
-            "kernel_launches": launches, "autotuned": chunks, "s_generate": t_gen, "s_autotune": t_tune}
+    parts = R.gather_to_root({"tuned": tuned, "Ns": Ns, "sides": sides, "launches": launches,
+                              "serial_sps": serial_sps}, dist)
+    if rank != 0:
+        return None
+    chunks, allN, allsides = {}, [], []
+    for part in parts:
+        allN += part["Ns"]
+        allsides += part["sides"]
+        for c, pp in part["tuned"]:
+            key = f"chunk{c}_pipe{pp}"
+            chunks[key] = chunks.get(key, 0) + 1
+    nsys = len(allN)
+    return {"systems": nsys, "ranks": world, "sides": {str(k): allsides.count(k) for k in sorted(set(allsides))},
+            "particles": int(sum(allN)), "steps": args.ensemble_steps, "ms": ms,
+            "system_steps_per_s": nsys * args.ensemble_steps / sec,
+            "particle_steps_per_s": sum(allN) * args.ensemble_steps / sec,
+            "one_by_one_system_steps_per_s": sum(p["serial_sps"] for p in parts), "graph_launches_per_step": 1,
+            "kernel_launches": sum(p["launches"] for p in parts), "autotuned": chunks, "s_generate": t_gen,
+            "s_autotune": t_tune}
 
 
 def main():
@@ -357,6 +376,7 @@ def main():
 
     __graft_entry__.build()
     from paper_2312_02968_gb300 import binding as B
+    from paper_2312_02968_gb300 import replicas as R
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -419,10 +439,7 @@ def main():
     stats = h.kernel_stats()
     h.set_option(B.OPT_TIMING, 0)
     h.sync()
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = R.max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     value = world * args.steps / (ms / 1000.0)
 
@@ -444,10 +461,7 @@ def main():
     w1.synchronize()
     barrier()
     wms = w0.elapsed_time(w1)
-    if dist is not None:
-        tt = torch.tensor([wms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        wms = float(tt.item())
+    wms = R.max_over_ranks(wms, dist, dev)
     warm_value = world * args.steps / (wms / 1000.0)
 
     # ---- accuracy against the converged field (not timed) ----------------------
@@ -482,17 +496,14 @@ def main():
         h.step_host(dt, K, B.WARM_NONE, cell_h, off_h, vel_h)
     barrier()
     e2e_s = time.perf_counter() - tq
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = R.max_over_ranks(e2e_s, dist, dev)
     e2e_value = world * args.steps / e2e_s
 
     learned = ensemble = None
     if rank == 0 and args.learned_pairs > 0:
         learned = run_learned(args, dev)
-    if rank == 0 and args.ensemble_systems > 0:
-        ensemble = run_ensemble(args, dev)
+    if args.ensemble_systems > 0:
+        ensemble = run_ensemble(args, dev, dist)
 
     if rank == 0:
         peak, peak_src = load_peaks()
