@@ -25,6 +25,13 @@ What pins each function (tests in ``tests/test_oracle_*.py``):
                   field reproduces the ball weight sum; two-body force.
   push            Eq. motion on hand-checked numbers; circular orbit period.
   particle_diag   two-body constants of motion on hand-made states.
+  field_density   closed form on a sine field; the spectral relation
+                  rho_B^ = (|k_FD|^2/|k|^2) rho^ (numpy FFT); Newtonian mu
+                  gives rho_A = rho_B; isothermal rho_A and M_A (Sect. 4.3).
+  box_flux_mass   equals the box sum of field_density (discrete Gauss
+                  theorem); the total mass of a periodic box is zero.
+  shell_mass      brute-force sums on small grids; enclosed M_A(r) of the
+                  isothermal sphere (Sect. 4.3 closed form).
 """
 from __future__ import annotations
 
@@ -91,6 +98,10 @@ def lib():
             L.ora_transform_count.restype = ctypes.c_longlong
             L.ora_num_threads.restype = i32
             L.ora_project_div.argtypes = [i32, f64, P, P]
+            L.ora_field_density.argtypes = [i32, f64, f64, P, P]
+            L.ora_box_flux_mass.restype = f64
+            L.ora_box_flux_mass.argtypes = [i32, f64, f64, P, P, P]
+            L.ora_shell_mass.argtypes = [i32, f64, P, P, f64, i32, P]
             _lib = L
         return _lib
 
@@ -223,6 +234,34 @@ def project_div(field, s: float):
     f = _c(field, np.float64)
     out = np.zeros_like(f)
     lib().ora_project_div(f.shape[1], float(s), _p(f), _p(out))
+    return out
+
+
+def field_density(g, s: float, G: float):
+    """Eq. apparentdensity: -(div_FD g) / (4 pi G) for a field [3, n, n, n]
+    (g_N gives rho_B, the MOND acceleration rho_A)."""
+    g = _c(g, np.float64)
+    out = np.zeros(g.shape[1:])
+    lib().ora_field_density(g.shape[1], float(s), float(G), _p(g), _p(out))
+    return out
+
+
+def box_flux_mass(g, s: float, G: float, lo, hi) -> float:
+    """Eq. totalmass: -(1/(4 pi G)) times the flux of g out of the box of
+    cells lo..hi (inclusive, (x, y, z) order, periodic)."""
+    g = _c(g, np.float64)
+    lo = np.ascontiguousarray(lo, np.int32)
+    hi = np.ascontiguousarray(hi, np.int32)
+    return float(lib().ora_box_flux_mass(g.shape[1], float(s), float(G), _p(g), _p(lo), _p(hi)))
+
+
+def shell_mass(rho, s: float, center, dr: float, nbins: int):
+    """Mass rho s^3 in shells [k dr, (k+1) dr) about center (physical (x, y, z),
+    cell i at (i - n/2) s, minimum image)."""
+    rho = _c(rho, np.float64)
+    c = np.ascontiguousarray(center, np.float64)
+    out = np.zeros(nbins)
+    lib().ora_shell_mass(rho.shape[0], float(s), _p(rho), _p(c), float(dr), int(nbins), _p(out))
     return out
 
 

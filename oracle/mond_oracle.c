@@ -702,3 +702,79 @@ void ora_project_div(int n, double s, const double* in, double* out) {
   for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, out + a * tot);
   free(cv);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Apparent density and enclosed mass (Eq. apparentdensity, Eq. totalmass)   */
+/* ------------------------------------------------------------------------ */
+
+/* rho = -(div g) / (4 pi G), the divergence taken with the periodic central
+ * difference of the gradient (f[i+1] - f[i-1]) / (2 s) on each axis.
+ * g_N gives the baryonic density rho_B, the MOND acceleration the apparent
+ * density rho_A. g: 3 planes (x, y, z components); rho: 1 plane. */
+void ora_field_density(int n, double s, double G, const double* g, double* rho) {
+  int64_t tot = (int64_t)n * n * n;
+  double c = -1.0 / (4.0 * M_PI * G);
+#pragma omp parallel for
+  for (int z = 0; z < n; z++)
+    for (int y = 0; y < n; y++)
+      for (int x = 0; x < n; x++) {
+        double dx = (g[idx3(n, wrap(x + 1, n), y, z)] - g[idx3(n, wrap(x - 1, n), y, z)]) / (2.0 * s);
+        double dy = (g[tot + idx3(n, x, wrap(y + 1, n), z)] - g[tot + idx3(n, x, wrap(y - 1, n), z)]) / (2.0 * s);
+        double dz = (g[2 * tot + idx3(n, x, y, wrap(z + 1, n))] - g[2 * tot + idx3(n, x, y, wrap(z - 1, n))]) /
+                    (2.0 * s);
+        rho[idx3(n, x, y, z)] = c * (dx + dy + dz);
+      }
+}
+
+/* Mass inside the box W of cells lo..hi (inclusive on each axis, periodic)
+ * from the outward flux of g through its six faces:
+ * M(W) = -(1/(4 pi G)) sum over faces of g.dS. On a face the normal
+ * component is the mean of the two cells the face separates, the face value
+ * that the central-difference divergence implies, so M(W) equals the sum of
+ * ora_field_density over W times s^3. */
+double ora_box_flux_mass(int n, double s, double G, const double* g, const int32_t* lo, const int32_t* hi) {
+  int64_t tot = (int64_t)n * n * n;
+  double flux = 0.0;
+  for (int a = 0; a < 3; a++) {
+    int b = (a + 1) % 3, c = (a + 2) % 3;
+    for (int side = 0; side < 2; side++) {
+      /* the two cells straddling the face, along axis a */
+      int in_a = side ? hi[a] : lo[a];
+      int out_a = side ? hi[a] + 1 : lo[a] - 1;
+      double sgn = side ? 1.0 : -1.0;
+      for (int ib = lo[b]; ib <= hi[b]; ib++)
+        for (int ic = lo[c]; ic <= hi[c]; ic++) {
+          int p[3], q[3];
+          p[a] = wrap(in_a, n);
+          q[a] = wrap(out_a, n);
+          p[b] = q[b] = wrap(ib, n);
+          p[c] = q[c] = wrap(ic, n);
+          double gin = g[a * tot + idx3(n, p[0], p[1], p[2])];
+          double gout = g[a * tot + idx3(n, q[0], q[1], q[2])];
+          flux += sgn * 0.5 * (gin + gout) * s * s;
+        }
+    }
+  }
+  return -flux / (4.0 * M_PI * G);
+}
+
+/* Mass in spherical shells about the point c (physical coordinates, cell i
+ * at (i - n/2) s): out[k] += rho s^3 over the cells whose centre lies at a
+ * minimum-image distance r with floor(r / dr) = k, for k < nbins. */
+void ora_shell_mass(int n, double s, const double* rho, const double* c, double dr, int nbins, double* out) {
+  double L = n * s;
+  for (int k = 0; k < nbins; k++) out[k] = 0.0;
+  for (int z = 0; z < n; z++)
+    for (int y = 0; y < n; y++)
+      for (int x = 0; x < n; x++) {
+        double d[3];
+        int ii[3] = {x, y, z};
+        for (int a = 0; a < 3; a++) {
+          d[a] = (ii[a] - n / 2) * s - c[a];
+          d[a] -= L * nearbyint(d[a] / L);
+        }
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double fk = floor(r / dr);
+        if (fk < nbins) out[(int)fk] += rho[idx3(n, x, y, z)] * s * s * s;
+      }
+}
