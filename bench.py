@@ -198,6 +198,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_density(h, B, stream, steps):
+    """Time the density kernels (Eq. apparentdensity) on the 256^3 fields of the
+    last solve: apparent (3 planes in, 1 out) and phantom (6 in, 1 out), and
+    one shell-mass profile (Eq. totalmass); compare the enclosed apparent mass
+    of the isothermal sphere with its closed form (Sect. 4.3)."""
+    import math
+
+    import torch
+
+    n = WL["n"]
+    plane = 4 * n ** 3
+    out = torch.empty((n, n, n), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    res = {}
+    for name, kind, nin in (("apparent", B.DENS_APPARENT, 3), ("phantom", B.DENS_PHANTOM, 6)):
+        for _ in range(3):
+            h.density(kind, out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            h.density(kind, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        algo = (nin + 1) * plane
+        res[name] = {"ms_per_launch": ms, "algorithmic_bytes": algo, "GBps": algo / (ms / 1e3) / 1e9}
+    s = WL["box"] / n
+    nb = int(0.45 * n)
+    h.shell_mass(B.DENS_APPARENT, [0.0, 0.0, 0.0], s, nb)
+    t0 = time.perf_counter()
+    shells = h.shell_mass(B.DENS_APPARENT, [0.0, 0.0, 0.0], s, nb)
+    res["shell_mass_ms"] = (time.perf_counter() - t0) * 1e3
+    b, M, a0, G = WL["b"] * s, 1.0, WL["a0"], WL["G"]
+    ratios = {}
+    for R in (16, 32, 48):
+        closed = math.sqrt(M * a0 / G) * R * s / (1 + (b / (R * s)) ** 1.5)
+        ratios[str(R)] = sum(shells[:R]) / closed
+    res["enclosed_apparent_mass_vs_closed_form"] = ratios
+    res["note"] = "fields of the last solve; inputs larger than L2"
+    return res
+
+
 def run_learned(args, dev):
     """Learned warm start (sphere mixtures, 256^3, standard mu, sigma 1 px,
     G = a0 = 1): train the FNO on solver-made pairs, then time and score
@@ -484,6 +526,11 @@ def main():
                     "ref_two_cycle_rel": float(torch.linalg.norm(g_a - g_b)) / nr}
         h.sync()
 
+    # ---- densities of Eq. apparentdensity from the last solve's fields ---------
+    dens_info = None
+    if rank == 0:
+        dens_info = run_density(h, B, stream, args.steps)
+
     # ---- end to end through host buffers -------------------------------------
     cell_h = init["cell"].cpu().pin_memory()
     off_h = init["offset"].cpu().pin_memory()
@@ -540,7 +587,7 @@ def main():
                         "d2h_bytes_per_step": 36 * N},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern,
                 "ms_per_step_event_timed": ms_timed_mode / args.steps,
-                "learned": learned, "ensemble": ensemble}
+                "density": dens_info, "learned": learned, "ensemble": ensemble}
         if cpu:
             line["cpu_baseline"] = {"value": 1.0 / cpu["t_step"], "unit": "solves/s", "cores": cpu["cores"],
                                     "kind": "oracle",

@@ -182,6 +182,37 @@ int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess)
  * mond_pm_get_field(MOND_FIELD_SMOOTH). */
 int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out);
 
+/* Densities from a field of the last solve (Eq. apparentdensity, Sect. 2.1):
+ * rho = -(div g) / (4 pi G), the divergence taken with the periodic central
+ * difference (f[i+1] - f[i-1]) / (2 s) of the solver's gradients. */
+enum {
+  MOND_DENS_BARYONIC = 0, /* from g_N: rho_B (the deposit's density seen through the discrete operators) */
+  MOND_DENS_APPARENT = 1, /* from the MOND acceleration mesh: rho_A, baryonic plus apparent dark matter */
+  MOND_DENS_PHANTOM = 2   /* rho_A - rho_B, the phantom dark matter density */
+};
+
+/* Write the density `which` (MOND_DENS_*) of the fields of the last solve to
+ * out (device float32, n_f^3 in z, y, x order, 16-byte aligned, caller-owned).
+ * Enqueued on the handle's stream; does not synchronise. Errors: MOND_EINVAL
+ * (unknown kind, null or misaligned out), MOND_ESTATE (no solve yet). */
+int mond_pm_density(mond_pm_t h, int which, float* out);
+
+/* Mass of the density `which` in spherical shells about center (physical
+ * (x, y, z); cell i sits at (i - n_f/2) s): out[k] (host, nbins doubles) is the
+ * FP64 sum of rho s^3 over the cells whose centre lies at a minimum-image
+ * distance r with floor(r / dr) = k, 1 <= nbins <= 4096, dr > 0. The shell of
+ * a cell is decided in IEEE double with every operation rounded on its own.
+ * The cumulative sum is the enclosed mass M(r) of Eq. totalmass.
+ * Synchronises and returns any latched device error. */
+int mond_pm_shell_mass(mond_pm_t h, int which, const double center[3], double dr, int nbins, double* out);
+
+/* Eq. totalmass for the box W of cells lo..hi (inclusive per axis, (x, y, z),
+ * periodic, 1 <= hi - lo + 1 <= n_f): *out (host) = -(1/(4 pi G)) times the
+ * outward flux of the field through the faces of W, the field on a face the
+ * mean of the two cells it separates (so that it equals the box sum of
+ * mond_pm_density times s^3). Synchronises. */
+int mond_pm_box_mass(mond_pm_t h, int which, const int32_t lo[3], const int32_t hi[3], double* out);
+
 /* Force at the particles from the acceleration mesh of the last solve
  * (Eq. gi, same ball and Gaussian as the deposit, FP32 weights), then the
  * leapfrog step of Eq. motion: v += g dt; r += v dt; the cell becomes the

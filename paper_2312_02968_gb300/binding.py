@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libmondpm.so")
 MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
 WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW = 0, 1, 2, 3
 FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
+DENS_BARYONIC, DENS_APPARENT, DENS_PHANTOM = 0, 1, 2
 OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK = 1, 2, 3, 4, 5, 6
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
@@ -54,6 +55,10 @@ SIGNATURES = {
     "mond_pm_gather_push": (_I, [_P, _D]),
     "mond_pm_half_kick": (_I, [_P, _D]),
     "mond_pm_gather": (_I, [_P, _P]),
+    "mond_pm_density": (_I, [_P, _I, _P]),
+    "mond_pm_shell_mass": (_I, [_P, _I, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_D)]),
+    "mond_pm_box_mass": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(_D)]),
     "mond_pm_step": (_I, [_P, _D, _I, _I]),
     "mond_pm_step_host": (_I, [_P, _D, _I, _I, _P, _P, _P]),
     "mond_pm_diagnostics": (_I, [_P, ctypes.POINTER(Diag)]),
@@ -239,6 +244,29 @@ class MondPM:
         """Host tensors (pinned, contiguous) in and out; synchronises."""
         self._check(lib().mond_pm_step_host(self.h, float(dt), int(n_iter), int(warm), _ptr(cell_host),
                                             _ptr(offset_host), _ptr(vel_host)))
+
+    def density(self, which: int, out=None):
+        """Density `which` (DENS_*) of the last solve's fields as [n, n, n] float32."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty((self.nf, self.nf, self.nf), dtype=torch.float32, device=self.device)
+        self._check(lib().mond_pm_density(self.h, int(which), _ptr(out)))
+        return out
+
+    def shell_mass(self, which: int, center, dr: float, nbins: int) -> list:
+        """Mass of density `which` in shells [k dr, (k+1) dr) about center (FP64, host)."""
+        c = (_D * 3)(*[float(v) for v in center])
+        out = (_D * int(nbins))()
+        self._check(lib().mond_pm_shell_mass(self.h, int(which), c, float(dr), int(nbins), out))
+        return list(out)
+
+    def box_mass(self, which: int, lo, hi) -> float:
+        """Mass in the box of cells lo..hi (inclusive, (x, y, z)) from the flux of the field."""
+        a = (ctypes.c_int32 * 3)(*[int(v) for v in lo])
+        b = (ctypes.c_int32 * 3)(*[int(v) for v in hi])
+        out = _D(0.0)
+        self._check(lib().mond_pm_box_mass(self.h, int(which), a, b, ctypes.byref(out)))
+        return out.value
 
     def diagnostics(self) -> dict:
         d = Diag()

@@ -14,6 +14,7 @@
 #include "../../include/mond_pm.h"
 #include "internal.h"
 #include "launch.h"
+#include "apparent.cuh"
 #include "particles.cuh"
 
 namespace {
@@ -22,7 +23,8 @@ thread_local std::string g_create_error;
 
 struct Workspace {
   uint32_t* status;
-  double* red;       // 256 doubles: [0..10] particle diag, [16..17] plane sums, [32..] dH pairs
+  double* red;       // 256 + dens::MAX_BINS doubles: [0..10] particle diag, [16..17] plane sums,
+                     // [24] box flux, [32..160) dH pairs, [256..) shell masses
   unsigned long long* isum;  // integer sum slot
   int* emax;
   int* counters;     // work counters (deposit, gather)
@@ -85,7 +87,7 @@ size_t carve(int n, int r, int nb, int64_t maxp, char* base, Workspace* w) {
   const int lw = 2 * r + 1;
   Workspace t{};
   t.status = (uint32_t*)take(256);
-  t.red = (double*)take(sizeof(double) * 256);
+  t.red = (double*)take(sizeof(double) * (256 + dens::MAX_BINS));
   t.isum = (unsigned long long*)take(64);
   t.emax = (int*)take(64);
   t.counters = (int*)take(256);
@@ -243,6 +245,7 @@ struct mond_pm {
   int kacc = 0;
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false, density_given = false;
   bool gn_valid = false;  // w.gN holds the Newton field of the current density
+  bool have_fields = false;  // w.gN and w.acc hold the fields of a solve
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
@@ -672,6 +675,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
       h->last_iters = 0;
       h->have_solve = true;
+      h->have_fields = true;
       h->gn_valid = true;
       return MOND_OK;
     }
@@ -754,8 +758,22 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   }
   h->last_iters = K;
   h->have_solve = true;
+  h->have_fields = true;
   return MOND_OK;
 }
+
+// Field pair of a density kind: the density is -(div g - div g2)/(4 pi G).
+int density_fields(mond_pm* h, int which, const float** g, const float** g2) {
+  if (!h->have_fields) return fail(h, MOND_ESTATE, "density before any solve_field");
+  switch (which) {
+    case MOND_DENS_BARYONIC: *g = h->w.gN; *g2 = nullptr; return MOND_OK;
+    case MOND_DENS_APPARENT: *g = h->w.acc; *g2 = nullptr; return MOND_OK;
+    case MOND_DENS_PHANTOM: *g = h->w.acc; *g2 = h->w.gN; return MOND_OK;
+    default: return fail(h, MOND_EINVAL, "unknown density kind %d", which);
+  }
+}
+
+float density_scale(const mond_pm* h) { return (float)(-1.0 / (2.0 * h->s * 4.0 * M_PI * h->G)); }
 
 }  // namespace
 
@@ -1384,6 +1402,69 @@ int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out) {
   for (int j = 0; j < 64; j++)
     out->dH[j] = (h->track_dh && j < h->last_iters - 1 && dh[2 * j + 1] > 0) ? sqrt(dh[2 * j] / dh[2 * j + 1]) : NAN;
   return read_status(h);
+}
+
+int mond_pm_density(mond_pm_t h, int which, float* out) {
+  if (!h) return MOND_EINVAL;
+  if (!out || ((uintptr_t)out & 15)) return fail(h, MOND_EINVAL, "out must be a 16-byte aligned device pointer");
+  const float *g, *g2;
+  int rc = density_fields(h, which, &g, &g2);
+  if (rc) return rc;
+  const int64_t q = h->n3 / 4;
+  const int nb = (int)std::min<int64_t>((q + dens::NT - 1) / dens::NT, (int64_t)h->sms * 8);
+  dens::k_density<<<nb, dens::NT, 0, h->st>>>(h->nf, g, g2, density_scale(h), out);
+  h->launches++;
+  CK(cudaGetLastError());
+  return MOND_OK;
+}
+
+int mond_pm_shell_mass(mond_pm_t h, int which, const double center[3], double dr, int nbins, double* out) {
+  if (!h) return MOND_EINVAL;
+  if (!center || !out || !(dr > 0) || nbins < 1 || nbins > dens::MAX_BINS)
+    return fail(h, MOND_EINVAL, "shell_mass: center, out, dr > 0 and 1 <= nbins <= %d required", dens::MAX_BINS);
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(center[a])) return fail(h, MOND_EINVAL, "shell_mass: non-finite center");
+  const float *g, *g2;
+  int rc = density_fields(h, which, &g, &g2);
+  if (rc) return rc;
+  double* bins = h->w.red + 256;
+  CK(cudaMemsetAsync(bins, 0, sizeof(double) * nbins, h->st));
+  const int64_t q = h->n3 / 4;
+  const int nb = (int)std::min<int64_t>((q + dens::NT - 1) / dens::NT, (int64_t)h->sms * 4);
+  dens::k_shell_mass<<<nb, dens::NT, 0, h->st>>>(h->nf, g, g2, density_scale(h), h->s, center[0], center[1],
+                                                 center[2], dr, nbins, bins);
+  h->launches++;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, bins, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->st));
+  return read_status(h);
+}
+
+int mond_pm_box_mass(mond_pm_t h, int which, const int32_t lo[3], const int32_t hi[3], double* out) {
+  if (!h) return MOND_EINVAL;
+  if (!lo || !hi || !out) return fail(h, MOND_EINVAL, "box_mass: null argument");
+  dens::Box bx{};
+  for (int a = 0; a < 3; a++) {
+    const int64_t w = (int64_t)hi[a] - lo[a] + 1;
+    if (w < 1 || w > h->nf) return fail(h, MOND_EINVAL, "box_mass: extent %lld on axis %d", (long long)w, a);
+    bx.lo[a] = lo[a];
+    bx.w[a] = (int)w;
+  }
+  const float *g, *g2;
+  int rc = density_fields(h, which, &g, &g2);
+  if (rc) return rc;
+  double* acc = h->w.red + 24;
+  CK(cudaMemsetAsync(acc, 0, sizeof(double), h->st));
+  int64_t faces = 0;
+  for (int a = 0; a < 3; a++) faces += 2 * (int64_t)bx.w[(a + 1) % 3] * bx.w[(a + 2) % 3];
+  const int nb = (int)std::min<int64_t>((faces + dens::NT - 1) / dens::NT, (int64_t)h->sms * 4);
+  dens::k_box_flux<<<nb, dens::NT, 0, h->st>>>(h->nf, g, g2, h->s, bx, acc);
+  h->launches++;
+  CK(cudaGetLastError());
+  double flux = 0.0;
+  CK(cudaMemcpyAsync(&flux, acc, sizeof flux, cudaMemcpyDeviceToHost, h->st));
+  rc = read_status(h);
+  *out = -flux / (4.0 * M_PI * h->G);
+  return rc;
 }
 
 int mond_pm_get_field(mond_pm_t h, int which, float* dst) {
