@@ -778,3 +778,50 @@ void ora_shell_mass(int n, double s, const double* rho, const double* c, double 
         if (fk < nbins) out[(int)fk] += rho[idx3(n, x, y, z)] * s * s * s;
       }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mesh-interpolating gather: the node-smoothed acceleration (the force Eq.  */
+/* gi gives a particle on each pixel centre) interpolated at the particles.  */
+/* ------------------------------------------------------------------------ */
+
+/* Interpolation weights along one axis for a particle at fraction t in [0, 1)
+ * past node b. order 1: linear, nodes b, b+1. order 3: Keys' cubic
+ * convolution kernel with a = -1/2, nodes b-1 .. b+2:
+ *   W(x) = 1.5|x|^3 - 2.5|x|^2 + 1             for |x| <= 1,
+ *   W(x) = -0.5|x|^3 + 2.5|x|^2 - 4|x| + 2     for 1 < |x| < 2. */
+static double keys(double x) {
+  x = fabs(x);
+  if (x <= 1.0) return 1.5 * x * x * x - 2.5 * x * x + 1.0;
+  if (x < 2.0) return -0.5 * x * x * x + 2.5 * x * x - 4.0 * x + 2.0;
+  return 0.0;
+}
+
+/* g_i = sum over the interpolation nodes of the product of the per-axis
+ * weights times S at the node (periodic). The particle sits at cell + off
+ * (pixel units); the node below it is b = cell - 1 when off < 0, else cell.
+ * S: 3 planes; out: [N][3]. */
+void ora_interp_gather(int n, int order, const double* S, int64_t N, const int32_t* cell, const double* off,
+                       double* out) {
+  int64_t tot = (int64_t)n * n * n;
+  int lo = order == 3 ? -1 : 0, hi = order == 3 ? 2 : 1;
+#pragma omp parallel for
+  for (int64_t i = 0; i < N; i++) {
+    int b[3];
+    double w[3][4];
+    for (int a = 0; a < 3; a++) {
+      double o = off[3 * i + a];
+      b[a] = cell[3 * i + a] + (o < 0 ? -1 : 0);
+      double t = o < 0 ? o + 1.0 : o;
+      for (int j = lo; j <= hi; j++) w[a][j - lo] = order == 3 ? keys(t - j) : (j == 0 ? 1.0 - t : t);
+    }
+    double g[3] = {0, 0, 0};
+    for (int dz = lo; dz <= hi; dz++)
+      for (int dy = lo; dy <= hi; dy++)
+        for (int dx = lo; dx <= hi; dx++) {
+          double wt = w[0][dx - lo] * w[1][dy - lo] * w[2][dz - lo];
+          int64_t j = idx3(n, wrap(b[0] + dx, n), wrap(b[1] + dy, n), wrap(b[2] + dz, n));
+          for (int a = 0; a < 3; a++) g[a] += wt * S[a * tot + j];
+        }
+    for (int a = 0; a < 3; a++) out[3 * i + a] = g[a];
+  }
+}
