@@ -240,6 +240,46 @@ def run_density(h, B, stream, steps):
     return res
 
 
+def run_interp(h, B, stream, t, init, steps, warmup):
+    """The mesh-interpolating gather (linear and Keys cubic interpolation of
+    the node-smoothed field) in place of Eq. gi: graph-replayed steps per
+    second on the same workload, and the force error of each against Eq. gi
+    on the same density (relative L2 over the particles)."""
+    import torch
+
+    K, dt = WL["K"], WL["dt"]
+    res = {}
+    for order in (1, 3):
+        for k in t:
+            t[k].copy_(init[k])
+        h.set_option(B.OPT_GATHER, order)
+        for _ in range(warmup):
+            h.step(dt, K, B.WARM_NONE)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            h.step(dt, K, B.WARM_NONE)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # accuracy on the current particles: exact ball sums, then the interpolation
+        h.set_option(B.OPT_GATHER, 0)
+        h.deposit()
+        h.solve_field(K, B.WARM_NONE)
+        g_exact = h.gather().double()
+        h.set_option(B.OPT_GATHER, order)
+        h.solve_field(K, B.WARM_NONE)
+        g_int = h.gather().double()
+        err = float(torch.linalg.norm(g_int - g_exact) / torch.linalg.norm(g_exact))
+        res["linear" if order == 1 else "cubic"] = {"steps_per_s": 1000.0 / ms, "ms_per_step": ms,
+                                                    "force_rel_err_vs_eq_gi": err}
+    h.set_option(B.OPT_GATHER, 0)
+    h.sync()
+    res["note"] = "same workload and K; node-smoothed mesh made by the final pass, interpolated at the particles"
+    return res
+
+
 def run_learned(args, dev):
     """Learned warm start (sphere mixtures, 256^3, standard mu, sigma 1 px,
     G = a0 = 1): train the FNO on solver-made pairs, then time and score
@@ -531,6 +571,10 @@ def main():
     if rank == 0:
         dens_info = run_density(h, B, stream, args.steps)
 
+    interp_info = None
+    if rank == 0:
+        interp_info = run_interp(h, B, stream, t, init, args.steps, args.warmup)
+
     # ---- end to end through host buffers -------------------------------------
     cell_h = init["cell"].cpu().pin_memory()
     off_h = init["offset"].cpu().pin_memory()
@@ -587,7 +631,7 @@ def main():
                         "d2h_bytes_per_step": 36 * N},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern,
                 "ms_per_step_event_timed": ms_timed_mode / args.steps,
-                "density": dens_info, "learned": learned, "ensemble": ensemble}
+                "density": dens_info, "interp_gather": interp_info, "learned": learned, "ensemble": ensemble}
         if cpu:
             line["cpu_baseline"] = {"value": 1.0 / cpu["t_step"], "unit": "solves/s", "cores": cpu["cores"],
                                     "kind": "oracle",

@@ -62,7 +62,8 @@ enum {
   MOND_FIELD_GN = 1,     /* Newtonian field g_N of the last solve, 3 planes */
   MOND_FIELD_H = 2,      /* H state: the last H formed by a solve (warm-start state), 3 planes */
   MOND_FIELD_PHI = 3,    /* MOND potential phi of the last solve, 1 plane (needs MOND_OPT_KEEP_PHI) */
-  MOND_FIELD_ACC = 4,    /* acceleration mesh a = -grad_FD phi of the last solve, 3 planes */
+  MOND_FIELD_ACC = 4,    /* acceleration mesh a = -grad_FD phi of the last solve, 3 planes (node-smoothed
+                            when the solve ran with MOND_OPT_GATHER 1 or 3) */
   MOND_FIELD_SMOOTH = 5  /* node-smoothed acceleration of the last mond_pm_smooth, 3 planes */
 };
 
@@ -89,8 +90,16 @@ enum {
   MOND_OPT_TIMING = 4,    /* value 1: bracket every launch with CUDA events (see mond_pm_kernel_stats) */
   MOND_OPT_PIPELINED = 5, /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
                              0: one tile per CTA with plain loads (same results) */
-  MOND_OPT_CHUNK = 6      /* particles per deposit/gather work item: a power of two in 256..4096
+  MOND_OPT_CHUNK = 6,     /* particles per deposit/gather work item: a power of two in 256..4096
                              (default 2048; same results) */
+  MOND_OPT_GATHER = 7     /* force at the particles. 0 (default): Eq. gi, the ball sum at each particle.
+                             1 or 3: the mesh-interpolating gather -- the final pass of a solve (n_iter >= 1)
+                             also multiplies the acceleration spectrum by the smoothing spectrum, so that
+                             MOND_FIELD_ACC holds the node-smoothed field of mond_pm_smooth, and the force
+                             at a particle is the linear (1) or Keys cubic (3, a = -1/2) interpolation of
+                             that field at its position: an approximation of Eq. gi whose error the caller
+                             measures against variant 0. A gather whose variant disagrees with the mesh
+                             the last solve made fails with MOND_ESTATE. */
 };
 
 /* Per kernel class: launches, device time between the events around each
@@ -212,6 +221,17 @@ int mond_pm_shell_mass(mond_pm_t h, int which, const double center[3], double dr
  * mean of the two cells it separates (so that it equals the box sum of
  * mond_pm_density times s^3). Synchronises. */
 int mond_pm_box_mass(mond_pm_t h, int which, const int32_t lo[3], const int32_t hi[3], double* out);
+
+/* External field by a dipole layer (Sect. 5.3): every later solve adds the
+ * density +mass/(n_f^2 s^3) on the last plane of the domain along `axis`
+ * (0, 1, 2 for x, y, z) and -mass/(n_f^2 s^3) on the first plane, the planes
+ * farthest from a system centred in the domain; the layer's net mass is zero.
+ * In Newtonian gravity it makes the field 4 pi G mass s / L^3 along +axis
+ * everywhere away from it (L = n_f s); the MOND field follows from the solve.
+ * The deposit's density (MOND_FIELD_RHO, the diagnostics) does not include it;
+ * g_N and the densities of mond_pm_density do. axis = -1 removes the layer.
+ * Enqueues nothing. Errors: MOND_EINVAL (axis outside -1..2, non-finite mass). */
+int mond_pm_set_dipole_layer(mond_pm_t h, int axis, double mass);
 
 /* Force at the particles from the acceleration mesh of the last solve
  * (Eq. gi, same ball and Gaussian as the deposit, FP32 weights), then the

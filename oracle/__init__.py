@@ -32,6 +32,9 @@ What pins each function (tests in ``tests/test_oracle_*.py``):
                   theorem); the total mass of a periodic box is zero.
   shell_mass      brute-force sums on small grids; enclosed M_A(r) of the
                   isothermal sphere (Sect. 4.3 closed form).
+  dipole_layer    Newtonian field of the layer away from it equals the
+                  closed form 4 pi G M s / L^3 (Gauss's law on the periodic
+                  box); zero net mass; the field reverses with the sign.
   node_smoothed   Eq. gi at pixel centres: the spectrum of the smoothing of
                   one mode equals the ball sum of the Gaussian (numpy).
   interp_gather   reproduces linear (order 1) and quadratic (order 3)
@@ -269,6 +272,20 @@ def shell_mass(rho, s: float, center, dr: float, nbins: int):
     out = np.zeros(nbins)
     lib().ora_shell_mass(rho.shape[0], float(s), _p(rho), _p(c), float(dr), int(nbins), _p(out))
     return out
+
+
+def dipole_layer(n: int, s: float, axis: int, mass: float):
+    """Density of the external-field dipole layer (Sect. 5.3): +mass spread
+    over the last plane along axis (0, 1, 2 = x, y, z) and -mass over the
+    first, as mass per s^3 on [n, n, n] (z, y, x)."""
+    rho = np.zeros((n, n, n))
+    sl_hi = [slice(None)] * 3
+    sl_lo = [slice(None)] * 3
+    sl_hi[2 - axis] = n - 1
+    sl_lo[2 - axis] = 0
+    rho[tuple(sl_hi)] += mass / (n * n * s ** 3)
+    rho[tuple(sl_lo)] -= mass / (n * n * s ** 3)
+    return rho
 
 
 def node_smoothed(sigma: float, acc):

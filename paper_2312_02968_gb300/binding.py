@@ -17,7 +17,7 @@ MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
 WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW = 0, 1, 2, 3
 FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
 DENS_BARYONIC, DENS_APPARENT, DENS_PHANTOM = 0, 1, 2
-OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK = 1, 2, 3, 4, 5, 6
+OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK, OPT_GATHER = 1, 2, 3, 4, 5, 6, 7
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
 
@@ -56,6 +56,7 @@ SIGNATURES = {
     "mond_pm_half_kick": (_I, [_P, _D]),
     "mond_pm_gather": (_I, [_P, _P]),
     "mond_pm_density": (_I, [_P, _I, _P]),
+    "mond_pm_set_dipole_layer": (_I, [_P, _I, _D]),
     "mond_pm_shell_mass": (_I, [_P, _I, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_D)]),
     "mond_pm_box_mass": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(_D)]),
@@ -244,6 +245,10 @@ class MondPM:
         """Host tensors (pinned, contiguous) in and out; synchronises."""
         self._check(lib().mond_pm_step_host(self.h, float(dt), int(n_iter), int(warm), _ptr(cell_host),
                                             _ptr(offset_host), _ptr(vel_host)))
+
+    def set_dipole_layer(self, axis: int, mass: float):
+        """External field by a dipole layer of masses +-mass on the domain's end planes along axis (-1: none)."""
+        self._check(lib().mond_pm_set_dipole_layer(self.h, int(axis), float(mass)))
 
     def density(self, which: int, out=None):
         """Density `which` (DENS_*) of the last solve's fields as [n, n, n] float32."""

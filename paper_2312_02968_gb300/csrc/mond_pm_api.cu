@@ -246,6 +246,10 @@ struct mond_pm {
   bool have_dep = false, have_solve = false, have_khat = false, have_smooth = false, density_given = false;
   bool gn_valid = false;  // w.gN holds the Newton field of the current density
   bool have_fields = false;  // w.gN and w.acc hold the fields of a solve
+  int gather_mode = 0;        // MOND_OPT_GATHER: 0 Eq. gi, 1 / 3 interpolation order
+  int ext_axis = -1;          // external-field dipole layer (mond_pm_set_dipole_layer), -1 none
+  double ext_mass = 0.0;
+  bool acc_smoothed = false;  // w.acc holds the node-smoothed field (final pass with the smoothing spectrum)
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
@@ -253,12 +257,15 @@ struct mond_pm {
   cudaGraphExec_t gexec = nullptr;
   struct GraphKey {
     double dt;
-    int n_iter, warm, keep_phi, track_dh, pipelined, chunk;
+    int n_iter, warm, keep_phi, track_dh, pipelined, chunk, gather_mode, ext_axis;
+    double ext_mass;
     int64_t N;
     const void* cell;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
-             track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk && N == o.N && cell == o.cell;
+             track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
+             gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
+             cell == o.cell;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -411,12 +418,13 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
   a.kv = h->w.kv;
   a.kp = h->w.kp;
   a.tw = h->w.tw;
-  a.khat = h->w.khat;
+  // the final pass multiplies by the smoothing spectrum only for the interpolating gather
+  a.khat = (mode == passes::Z_FINAL && !h->gather_mode) ? nullptr : h->w.khat;
   a.norm = (float)(1.0 / ((double)h->nf * h->nf * h->nf));
   a.coef = (float)(4.0 * M_PI * h->G);
   int nin = (mode == passes::Z_NEWTON) ? 1 : 3;
   int nwr = (mode == passes::Z_NEWTON || mode == passes::Z_FINAL) ? nout : 3;
-  double zb = (nin + nwr) * spec_bytes(h) + (mode == passes::Z_SMOOTH ? 0.5 * real_bytes(h) : 0.0);
+  double zb = (nin + nwr) * spec_bytes(h) + (a.khat && mode != passes::Z_NEWTON ? 0.5 * real_bytes(h) : 0.0);
   int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : mode == passes::Z_DIV ? KC_Z_DIV
            : mode == passes::Z_FINAL ? KC_Z_FINAL : KC_Z_SMOOTH;
   Timed tm(h, zc, zb);
@@ -622,6 +630,19 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   g.gnorm = (float)(1.0 / (h->sigma * sqrt(2.0 * M_PI)));
   g.work_counter = h->w.counters + 1;
   g.status = h->w.status;
+  if ((h->gather_mode != 0) != h->acc_smoothed)
+    return fail(h, MOND_ESTATE, h->gather_mode ? "the interpolating gather needs a solve with n_iter >= 1 made with "
+                                                 "MOND_OPT_GATHER set"
+                                               : "the acceleration mesh is smoothed: solve again with MOND_OPT_GATHER 0");
+  if (h->gather_mode) {
+    Timed tm(h, KC_GATHER, 3.0 * real_bytes(h) + 64.0 * h->N);
+    const int nbk = h->sms * 8;
+    if (h->gather_mode == 1) parts::k_interp_push<1><<<nbk, 256, 0, h->st>>>(g);
+    else parts::k_interp_push<3><<<nbk, 256, 0, h->st>>>(g);
+    h->launches++;
+    CK(cudaGetLastError());
+    return MOND_OK;
+  }
   CK(cudaMemsetAsync(h->w.counters + 1, 0, sizeof(int), h->st));
   size_t sm = gat_smem(h);
   {
@@ -639,6 +660,17 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
   return MOND_OK;
 }
 
+// The smoothing spectrum (ball-truncated Gaussian sampled at the nodes), made once.
+int ensure_khat(mond_pm* h) {
+  if (h->have_khat) return MOND_OK;
+  int64_t tot = (int64_t)h->nf * h->nf * (h->nf / 2 + 1);
+  k_khat<<<(unsigned)((tot + 255) / 256), 256, 0, h->st>>>(h->nf, h->r, h->sigma, h->w.khat);
+  h->launches++;
+  CK(cudaGetLastError());
+  h->have_khat = true;
+  return MOND_OK;
+}
+
 // Field solve: the pass sequence of the iteration (see mond_pm_solve_field).
 int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   const int nout = h->keep_phi ? 4 : 3;
@@ -653,12 +685,16 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     x.dep = h->w.dep;
     x.rho_out = h->w.rho;
     x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
+    x.ext_axis1 = h->ext_axis + 1;
+    x.ext_rho = (float)(h->ext_mass / ((double)h->nf * h->nf * h->s * h->s * h->s));
     if (h->density_given) {
       // density set by mond_pm_set_density: forward x-transform of the FP32 plane
       passes::XArgs xf{};
       xf.ncomp = 1;
       xf.spec = W;
       xf.real_in = h->w.rho;
+      xf.ext_axis1 = x.ext_axis1;
+      xf.ext_rho = x.ext_rho;
       PK(xpass(h, passes::X_FWD, xf));
     } else {
       PK(xpass(h, passes::X_RHO, x));
@@ -674,6 +710,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       PK(xpass(h, passes::X_INV, xi));
       CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
       h->last_iters = 0;
+      h->acc_smoothed = false;
       h->have_solve = true;
       h->have_fields = true;
       h->gn_valid = true;
@@ -719,6 +756,10 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     PK(ypass(h, -1, W, 3));
     const bool last = (j == K);
     if (last) {
+      if (h->gather_mode) {
+        int rk = ensure_khat(h);
+        if (rk) return rk;
+      }
       PK(zpass(h, passes::Z_FINAL, W, A, nout));
       PK(ypass(h, +1, A, nout));
       passes::XArgs xi{};
@@ -726,6 +767,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       xi.spec = A;
       xi.real_out = h->w.acc;
       PK(xpass(h, passes::X_INV, xi));
+      h->acc_smoothed = h->gather_mode != 0;
       if (warm == MOND_WARM_NONE || warm == MOND_WARM_GUESS_RAW) break;  // no H state to carry on
     }
     PK(zpass(h, passes::Z_CURL, W, W, 3));
@@ -973,6 +1015,10 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_PIPELINED:
       h->pipelined = value ? 1 : 0;
       return MOND_OK;
+    case MOND_OPT_GATHER:
+      if (value != 0 && value != 1 && value != 3) return fail(h, MOND_EINVAL, "gather variant must be 0, 1 or 3");
+      h->gather_mode = (int)value;
+      return value ? ensure_khat(h) : MOND_OK;  // made here, outside any stream capture
     case MOND_OPT_TIMING:
       collect_timing(h);
       h->timing = value ? 1 : 0;
@@ -1015,6 +1061,15 @@ int mond_pm_deposit(mond_pm_t h) {
   return do_deposit(h);
 }
 
+int mond_pm_set_dipole_layer(mond_pm_t h, int axis, double mass) {
+  if (!h) return MOND_EINVAL;
+  if (axis < -1 || axis > 2 || !std::isfinite(mass)) return fail(h, MOND_EINVAL, "dipole layer: axis -1..2, finite mass");
+  h->ext_axis = axis;
+  h->ext_mass = axis >= 0 ? mass : 0.0;
+  h->gn_valid = false;  // the solved density changes
+  return MOND_OK;
+}
+
 int mond_pm_set_density(mond_pm_t h, const float* rho) {
   if (!h || !rho) return MOND_EINVAL;
   CK(cudaMemcpyAsync(h->w.rho, rho, sizeof(float) * h->n3, cudaMemcpyDeviceToDevice, h->st));
@@ -1039,13 +1094,8 @@ int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess)
 int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out) {
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "smooth before solve_field");
-  if (!h->have_khat) {
-    int64_t tot = (int64_t)h->nf * h->nf * (h->nf / 2 + 1);
-    k_khat<<<(unsigned)((tot + 255) / 256), 256, 0, h->st>>>(h->nf, h->r, h->sigma, h->w.khat);
-    h->launches++;
-    CK(cudaGetLastError());
-    h->have_khat = true;
-  }
+  int rk = ensure_khat(h);
+  if (rk) return rk;
   passes::XArgs xf{};
   xf.ncomp = 3;
   xf.spec = h->w.A;
@@ -1068,8 +1118,10 @@ int mond_pm_gather_push(mond_pm_t h, double dt) {
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "gather_push before solve_field");
   int rc = do_gather(h, nullptr, dt, 1, 1);
-  h->have_dep = false;  // particles moved: the binning is stale
-  h->have_solve = false;
+  if (rc == MOND_OK) {
+    h->have_dep = false;  // particles moved: the binning is stale
+    h->have_solve = false;
+  }
   return rc;
 }
 
@@ -1105,6 +1157,7 @@ int step_checks(mond_pm_t h, int n_iter, int warm) {
   if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
   if (warm != MOND_WARM_NONE && warm != MOND_WARM_PREV) return fail(h, MOND_EINVAL, "step takes warm NONE or PREV");
   if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
+  if (h->gather_mode && n_iter == 0) return fail(h, MOND_EINVAL, "the interpolating gather needs n_iter >= 1");
   return MOND_OK;
 }
 
@@ -1115,7 +1168,8 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   if (!capturable(h->st)) return fail(h, MOND_ESTATE, "a captured step needs a non-default stream");
   int rc = step_checks(h, n_iter, warm);
   if (rc) return rc;
-  const mond_pm::GraphKey key{dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->N, h->cell};
+  const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
+                              h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -1150,6 +1204,8 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
 int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
   if (!h) return MOND_EINVAL;
   if (h->use_graph && !h->timing) return step_graph(h, dt, n_iter, warm);
+  const int rc = step_checks(h, n_iter, warm);
+  if (rc) return rc;
   return step_direct(h, dt, n_iter, warm);
 }
 
@@ -1227,7 +1283,8 @@ int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, in
   }
   std::vector<mond_pm::GraphKey> keys;
   for (auto h : b->hs)
-    keys.push_back({dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->N, h->cell});
+    keys.push_back({dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->gather_mode, h->ext_axis,
+                    h->ext_mass, h->N, h->cell});
   bool same = b->gexec && keys.size() == b->keys.size();
   for (size_t i = 0; same && i < keys.size(); i++) same = keys[i] == b->keys[i];
   if (!same) {

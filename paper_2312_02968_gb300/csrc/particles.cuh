@@ -678,6 +678,92 @@ __global__ void __launch_bounds__(GAT_NT, 2) k_gather_push(GatArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Mesh-interpolating gather. The acceleration mesh then holds the
+// node-smoothed field (the force Eq. gi gives a particle on each pixel
+// centre); the force at a particle is the linear (ORDER 1) or Keys cubic
+// (ORDER 3, a = -1/2) interpolation of that field at the particle's position,
+// followed by the kick and drift of k_gather_push. One thread per particle, in
+// binned order, so that neighbouring threads read neighbouring nodes.
+// ---------------------------------------------------------------------------
+// Weights of the nodes -1, 0, 1, 2 for a point at fraction t in [0, 1) past
+// node 0: Keys' kernel at distances 1 + t, t, 1 - t, 2 - t.
+__device__ __forceinline__ void keys_weights(float t, float* w) {
+  const float u = 1.0f - t;
+  w[1] = (1.5f * t - 2.5f) * t * t + 1.0f;
+  w[2] = (1.5f * u - 2.5f) * u * u + 1.0f;
+  const float p = 1.0f + t, q = 2.0f - t;
+  w[0] = ((-0.5f * p + 2.5f) * p - 4.0f) * p + 2.0f;
+  w[3] = ((-0.5f * q + 2.5f) * q - 4.0f) * q + 2.0f;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_interp_push(GatArgs a) {
+  constexpr int NW = ORDER == 3 ? 4 : 2;
+  constexpr int LO = ORDER == 3 ? -1 : 0;
+  const int nbinned = __ldg(a.tile_start + a.ntile);
+  const int n = a.n;
+  const int64_t n3 = (int64_t)n * n * n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nbinned; q += gridDim.x * blockDim.x) {
+    const uint32_t i = __ldg(a.perm + q);
+    int c[3], b[3];
+    float w[3][NW];
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      c[ax] = a.cell[3 * i + ax];
+      const float o = a.off[3 * i + ax];
+      b[ax] = c[ax] + (o < 0.f ? -1 : 0) + LO;
+      const float t = o < 0.f ? o + 1.0f : o;
+      if constexpr (ORDER == 3) {
+        keys_weights(t, w[ax]);
+      } else {
+        w[ax][0] = 1.0f - t;
+        w[ax][1] = t;
+      }
+    }
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < NW; dz++) {
+      int z = b[2] + dz;
+      z += z < 0 ? n : (z >= n ? -n : 0);
+#pragma unroll
+      for (int dy = 0; dy < NW; dy++) {
+        int y = b[1] + dy;
+        y += y < 0 ? n : (y >= n ? -n : 0);
+        const float wyz = w[1][dy] * w[2][dz];
+        const int64_t row = ((int64_t)z * n + y) * n;
+#pragma unroll
+        for (int dx = 0; dx < NW; dx++) {
+          int x = b[0] + dx;
+          x += x < 0 ? n : (x >= n ? -n : 0);
+          const float wt = w[0][dx] * wyz;
+          g0 = fmaf(wt, __ldg(a.acc + row + x), g0);
+          g1 = fmaf(wt, __ldg(a.acc + n3 + row + x), g1);
+          g2 = fmaf(wt, __ldg(a.acc + 2 * n3 + row + x), g2);
+        }
+      }
+    }
+    const float g[3] = {g0, g1, g2};
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      if (a.g_out) a.g_out[3 * i + ax] = g[ax];
+      if (!isfinite(g[ax])) set_status(a.status, ST_NAN);
+      if (a.do_kick) {
+        const float v = a.vel[3 * i + ax] + g[ax] * a.dt;
+        a.vel[3 * i + ax] = v;
+        if (a.do_drift) {
+          const float o = a.off[3 * i + ax] + v * a.dt_over_s;
+          const float sh = floorf(o + 0.5f);
+          int cc = c[ax] + (int)sh;
+          cc += cc < 0 ? n : (cc >= n ? -n : 0);
+          a.off[3 * i + ax] = o - sh;
+          a.cell[3 * i + ax] = cc;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 particle diagnostics: slots [0] mass, [1..3] momentum, [4..6] sum m x,
 // [7..9] angular momentum about the origin, [10] kinetic energy.
 // ---------------------------------------------------------------------------

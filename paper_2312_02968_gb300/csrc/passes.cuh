@@ -70,6 +70,8 @@ struct XArgs {
   uint64_t* dep;         // X_RHO: accumulator
   float* rho_out;        // X_RHO: density plane (may be null)
   double rho_scale;      // X_RHO: 2^-Kacc / s^3
+  int ext_axis1;         // X_RHO, X_FWD of a density: 1 + axis of the external-field dipole layer, 0 none
+  float ext_rho;         // its density: +ext_rho on the last plane along that axis, -ext_rho on the first
   double* red;           // dH reduction slots (2 doubles) or null
   const float2* tw;      // twiddles, N entries
   uint32_t* status;
@@ -129,6 +131,23 @@ __device__ __forceinline__ float mu_factor(int kind, float gm, float a0) {
 // ---------------------------------------------------------------------------
 // x-pass
 // ---------------------------------------------------------------------------
+// Dipole layer of the external field (Sect. 5.3) at samples x, x + 1 of line
+// `line` (= z N + y): +ext_rho on the last plane along axis ext_axis1 - 1,
+// -ext_rho on the first.
+template <int N>
+__device__ __forceinline__ float2 dipole2(const XArgs& a, int64_t line, int x) {
+  int v0, v1;
+  if (a.ext_axis1 == 1) {
+    v0 = x;
+    v1 = x + 1;
+  } else {
+    v0 = v1 = a.ext_axis1 == 2 ? (int)(line % N) : (int)(line / N);
+  }
+  const float e0 = v0 == N - 1 ? a.ext_rho : (v0 == 0 ? -a.ext_rho : 0.f);
+  const float e1 = v1 == N - 1 ? a.ext_rho : (v1 == 0 ? -a.ext_rho : 0.f);
+  return make_float2(e0, e1);
+}
+
 template <int N>
 __device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict__ g, int64_t line0, int tid) {
   using C = XCfg<N>;
@@ -253,9 +272,19 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
       float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.x), a.rho_scale));
       float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.y), a.rho_scale));
       if (a.rho_out) *reinterpret_cast<float2*>(a.rho_out + ri) = make_float2(r0, r1);
+      if (a.ext_axis1) {
+        const float2 e = dipole2<N>(a, line0 + l, 2 * j);
+        r0 += e.x;
+        r1 += e.y;
+      }
       *p0 = make_float2(r0, r1);
     } else if constexpr (MODE == X_FWD) {
       for (int c = 0; c < nc; c++) p0[c * TILE] = *reinterpret_cast<const float2*>(a.real_in + (int64_t)c * N * N * N + ri);
+      if (a.ext_axis1) {
+        const float2 e = dipole2<N>(a, line0 + l, 2 * j);
+        p0[0].x += e.x;
+        p0[0].y += e.y;
+      }
     } else if constexpr (MODE == X_INV) {
       for (int c = 0; c < nc; c++) {
         float2 v = p0[c * TILE];
@@ -479,11 +508,14 @@ __global__ void __launch_bounds__(NT) k_zpass(ZArgs a) {
           if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
         float f = A * a.norm;
         float2 aS = cscale(S, f);
-        // a^ = -i kappa phi^ = kappa A S
+        // a^ = -i kappa phi^ = kappa A S, times the smoothing spectrum when
+        // the mesh is to hold the node-smoothed field
+        const float fk = a.khat ? a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] : 1.0f;
+        const float2 aK = cscale(aS, fk);
         float2* dst = tile;
-        dst[i] = cscale(aS, kpx);
-        dst[T + i] = cscale(aS, kpy);
-        dst[2 * T + i] = cscale(aS, kpz);
+        dst[i] = cscale(aK, kpx);
+        dst[T + i] = cscale(aK, kpy);
+        dst[2 * T + i] = cscale(aK, kpz);
         if (nout_extra == 4) dst[3 * T + i] = cmul_i<1>(aS);
       }
       if constexpr (MODE == Z_CURL || MODE == Z_DIV) {
@@ -637,53 +669,6 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(const __grid_constant__ tma::
   pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
 }
 
-// Spectral operator of a z-pass at one point (kx = col, ky = y, kz = row) of a
-// tile with ntile components at stride T; see k_zpass for the formulas.
-template <int N, int MODE>
-__device__ __forceinline__ void zop(float2* tile, int T, int i, int col, int row, int y, const float* kv,
-                                    const float* kp, const PipeZArgs& a) {
-  const float kx = kv[col], ky = kv[y], kz = kv[row];
-  const bool nx = (col == N / 2), ny = (y == N / 2), nz = (row == N / 2);
-  const float kk = kx * kx + ky * ky + kz * kz;
-  const float A = kk > 0.f ? 1.0f / kk : 0.f;
-  const float kpx = kp[col], kpy = kp[y], kpz = kp[row];
-  if constexpr (MODE == Z_NEWTON) {
-    const float2 r = tile[i];
-    const float f = a.coef * A * a.norm;
-    const float2 ir = cmul_i<1>(r);
-    tile[i] = cscale(ir, f * kpx);
-    tile[T + i] = cscale(ir, f * kpy);
-    tile[2 * T + i] = cscale(ir, f * kpz);
-    if (a.nout == 4) tile[3 * T + i] = cscale(r, -f);
-  } else if constexpr (MODE == Z_SMOOTH) {
-    const int64_t kidx = ((int64_t)row * N + y) * (N / 2 + 1) + col;
-    const float f = a.khat[kidx] * a.norm;
-    for (int c = 0; c < 3; c++) tile[c * T + i] = cscale(tile[c * T + i], f);
-  } else {
-    const float2 gg[3] = {tile[i], tile[T + i], tile[2 * T + i]};
-    const float k3[3] = {kx, ky, kz};
-    const bool n3[3] = {nx, ny, nz};
-    if constexpr (MODE == Z_FINAL) {
-      float2 S = make_float2(0.f, 0.f);
-      for (int b = 0; b < 3; b++)
-        if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
-      const float2 aS = cscale(S, A * a.norm);
-      tile[i] = cscale(aS, kpx);
-      tile[T + i] = cscale(aS, kpy);
-      tile[2 * T + i] = cscale(aS, kpz);
-      if (a.nout == 4) tile[3 * T + i] = cmul_i<1>(aS);
-    } else {
-      for (int aa = 0; aa < 3; aa++) {
-        float2 t = make_float2(0.f, 0.f);
-        for (int b = 0; b < 3; b++)
-          if (aa == b || n3[aa] == n3[b]) t = cadd(t, cscale(gg[b], k3[aa] * k3[b] * A));
-        const float2 o = (MODE == Z_DIV) ? csub(gg[aa], t) : t;
-        tile[aa * T + i] = cscale(o, a.norm);
-      }
-    }
-  }
-}
-
 // z-pass over the tile of (column block, y): forward z, the spectral
 // operator, inverse z. Each stage holds a vector region [z row][3][column]
 // (4-D maps with the component as a dimension, so one FFT call transforms the
@@ -789,9 +774,12 @@ __global__ void __launch_bounds__(NTZ, 2) k_zpass_pipe(const __grid_constant__ t
           for (int b = 0; b < 3; b++)
             if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
           const float2 aS = cscale(S, A * a.norm);
-          v[0] = cscale(aS, kp[col]);
-          v[P] = cscale(aS, kpy);
-          v[2 * P] = cscale(aS, kp[row]);
+          // times the smoothing spectrum when the mesh is to hold the node-smoothed field
+          const float fk = a.khat ? a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] : 1.0f;
+          const float2 aK = cscale(aS, fk);
+          v[0] = cscale(aK, kp[col]);
+          v[P] = cscale(aK, kpy);
+          v[2 * P] = cscale(aK, kp[row]);
           if constexpr (SC) *sc = cmul_i<1>(aS);
         } else {
           // P_ab = k_a k_b A, off-diagonal terms dropped when exactly one of a, b is on its Nyquist plane

@@ -181,3 +181,54 @@ def test_errors(B):
     h.gather_push(0.1)
     assert np.isfinite(h.density(1).cpu().numpy()).all()
     h.close()
+
+
+@pytest.mark.parametrize("axis,mu", [(2, 0), (0, 2), (1, 3)])
+def test_dipole_layer_solve(B, axis, mu):
+    """The external-field dipole layer (Sect. 5.3) in the solve, against the
+    oracle's solve of the deposit plus the layer's density."""
+    n, s, sigma, N, M = 32, 1.0, 1.0, 3000, 3.0
+    p = W.isothermal(n, s, N, 3.0, 0.3 * n, seed=12)
+    dev = torch.device("cuda", 0)
+    h = B.MondPM(n, 1, n * s, 1.0, 1.0, mu, sigma, N)
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    h.bind_particles(*t)
+    h.set_dipole_layer(axis, M)
+    h.deposit()
+    K = 0 if mu == 3 else 4
+    h.solve_field(K)
+    dep, ka, _ = oracle.deposit_fixed(n, sigma, p["cell"], p["offset"], p["mass"])
+    rho32, rho = oracle.acc_to_rho(dep, ka, s)
+    # the deposit's own density is untouched by the layer
+    assert np.array_equal(h.get_field(B.FIELD_RHO).cpu().numpy(), rho32)
+    ref = oracle.solve(rho + oracle.dipole_layer(n, s, axis, M), s, 1.0, 1.0, mu, K, want=("gN", "acc"))
+    assert rel(h.get_field(B.FIELD_GN).cpu().numpy(), ref["gN"]) < 1e-5
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < 1e-5
+    # removing the layer gives the plain solve back
+    h.set_dipole_layer(-1, 0.0)
+    h.solve_field(K)
+    plain = oracle.solve(rho, s, 1.0, 1.0, mu, K, want=("acc",))["acc"]
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), plain) < 1e-5
+    h.close()
+
+
+def test_dipole_layer_graph_recapture(B):
+    n, s, N = 32, 1.0, 2000
+    p = W.isothermal(n, s, N, 3.0, 0.3 * n, seed=13)
+    st = torch.cuda.Stream()
+    out = []
+    for masses in ((2.0, 2.0), (2.0, 5.0)):
+        with torch.cuda.stream(st):
+            h = B.MondPM(n, 1, n * s, 1.0, 1.0, 0, 1.0, N, stream=st)
+            t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+        torch.cuda.synchronize()
+        h.bind_particles(*t)
+        h.set_option(B.OPT_USE_GRAPH, 1)
+        for m in masses:
+            h.set_dipole_layer(2, m)
+            h.step(0.1, 2, B.WARM_NONE)
+        h.sync()
+        out.append(t[2].cpu().numpy().copy())
+        h.close()
+    # the second run changed the mass between steps: the replayed graph must see it
+    assert not np.array_equal(out[0], out[1])

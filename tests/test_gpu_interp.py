@@ -1,0 +1,140 @@
+"""The mesh-interpolating gather (MOND_OPT_GATHER 1 and 3) against the oracle:
+the node-smoothed mesh the final pass makes, the interpolation at the
+particles on the same mesh, the kick and drift, and its distance from Eq. gi
+(measured and bounded, not a parity claim)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02968_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N_MESH, SIGMA, N_PART, K, DT = 48, 1.5, 20000, 4, 0.2
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2312_02968_gb300 import binding
+
+    return binding
+
+
+@pytest.fixture(scope="module")
+def setup(B):
+    p = W.isothermal(N_MESH, 1.0, N_PART, 4.0, 0.35 * N_MESH, seed=21)
+    dep, ka, _ = oracle.deposit_fixed(N_MESH, SIGMA, p["cell"], p["offset"], p["mass"])
+    _, rho = oracle.acc_to_rho(dep, ka, 1.0)
+    ref = oracle.solve(rho, 1.0, 1.0, 1.0, oracle.MU_DEEP, K, want=("acc",))["acc"]
+    S_ref = oracle.node_smoothed(SIGMA, ref)
+    return p, ref, S_ref
+
+
+def make(B, p, mode, stream=None):
+    dev = torch.device("cuda", 0)
+    h = B.MondPM(N_MESH, 1, float(N_MESH), 1.0, 1.0, B.MU_DEEP, SIGMA, N_PART, stream=stream)
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    h.bind_particles(*t)
+    h.set_option(B.OPT_GATHER, mode)
+    return h, t
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_smoothed_mesh_and_interpolation(B, setup, order):
+    p, ref, S_ref = setup
+    h, t = make(B, p, order)
+    h.deposit()
+    h.solve_field(K)
+    S = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    # the final pass times the smoothing spectrum = Eq. gi at every pixel centre
+    assert rel(S, S_ref) < 1e-5
+    g = h.gather().cpu().numpy()
+    want_same = oracle.interp_gather(order, S, p["cell"], p["offset"].astype(np.float64))
+    assert rel(g, want_same) < 2e-6
+    want = oracle.interp_gather(order, S_ref, p["cell"], p["offset"].astype(np.float64))
+    assert rel(g, want) < 1e-5
+    h.close()
+
+
+def test_distance_from_eq_gi(B, setup):
+    # measured on this workload: the cubic is closer to Eq. gi than the linear
+    # interpolation, both well inside a few per cent
+    p, ref, S_ref = setup
+    exact = oracle.gather(SIGMA, ref, p["cell"], p["offset"])
+    err = {o: rel(oracle.interp_gather(o, S_ref, p["cell"], p["offset"].astype(np.float64)), exact) for o in (1, 3)}
+    assert err[3] < err[1] < 0.05
+    assert err[3] < 0.01
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_kick_drift(B, setup, order):
+    p, ref, S_ref = setup
+    h, t = make(B, p, order)
+    h.deposit()
+    h.solve_field(K)
+    S = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    h.gather_push(DT)
+    h.sync()
+    g = oracle.interp_gather(order, S, p["cell"], p["offset"].astype(np.float64))
+    c1, o1, v1 = oracle.push(N_MESH, 1.0, DT, g, p["cell"], p["offset"], p["vel"])
+    vel = t[2].cpu().numpy().astype(np.float64)
+    assert rel(vel - p["vel"], v1 - p["vel"]) < 1e-5
+    pos = t[0].cpu().numpy() + t[1].cpu().numpy().astype(np.float64)
+    d = np.abs(((pos - (c1 + o1)) + N_MESH / 2) % N_MESH - N_MESH / 2)
+    assert d.max() < 1e-4
+    h.close()
+
+
+def test_graph_step_matches_direct_step(B, setup):
+    p, _, _ = setup
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        h1, t1 = make(B, p, 3, stream=st)
+        h2, t2 = make(B, p, 3, stream=st)
+    torch.cuda.synchronize()
+    h2.set_option(B.OPT_USE_GRAPH, 1)
+    for _ in range(3):
+        h1.step(DT, 2, B.WARM_NONE)
+        h2.step(DT, 2, B.WARM_NONE)
+    h1.sync()
+    h2.sync()
+    for a, b in zip(t1[:3], t2[:3]):
+        assert torch.equal(a, b)
+    h1.close()
+    h2.close()
+
+
+def test_state_errors(B, setup):
+    p, _, _ = setup
+    h, _ = make(B, p, 0)
+    h.deposit()
+    h.solve_field(K)
+    h.set_option(B.OPT_GATHER, 1)
+    with pytest.raises(B.MondError):  # the mesh was not smoothed by the solve
+        h.gather()
+    h.solve_field(K)
+    h.gather()
+    with pytest.raises(B.MondError):
+        h.set_option(B.OPT_GATHER, 2)
+    h.set_option(B.OPT_GATHER, 0)
+    with pytest.raises(B.MondError):  # the mesh is smoothed
+        h.gather()
+    h.set_option(B.OPT_GATHER, 3)
+    with pytest.raises(B.MondError):
+        h.step(DT, 0, B.WARM_NONE)
+    h.solve_field(0)
+    with pytest.raises(B.MondError):  # Newton only: no smoothed mesh
+        h.gather()
+    h.close()

@@ -160,3 +160,26 @@ def test_isothermal_enclosed_apparent_mass(isothermal_solution):
         assert abs(cumB[R - 1] / MB - 1) < 0.04, R
     # the phantom (apparent minus baryonic) mass grows outward: deep MOND
     assert np.all(np.diff((cumA - cumB)[4:12]) > 0)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_dipole_layer_newtonian_field(axis):
+    """Sect. 5.3: a layer of mass M on the last plane and -M on the adjacent
+    (periodic) first one. Gauss's law on the periodic box, whose field has
+    zero mean: away from the layer the field is uniform, 4 pi G M s / L^3
+    along +axis."""
+    n, s, G, M = 32, 0.5, 1.3, 2.0
+    rho = oracle.dipole_layer(n, s, axis, M)
+    assert abs(rho.sum()) < 1e-12
+    assert rho.sum(axis=tuple(a for a in range(3) if a != 2 - axis)).max() * s ** 3 == pytest.approx(M)
+    gN = oracle.solve(rho, s, G, 1.0, oracle.MU_NEWTON, 0, want=("gN",))["gN"]
+    want = 4 * math.pi * G * M * s / (n * s) ** 3
+    # the middle third of the box along the axis, all components
+    mid = [slice(None)] * 3
+    mid[2 - axis] = slice(n // 3, 2 * n // 3)
+    g = gN[(slice(None),) + tuple(mid)]
+    assert np.max(np.abs(g[axis] / want - 1)) < 3e-3
+    others = [a for a in range(3) if a != axis]
+    assert np.max(np.abs(g[others])) < 1e-12
+    gneg = oracle.solve(oracle.dipole_layer(n, s, axis, -M), s, G, 1.0, oracle.MU_NEWTON, 0, want=("gN",))["gN"]
+    assert np.allclose(gneg, -gN, atol=1e-15)
