@@ -707,8 +707,12 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       xi.ncomp = nout;
       xi.spec = A;
       xi.real_out = h->w.acc;
+      // g_N = the acceleration of a Newton-only solve: written by the same pass
+      // when there is no potential plane (g_N holds three planes)
+      if (nout == 3) xi.real_out2 = h->w.gN;
       PK(xpass(h, passes::X_INV, xi));
-      CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
+      if (nout != 3)
+        CK(cudaMemcpyAsync(h->w.gN, h->w.acc, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
       h->last_iters = 0;
       h->acc_smoothed = false;
       h->have_solve = true;

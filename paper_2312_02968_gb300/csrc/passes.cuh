@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(NT) k_zpass(ZArgs a) {
     float kx = kv[col], kz = kv[row];
     bool nx = (col == N / 2), nz = (row == N / 2);
     float kk = kx * kx + ky * ky + kz * kz;
-    float A = kk > 0.f ? 1.0f / kk : 0.f;
+    float A = kk > 0.f ? __frcp_rn(kk) : 0.f;  // correctly rounded, as 1.0f / kk
     float kpx = kp[col], kpz = kp[row];
     if constexpr (MODE == Z_NEWTON) {
       float2 r = tile[i];
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(NTZ, 2) k_zpass_pipe(const __grid_constant__ t
       const float kx = kv[col], kz = kv[row];
       const bool nx = (col == N / 2), nz = (row == N / 2);
       const float kk = kx * kx + ky * ky + kz * kz;
-      const float A = kk > 0.f ? 1.0f / kk : 0.f;
+      const float A = kk > 0.f ? __frcp_rn(kk) : 0.f;  // correctly rounded, as 1.0f / kk
       if constexpr (MODE == Z_NEWTON) {
         float2 r;
         if constexpr (SC) r = *sc;

@@ -124,3 +124,41 @@ def test_ring_config_at_512_against_eq_ringforce():
     # the ring's pulls on the central body cancel; what is left is the mesh
     # self-force, about 1.08e-3 sqrt(G m0 a0)/s for sigma = 1 px (Sect. 4)
     assert np.linalg.norm(g[0]) < 2e-3
+
+
+def test_fullsize_density_and_interpolating_gather(setup):
+    """The density kernels and the cubic interpolating gather at the bench's
+    size (256^3, 1e6 particles) as the bench runs them: the apparent density of
+    the GPU's field against the oracle's divergence of the same field, the
+    node-smoothed mesh against the oracle's Eq. gi at every pixel centre of
+    its own mesh, and the interpolation at a seeded sample of 20000 particles."""
+    B, p, _, _, a_ref = setup
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        h = B.MondPM(N_MESH, 1, float(N_MESH), 1.0, 1.0, B.MU_DEEP, SIGMA, N_PART, stream=st)
+        t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+    torch.cuda.synchronize()
+    h.bind_particles(*t)
+    h.deposit()
+    h.solve_field(K)
+    acc = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    rA_dev = h.density(B.DENS_APPARENT)
+    h.sync()  # the handle's stream is not torch's: wait before reading
+    rA = rA_dev.cpu().numpy()
+    assert rel(rA, oracle.field_density(acc, 1.0, 1.0)) < 2e-6
+    h.set_option(B.OPT_GATHER, 3)
+    h.solve_field(K)
+    S = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(N_PART, 20000, replace=False))
+    g_dev = h.gather()
+    h.sync()
+    g = g_dev.cpu().numpy()[idx]
+    cell, off = p["cell"][idx], p["offset"][idx]
+    assert rel(g, oracle.interp_gather(3, S, cell, off.astype(np.float64))) < 2e-6
+    # the smoothed mesh at the nodes around the sample: Eq. gi there on the oracle's mesh
+    nodes = np.unique(cell, axis=0)[:4000]
+    S_nodes = S[:, nodes[:, 2], nodes[:, 1], nodes[:, 0]].T
+    want = oracle.gather(SIGMA, a_ref, nodes.astype(np.int32), np.zeros_like(nodes, dtype=np.float32))
+    assert rel(S_nodes, want) < 1e-5
+    h.close()
