@@ -84,7 +84,7 @@ int mond_fno_input(int N, int n, float a0, const float* gN, float* x, float* sca
 
 /* Fine field from a coarse network output: H [3][N^3] = s * cubic-convolution
  * upsampling (Keys, a = -1/2; periodic, cell centred; one axis at a time) of
- * y [3][n^3]; s read from scale. N must be a multiple of n. scratch: device
+ * y [3][n^3]; s read from scale. N must be a multiple of n, at most 64 n. scratch: device
  * memory of mond_fno_output_scratch_bytes(N, n) bytes. */
 int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, void* scratch, void* stream);
 

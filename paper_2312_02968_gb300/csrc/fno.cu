@@ -491,8 +491,9 @@ __global__ void k_mix_fwd(const float2* __restrict__ s, const uint16_t* __restri
   float2 acc = make_float2(0.f, 0.f);
   if (lane < C) {
     const uint32_t* R2 = reinterpret_cast<const uint32_t*>(R);
+#pragma unroll 8
     for (int j = 0; j < C; j++) {
-      const uint32_t wbits = R2[((int64_t)k * C + j) * C + lane];
+      const uint32_t wbits = __ldcs(R2 + ((int64_t)k * C + j) * C + lane);  // read once per forward
       const float wr = __uint_as_float(wbits << 16), wi = __uint_as_float(wbits & 0xffff0000u);
       const float2 sj = s[(int64_t)j * K + k];
       acc.x = fmaf(wr, sj.x, fmaf(-wi, sj.y, acc.x));
@@ -709,22 +710,39 @@ __global__ void k_up_x(int n, int N, const float* __restrict__ in, float* __rest
   }
 }
 
-// middle axis: in [outer][n][inner] -> out [outer][N][inner] (times scale when given)
-__global__ void k_up_mid(int n, int N, int inner, const float* __restrict__ in, float* __restrict__ out,
-                         const float* __restrict__ scale) {
+// One axis of the upsampling, in [outer][n][inner] -> out [outer][N][inner]
+// (times scale when given), by coarse interval: CTA row (outer, j) reads the
+// four coarse rows j-1..j+2 once per inner index and writes the f = N / n fine
+// rows whose taps they are, Y = f j + f/2 + q (mod N), q < f (the fine rows
+// with floor((Y + 1/2)/f - 1/2) = j). blockIdx.y splits the inner axis.
+__global__ void k_up_axis(int n, int N, int64_t inner, int64_t chunk, const float* __restrict__ in,
+                          float* __restrict__ out, const float* __restrict__ scale) {
+  extern __shared__ float upw[];  // f x 4 weights
+  __shared__ int upy[64];         // fine row of each q (f <= 64)
   const int f = N / n;
-  const int64_t orow = blockIdx.x;  // outer * N + Y
-  const int Y = (int)(orow % N);
-  const int64_t outer = orow / N;
-  int idx[4];
-  float w[4];
-  up_taps(Y, n, f, idx, w);
+  const int j = (int)(blockIdx.x % n);
+  const int64_t outer = blockIdx.x / n;
+  for (int q = threadIdx.x; q < f; q += blockDim.x) {
+    const int Y = (f * j + f / 2 + q) % N;
+    int idx[4];
+    up_taps(Y, n, f, idx, upw + 4 * q);
+    upy[q] = Y;
+  }
+  __syncthreads();
   const float s = scale ? *scale : 1.f;
-  const float* base = in + outer * n * inner;
-  for (int X = threadIdx.x; X < inner; X += blockDim.x) {
-    const float v = w[0] * base[(int64_t)idx[0] * inner + X] + w[1] * base[(int64_t)idx[1] * inner + X] +
-                    w[2] * base[(int64_t)idx[2] * inner + X] + w[3] * base[(int64_t)idx[3] * inner + X];
-    out[orow * inner + X] = s * v;
+  const float* b0 = in + (outer * n + (j - 1 + n) % n) * inner;
+  const float* b1 = in + (outer * n + j) * inner;
+  const float* b2 = in + (outer * n + (j + 1) % n) * inner;
+  const float* b3 = in + (outer * n + (j + 2) % n) * inner;
+  float* o = out + outer * N * inner;
+  const int64_t x0 = (int64_t)blockIdx.y * chunk, x1 = min(inner, x0 + chunk);
+  for (int64_t X = x0 + threadIdx.x; X < x1; X += blockDim.x) {
+    const float v0 = __ldg(b0 + X), v1 = __ldg(b1 + X), v2 = __ldg(b2 + X), v3 = __ldg(b3 + X);
+    for (int q = 0; q < f; q++) {
+      const float* w = upw + 4 * q;
+      const float v = w[0] * v0 + w[1] * v1 + w[2] * v2 + w[3] * v3;
+      o[(int64_t)upy[q] * inner + X] = s * v;
+    }
   }
 }
 
@@ -983,8 +1001,12 @@ int mond_fno_output(int N, int n, const float* y, const float* scale, float* H, 
   float* t2 = t1 + (size_t)3 * n * n * N;   // [3 n][N][N]  x, y upsampled
   const int threads = N < 256 ? ((N + 31) / 32) * 32 : 256;
   k_up_x<<<(unsigned)(3 * n * n), threads, 0, st>>>(n, N, y, t1);
-  k_up_mid<<<(unsigned)(3 * n * N), threads, 0, st>>>(n, N, N, t1, t2, nullptr);
-  k_up_mid<<<(unsigned)(3 * N), threads, 0, st>>>(n, N, N * N, t2, H, scale);
+  if (N / n > 64) return -1;
+  const size_t wsm = sizeof(float) * 4 * (N / n);
+  const int64_t inner2 = (int64_t)N * N, chunk2 = inner2 < 2048 ? inner2 : 2048;
+  k_up_axis<<<dim3((unsigned)(3 * n * n), 1), threads, wsm, st>>>(n, N, N, N, t1, t2, nullptr);
+  k_up_axis<<<dim3((unsigned)(3 * n), (unsigned)((inner2 + chunk2 - 1) / chunk2)), 256, wsm, st>>>(
+      n, N, inner2, chunk2, t2, H, scale);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

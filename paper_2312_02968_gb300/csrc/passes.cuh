@@ -15,6 +15,7 @@
 // L^-3 of App. Fourier.
 #pragma once
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace passes {
 
@@ -148,16 +149,17 @@ __device__ __forceinline__ float2 dipole2(const XArgs& a, int64_t line, int x) {
   return make_float2(e0, e1);
 }
 
+// Issue the asynchronous copies of one component's spectral tile into the
+// transposed shared layout [kk][line]; they complete at tma::async_wait_all,
+// so the tiles of all components are in flight together.
 template <int N>
 __device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict__ g, int64_t line0, int tid) {
   using C = XCfg<N>;
-  constexpr int Q = C::SP / 2;  // float4 per line
-  const float4* src = reinterpret_cast<const float4*>(g + line0 * C::SP);
-  for (int i = tid; i < C::L * Q; i += NT) {
-    int l = i / Q, kk = (i % Q) * 2;
-    float4 v = __ldcs(src + i);
-    sm[kk * C::LP + l] = make_float2(v.x, v.y);
-    if (kk + 1 <= C::H) sm[(kk + 1) * C::LP + l] = make_float2(v.z, v.w);
+  constexpr int SPL = C::H + 1;  // complex values of a line that are used (kx = 0..N/2)
+  const float2* src = g + line0 * C::SP;
+  for (int i = tid; i < C::L * SPL; i += NT) {
+    const int l = i / SPL, kk = i % SPL;
+    tma::async_copy8(sm + kk * C::LP + l, src + (int64_t)l * C::SP + kk);
   }
 }
 
@@ -250,8 +252,23 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
   constexpr bool FWD = (MODE == X_RHO || MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_FWD ||
                         MODE == X_NU_REAL);
 
+  if (tid == 0) {
+    // the real-space planes the pointwise stage reads, brought into L2 while
+    // the spectral tile is loaded and transformed (L lines: contiguous)
+    const uint32_t rb = (uint32_t)(C::L * N * sizeof(float));
+    const int64_t r0 = line0 * N;
+    for (int c = 0; c < 3; c++) {
+      const int64_t o = (int64_t)c * N * N * N + r0;
+      if constexpr (MODE == X_NU || MODE == X_MU || MODE == X_NU_REAL) tma::prefetch_l2(a.gN + o, rb);
+      if constexpr (MODE == X_NU_FIRST || MODE == X_NU_REAL)
+        if (a.H0) tma::prefetch_l2(a.H0 + o, rb);
+      if constexpr (MODE == X_NU)
+        if (a.Hs_out && a.red) tma::prefetch_l2(a.Hs_out + o, rb);
+    }
+  }
   if constexpr (INV) {
     for (int c = 0; c < nc; c++) x_load_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
+    tma::async_wait_all();
     __syncthreads();
     for (int c = 0; c < nc; c++) {
       x_pre_c2r<N>(buf + c * TILE, tw, tid);
@@ -551,7 +568,6 @@ __global__ void __launch_bounds__(NT) k_zpass(ZArgs a) {
 // mbarrier) for tile i+1 and TMA stores of tile i-1 while all threads
 // transform tile i, so HBM traffic overlaps the shared-memory FFT.
 // ===========================================================================
-#include "tma.cuh"
 
 namespace passes {
 

@@ -156,3 +156,18 @@ def test_features_upsample_coarsen_mixture(env):
     del keep
     want = F.mixture_density(N, 0.5, sp["centre"], sp["mass"], sp["radius"], sp["kind"], 25.6)
     assert rel(rho.cpu().numpy(), want) < 1e-5
+
+
+@pytest.mark.parametrize("N,n", [(48, 16), (64, 8), (96, 8), (32, 32)])
+def test_upsample_factors(env, N, n):
+    # odd, even and unit factors; the fine rows of every coarse interval,
+    # including the interval that wraps through the periodic face
+    torch, S = env
+    st = torch.cuda.current_stream()
+    rng = np.random.default_rng(N + n)
+    y = rng.normal(size=(3, n, n, n)).astype(np.float32)
+    scale = torch.tensor([1.7, 0.0, 0.0, 0.0], device="cuda")
+    H = torch.empty((3, N, N, N), device="cuda")
+    S.upsample(torch.from_numpy(y).cuda(), N, n, scale, H, st)
+    torch.cuda.synchronize()
+    assert rel(H.cpu().numpy(), F.upsample(y.astype(np.float64), N, 1.7)) < 1e-6
