@@ -9,6 +9,7 @@
 // and no 1/n^3 is the adjoint of the forward, which the backward pass uses.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -110,6 +111,15 @@ size_t carve(const Shape& s, char* base, Work* w) {
 __device__ __forceinline__ float bf(const uint16_t* p, int64_t i) {
   return __bfloat162float(__ushort_as_bfloat16(p[i]));
 }
+
+// 16-byte asynchronous copy global -> shared; groups complete in order.
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
 
 // e^{sign 2 pi i m / n} with exact argument reduction of m modulo n.
 __device__ __forceinline__ float2 cis(int64_t m, int n, float sign) {
@@ -240,7 +250,7 @@ __global__ void k_tables(int n, int M, float invV, Tabs t) {
 // loop over planes, so the tables are read once per CTA.
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 size_t smem_xy_fwd(int n, int M) {
-  return sizeof(float) * ((size_t)n * n + (size_t)n * round4(2 * M) + (size_t)2 * M * M * 2) +
+  return sizeof(float) * ((size_t)2 * n * n + (size_t)n * round4(2 * M) + (size_t)2 * M * M * 2) +
          sizeof(float2) * (size_t)2 * M * (n + 1);
 }
 template <int NX>  // n <= NX
@@ -249,8 +259,8 @@ __global__ void __launch_bounds__(256, 2) k_xy_fwd(const float* __restrict__ v, 
                                                 int M, int64_t nplanes) {
   extern __shared__ __align__(16) float smf[];
   const int M2 = 2 * M, XS = round4(M2), SXF = sxf(M);
-  float* sP = smf;                                          // n * n
-  float* sX = sP + n * n;                                   // n * XS
+  float* sP = smf;                                          // 2 * n * n: the plane, double buffered
+  float* sX = sP + 2 * n * n;                               // n * XS
   float2* sO = reinterpret_cast<float2*>(sX + n * XS);      // M2 * M
   float2* sY = sO + M2 * M;                                 // M2 * (n + 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -259,25 +269,21 @@ __global__ void __launch_bounds__(256, 2) k_xy_fwd(const float* __restrict__ v, 
   for (int x = 0; x < NX; x++) tx[x] = (x < n && lane < M2) ? fx[x * SXF + lane] : 0.f;
   for (int e = tid; e < M2 * n; e += blockDim.x) sY[(e / n) * (n + 1) + e % n] = tf[e];
   const int KPG = (M + 7) / 8;  // kx per warp in the y stage
-  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+  // the next plane is copied in while this one is transformed
+  auto fetch = [&](int64_t plane, float* dst) {
+    const float* src = v + plane * n * n;
+    for (int e = tid; e < n * n / 4; e += blockDim.x) cp16(dst + 4 * e, src + 4 * e);
+  };
+  if ((int64_t)blockIdx.x < nplanes) fetch(blockIdx.x, sP);
+  cp_commit();
+  int it = 0;
+  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x, it++) {
+    const int64_t nxt = plane + gridDim.x;
+    if (nxt < nplanes) fetch(nxt, sP + ((it + 1) & 1) * n * n);
+    cp_commit();
+    cp_wait<1>();  // this plane's group is complete
     __syncthreads();
-    const float4* src = reinterpret_cast<const float4*>(v + plane * n * n);
-    float4* sP4 = reinterpret_cast<float4*>(sP);
-    {
-      // at most 4 float4 per thread (n <= 64): issue all loads, then store
-      float4 q[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int e = tid + k * 256;
-        if (e < n * n / 4) q[k] = src[e];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int e = tid + k * 256;
-        if (e < n * n / 4) sP4[e] = q[k];
-      }
-    }
-    __syncthreads();
+    const float4* sP4 = reinterpret_cast<const float4*>(sP + (it & 1) * n * n);
     for (int r = warp; r < n; r += 16) {
       const int r2 = r + 8;
       const float4* a0 = sP4 + r * (n / 4);
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(256, 2) k_xy_fwd(const float* __restrict__ v, 
 // y: lane = y; x: thread = x with its table column in registers.
 size_t smem_xy_inv(int n, int M) {
   return sizeof(float) * ((size_t)n * (round4(2 * M) + 4)) +
-         sizeof(float2) * ((size_t)n * (2 * M + 1) + (size_t)2 * M * M);
+         sizeof(float2) * ((size_t)n * (2 * M + 1) + (size_t)2 * 2 * M * M);
 }
 template <int NX, int MX>  // n <= NX, 2M <= MX
 __global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in, float* __restrict__ z,
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in
   const int M2 = 2 * M, XS = round4(M2) + 4, SXI = sxi(n);  // XS: 4-way write conflicts at most
   float* sX = smf;                                          // n * XS
   float2* sTi = reinterpret_cast<float2*>(sX + n * XS);     // n * (M2 + 1)
-  float2* sI = sTi + n * (M2 + 1);                          // M2 * M
+  float2* sI = sTi + n * (M2 + 1);                          // 2 * M2 * M: the input plane, double buffered
   const int tid = threadIdx.x;
   const int xl = tid & 63, grp = tid >> 6;  // x stage: column x, row group (4 groups)
   float tt[MX];
@@ -354,11 +360,21 @@ __global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in
   for (int e = tid; e < n * M2; e += blockDim.x) sTi[(e / M2) * (M2 + 1) + e % M2] = ti[e];
   for (int e = tid; e < n * XS; e += blockDim.x) sX[e] = 0.f;  // the row padding is read (times 0) below
   const int KPG = (M + 3) / 4;  // kx per group in the y stage
-  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+  // the next input plane is copied in while this one is transformed
+  auto fetch = [&](int64_t plane, float2* dst) {
+    const float2* src = in + plane * M2 * M;
+    for (int e = tid; e < M2 * M / 2; e += blockDim.x) cp16(dst + 2 * e, src + 2 * e);
+  };
+  if ((int64_t)blockIdx.x < nplanes) fetch(blockIdx.x, sI);
+  cp_commit();
+  int it = 0;
+  for (int64_t plane = blockIdx.x; plane < nplanes; plane += gridDim.x, it++) {
+    const int64_t nxt = plane + gridDim.x;
+    if (nxt < nplanes) fetch(nxt, sI + ((it + 1) & 1) * M2 * M);
+    cp_commit();
+    cp_wait<1>();
     __syncthreads();
-    const float2* ip = in + plane * M2 * M;
-    for (int e = tid; e < M2 * M; e += blockDim.x) sI[e] = ip[e];
-    __syncthreads();
+    const float2* sIc = sI + (it & 1) * M2 * M;
     if (xl < n) {
       const float2* t = sTi + xl * (M2 + 1);  // row y = xl of the inverse table
       float2 acc[8];
@@ -366,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in
       for (int k = 0; k < 8; k++) acc[k] = make_float2(0.f, 0.f);
       for (int p = 0; p < M2; p++) {
         const float2 w = t[p];
-        const float2* ir = sI + p * M;
+        const float2* ir = sIc + p * M;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
           const int kx = grp * KPG + k;
@@ -425,42 +441,54 @@ __global__ void __launch_bounds__(256, 2) k_xy_inv(const float2* __restrict__ in
 // Complex contraction along a middle axis: out[b][p][i] = sum_q T[p][q] in[b][q][i]
 // (P, Q <= 64). Tiles of 16 columns i; a thread owns one column and the
 // rows p = p0, p0 + 16, ...; T stays in shared memory (row stride Q + 1).
+// Persistent CTAs: T is read once per CTA, and the next tile is copied in
+// (asynchronously, double buffered) while this one is contracted.
 constexpr int AXI = 16;
 __global__ void __launch_bounds__(256) k_axis(const float2* __restrict__ in, float2* __restrict__ out,
                                               const float2* __restrict__ T, int64_t B, int P, int Q, int I) {
-  extern __shared__ float2 sma[];
+  extern __shared__ __align__(16) float2 sma[];
   const int QS = Q + 1;
-  float2* sT = sma;              // P * QS
-  float2* sIn = sma + P * QS;    // Q * AXI
+  float2* sT = sma;                                      // P * QS
+  float2* sIn = sma + ((P * QS + 1) & ~1);               // 2 * Q * AXI, 16-byte aligned
   for (int e = threadIdx.x; e < P * Q; e += blockDim.x) sT[(e / Q) * QS + e % Q] = T[e];
   const int nchunk = (I + AXI - 1) / AXI;
   const int64_t tiles = B * nchunk;
   const int i = threadIdx.x % AXI, p0 = threadIdx.x / AXI;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  // tile -> [Q][AXI] in shared memory; whole 16-column chunks by 16-byte
+  // asynchronous copies, a ragged last chunk by plain loads with zero fill
+  auto fetch = [&](int64_t tile, float2* dst) {
     const int64_t b = tile / nchunk;
     const int i0 = (int)(tile % nchunk) * AXI;
-    __syncthreads();
-    {
-      // at most 4 elements per thread (Q <= 64): issue all loads, then store
-      float2 q4[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int e = threadIdx.x + k * 256;
-        const int q = e / AXI, ii = e % AXI;
-        q4[k] = (e < Q * AXI && i0 + ii < I) ? in[(b * Q + q) * I + i0 + ii] : make_float2(0.f, 0.f);
+    if (i0 + AXI <= I && (I & 1) == 0) {
+      for (int e = threadIdx.x; e < Q * AXI / 2; e += blockDim.x) {
+        const int q = e / (AXI / 2), ii = 2 * (e % (AXI / 2));
+        cp16(dst + q * AXI + ii, in + (b * Q + q) * I + i0 + ii);
       }
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int e = threadIdx.x + k * 256;
-        if (e < Q * AXI) sIn[e] = q4[k];
+    } else {
+      for (int e = threadIdx.x; e < Q * AXI; e += blockDim.x) {
+        const int q = e / AXI, ii = e % AXI;
+        dst[e] = i0 + ii < I ? in[(b * Q + q) * I + i0 + ii] : make_float2(0.f, 0.f);
       }
     }
+  };
+  if ((int64_t)blockIdx.x < tiles) fetch(blockIdx.x, sIn);
+  cp_commit();
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, it++) {
+    const int64_t b = tile / nchunk;
+    const int i0 = (int)(tile % nchunk) * AXI;
+    const int64_t nxt = tile + gridDim.x;
+    __syncthreads();  // every thread is done with the buffer the next fetch overwrites
+    if (nxt < tiles) fetch(nxt, sIn + ((it + 1) & 1) * Q * AXI);
+    cp_commit();
+    cp_wait<1>();
     __syncthreads();
+    const float2* cur = sIn + (it & 1) * Q * AXI;
     float2 acc[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[k] = make_float2(0.f, 0.f);
     for (int q = 0; q < Q; q++) {
-      const float2 x = sIn[q * AXI + i];
+      const float2 x = cur[q * AXI + i];
 #pragma unroll
       for (int k = 0; k < 4; k++) {
         const int p = p0 + 16 * k;
@@ -776,8 +804,9 @@ unsigned grid_stride(int64_t n) {
   return (unsigned)(b < 4096 ? b : 4096);
 }
 
-size_t smem_axis(int P, int Q) { return sizeof(float2) * ((size_t)P * (Q + 1) + (size_t)Q * AXI); }
-unsigned tiles_grid(int64_t tiles) { return (unsigned)(tiles < 152 * 8 ? tiles : 152 * 8); }
+size_t smem_axis(int P, int Q) { return sizeof(float2) * ((size_t)((P * (Q + 1) + 1) & ~1) + (size_t)2 * Q * AXI); }
+// k_axis: two persistent CTAs per SM, so that each streams several tiles
+unsigned axis_grid(int64_t tiles) { return (unsigned)(tiles < 152 * 2 ? tiles : 152 * 2); }
 
 // The fused plane kernels may need more than the default 48 KB of shared memory.
 template <typename K>
@@ -795,8 +824,9 @@ bool smem_opt_in() {
 // Forward transform of C channels of real fields v -> out [C][K] (kept modes).
 void dft3(const Shape& s, const Work& w, const float* v, float2* out, cudaStream_t st) {
   const int n = s.n, M = s.M, C = s.C;
-  // x and y per (c, z) plane: [C n][n][n] -> [C n][2M][M]
-  const unsigned g = tiles_grid((int64_t)C * n / 2);
+  // x and y per (c, z) plane: [C n][n][n] -> [C n][2M][M]; two CTAs per SM,
+  // each streaming its planes through a double buffer
+  const unsigned g = (unsigned)std::min<int64_t>((int64_t)C * n, 2 * 152);
   const size_t sm = smem_xy_fwd(n, M);
   const int64_t np = (int64_t)C * n;
   if (n <= 16) k_xy_fwd<16><<<g, 256, sm, st>>>(v, w.b, w.tab.fx, w.tab.tf, n, M, np);
@@ -804,7 +834,7 @@ void dft3(const Shape& s, const Work& w, const float* v, float2* out, cudaStream
   else k_xy_fwd<64><<<g, 256, sm, st>>>(v, w.b, w.tab.fx, w.tab.tf, n, M, np);
   // z: [C][n][2M M] -> [C][2M][2M M]
   const int Iz = 2 * M * M;
-  k_axis<<<tiles_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(2 * M, n), st>>>(w.b, out, w.tab.tf, C,
+  k_axis<<<axis_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(2 * M, n), st>>>(w.b, out, w.tab.tf, C,
                                                                                               2 * M, n, Iz);
 }
 
@@ -813,9 +843,9 @@ void idft3(const Shape& s, const Work& w, const float2* in, float* z, float* v, 
            cudaStream_t st) {
   const int n = s.n, M = s.M, C = s.C;
   const int Iz = 2 * M * M;
-  k_axis<<<tiles_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(n, 2 * M), st>>>(in, w.b, w.tab.ti, C, n,
+  k_axis<<<axis_grid((int64_t)C * ((Iz + AXI - 1) / AXI)), 256, smem_axis(n, 2 * M), st>>>(in, w.b, w.tab.ti, C, n,
                                                                                               2 * M, Iz);
-  const unsigned g = tiles_grid((int64_t)C * n / 2);
+  const unsigned g = (unsigned)std::min<int64_t>((int64_t)C * n, 2 * 152);
   const size_t sm = smem_xy_inv(n, M);
   const int64_t np = (int64_t)C * n;
   const int M2 = 2 * M;
