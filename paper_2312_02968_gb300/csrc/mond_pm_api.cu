@@ -170,25 +170,55 @@ bool encode_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int b
 double g1(double u, double sigma) { return exp(-(u * u) / (2.0 * sigma * sigma)) / (sigma * sqrt(2.0 * M_PI)); }
 
 // node-smoothing kernel spectrum: K^(k) = sum_{d in ball} w(d) cos(kx dx s) cos(ky dy s) cos(kz dz s)
+// Smoothing spectrum: the DFT of the ball-truncated Gaussian w(d) sampled at
+// the integer offsets d, K(k) = sum_{|d|^2 < 16 sigma^2} w(d) cos(k . d)
+// (w is even in every axis). w is a product of 1-D Gaussians g(d_a) cut by
+// the ball into rows (dy, dz) of half-length L(dy, dz), so with
+// P(kx, L) = g(0) + 2 sum_{dx=1..L} g(dx) cos(kx dx):
+//   K(k) = sum_{dy, dz >= 0} m(dy) m(dz) g(dy) g(dz) cos(ky dy) cos(kz dz) P(kx, L(dy, dz)),
+// m(0) = 1, m(d > 0) = 2. FP64 throughout; each persistent CTA builds the
+// cosine table cos(2 pi f(i) d / n) (i < n, d <= r) once in shared memory.
 __global__ void k_khat(int n, int r, double sigma, float* khat) {
-  int64_t tot = (int64_t)n * n * (n / 2 + 1);
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= tot) return;
-  int kx = (int)(i % (n / 2 + 1)), ky = (int)((i / (n / 2 + 1)) % n), kz = (int)(i / ((int64_t)(n / 2 + 1) * n));
-  double lim = 16.0 * sigma * sigma;
-  double ax = 2.0 * M_PI * freq_of(kx, n) / n, ay = 2.0 * M_PI * freq_of(ky, n) / n,
-         az = 2.0 * M_PI * freq_of(kz, n) / n;
-  double norm = 1.0 / (sigma * sqrt(2.0 * M_PI));
-  double sum = 0.0;
-  for (int dz = -r; dz <= r; dz++)
-    for (int dy = -r; dy <= r; dy++) {
-      double wyz = exp(-(double)(dy * dy + dz * dz) / (2.0 * sigma * sigma)) * norm * norm * cos(ay * dy) * cos(az * dz);
-      double row = 0.0;
-      for (int dx = -r; dx <= r; dx++)
-        if ((double)(dx * dx + dy * dy + dz * dz) < lim) row += exp(-(double)(dx * dx) / (2.0 * sigma * sigma)) * norm * cos(ax * dx);
-      sum += wyz * row;
+  extern __shared__ double kh_s[];
+  const int R1 = r + 1;
+  double* tc = kh_s;             // n * R1
+  double* g = tc + n * R1;       // R1
+  int* rowL = (int*)(g + R1);    // R1 * R1: L(dy, dz), -1 for an empty row
+  const double lim = 16.0 * sigma * sigma;
+  const double norm = 1.0 / (sigma * sqrt(2.0 * M_PI));
+  for (int e = threadIdx.x; e < n * R1; e += blockDim.x) {
+    const int i = e / R1, d = e % R1;
+    tc[e] = cos(2.0 * M_PI * (double)((int64_t)freq_of(i, n) * d % n) / n);
+  }
+  for (int d = threadIdx.x; d < R1; d += blockDim.x) g[d] = exp(-(double)(d * d) / (2.0 * sigma * sigma)) * norm;
+  for (int e = threadIdx.x; e < R1 * R1; e += blockDim.x) {
+    const int dy = e % R1, dz = e / R1;
+    int L = -1;
+    while (L + 1 <= r && (double)((L + 1) * (L + 1) + dy * dy + dz * dz) < lim) L++;
+    rowL[e] = L;
+  }
+  __syncthreads();
+  const int NX = n / 2 + 1;
+  const int64_t tot = (int64_t)n * n * NX;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % NX), ky = (int)((i / NX) % n), kz = (int)(i / ((int64_t)NX * n));
+    double P[16];  // prefix sums over dx, L = 0..r (r <= 15)
+    double acc = g[0];
+    P[0] = acc;
+    for (int dx = 1; dx <= r; dx++) {
+      acc += 2.0 * g[dx] * tc[kx * R1 + dx];
+      P[dx] = acc;
     }
-  khat[i] = (float)sum;
+    double sum = 0.0;
+    for (int dz = 0; dz <= r; dz++) {
+      const double wz = (dz ? 2.0 : 1.0) * g[dz] * tc[kz * R1 + dz];
+      for (int dy = 0; dy <= r; dy++) {
+        const int L = rowL[dz * R1 + dy];
+        if (L >= 0) sum += wz * (dy ? 2.0 : 1.0) * g[dy] * tc[ky * R1 + dy] * P[L];
+      }
+    }
+    khat[i] = (float)sum;
+  }
 }
 
 // FP32 density from the accumulator (same rule as the x-pass).
@@ -664,7 +694,10 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
 int ensure_khat(mond_pm* h) {
   if (h->have_khat) return MOND_OK;
   int64_t tot = (int64_t)h->nf * h->nf * (h->nf / 2 + 1);
-  k_khat<<<(unsigned)((tot + 255) / 256), 256, 0, h->st>>>(h->nf, h->r, h->sigma, h->w.khat);
+  const size_t sm = sizeof(double) * ((size_t)h->nf * (h->r + 1) + (h->r + 1)) + sizeof(int) * (h->r + 1) * (h->r + 1);
+  if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_khat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const int64_t nb = std::min<int64_t>((tot + 255) / 256, (int64_t)h->sms * 4);
+  k_khat<<<(unsigned)nb, 256, sm, h->st>>>(h->nf, h->r, h->sigma, h->w.khat);
   h->launches++;
   CK(cudaGetLastError());
   h->have_khat = true;
