@@ -4,6 +4,7 @@
 #pragma once
 #include "common.cuh"
 #include "fixed_point.cuh"
+#include "tma.cuh"
 
 namespace parts {
 
@@ -666,10 +667,15 @@ __global__ void __launch_bounds__(GAT_NT, 2) k_gather_push(GatArgs a) {
       for (int lx = lane; lx < hw; lx += 32) {
         int gx = ox + lx;
         if (!inside) gx += gx < 0 ? a.n : (gx >= a.n ? -a.n : 0);
-        sa[row * px + lx] = make_float4(__ldg(a.acc + rbase + gx), __ldg(a.acc + n3 + rbase + gx),
-                                        __ldg(a.acc + 2 * n3 + rbase + gx), 0.f);
+        // three components into one 16-byte cell (the fourth float is never read);
+        // asynchronous, so all rows of the tile are in flight together
+        float* d = reinterpret_cast<float*>(sa + row * px + lx);
+        tma::async_copy4(d, a.acc + rbase + gx);
+        tma::async_copy4(d + 1, a.acc + n3 + rbase + gx);
+        tma::async_copy4(d + 2, a.acc + 2 * n3 + rbase + gx);
       }
     }
+    tma::async_wait_all();
     __syncthreads();
     const int len = (p1 - p0 + nw - 1) / nw;
     const int q0 = min(p1, p0 + warp * len), q1 = min(p1, q0 + len);
