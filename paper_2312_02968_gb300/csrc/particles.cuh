@@ -253,6 +253,14 @@ struct PartIn {
   float o[2];
   uint32_t mb;
   uint32_t lw[2];  // deposit: the axis-table words of this lane's slots
+  float kv, ko;    // gather: velocity and offset of the axis this lane kicks (if any)
+  // gather: request them ahead of the kick (kax: the lane's axis, -1 none)
+  __device__ __forceinline__ void fetch_kick(const float* vel, const float* off, int kax) {
+    if (kax >= 0) {
+      kv = vel[3 * i + kax];
+      ko = off[3 * i + kax];
+    }
+  }
   // deposit: request the table words for the fetched offsets (q = round(2^16 o))
   __device__ __forceinline__ void fetch_lut(const uint32_t* lut, int w, const LaneSlots& ls) {
 #pragma unroll
@@ -506,13 +514,26 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
   // the cell and offset of a particle are rewritten (drift) only by this warp,
   // after their last use, so reading them ahead is safe
   PartIn pa, pb, na, nb;
+  // lanes 0..2 kick the first particle of a pair, lanes 3..5 the second
+  const int kax_a = a.do_kick && lane < 3 ? lane : -1;
+  const int kax_b = a.do_kick && lane >= 3 && lane < 6 ? lane - 3 : -1;
   pa.fetch(__ldg(a.perm + q0), a.cell, a.off, nullptr, ls);
-  if (q0 + 1 < q1) pb.fetch(__ldg(a.perm + q0 + 1), a.cell, a.off, nullptr, ls);
+  pa.fetch_kick(a.vel, a.off, kax_a);
+  if (q0 + 1 < q1) {
+    pb.fetch(__ldg(a.perm + q0 + 1), a.cell, a.off, nullptr, ls);
+    pb.fetch_kick(a.vel, a.off, kax_b);
+  }
   uint32_t ia = q0 + 2 < q1 ? __ldg(a.perm + q0 + 2) : 0u, ib = q0 + 3 < q1 ? __ldg(a.perm + q0 + 3) : 0u;
   for (int p = q0; p < q1; p += 2) {
     const bool two = p + 1 < q1;
-    if (p + 2 < q1) na.fetch(ia, a.cell, a.off, nullptr, ls);
-    if (p + 3 < q1) nb.fetch(ib, a.cell, a.off, nullptr, ls);
+    if (p + 2 < q1) {
+      na.fetch(ia, a.cell, a.off, nullptr, ls);
+      na.fetch_kick(a.vel, a.off, kax_a);
+    }
+    if (p + 3 < q1) {
+      nb.fetch(ib, a.cell, a.off, nullptr, ls);
+      nb.fetch_kick(a.vel, a.off, kax_b);
+    }
     if (p + 4 < q1) ia = __ldg(a.perm + p + 4);
     if (p + 5 < q1) ib = __ldg(a.perm + p + 5);
 #pragma unroll
@@ -597,10 +618,10 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
       if (a.g_out) a.g_out[3 * i + ax] = g;
       if (!isfinite(g)) set_status(a.status, ST_NAN);
       if (a.do_kick) {
-        const float v = a.vel[3 * i + ax] + g * a.dt;
+        const float v = q.kv + g * a.dt;
         a.vel[3 * i + ax] = v;
         if (a.do_drift) {
-          const float o = a.off[3 * i + ax] + v * a.dt_over_s;
+          const float o = q.ko + v * a.dt_over_s;
           const float sh = floorf(o + 0.5f);
           int c = (ax == 0 ? q.c0 : (ax == 1 ? q.c1 : q.c2)) + (int)sh;
           c += c < 0 ? a.n : (c >= a.n ? -a.n : 0);
