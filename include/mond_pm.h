@@ -222,6 +222,14 @@ int mond_pm_shell_mass(mond_pm_t h, int which, const double center[3], double dr
  * mond_pm_density times s^3). Synchronises. */
 int mond_pm_box_mass(mond_pm_t h, int which, const int32_t lo[3], const int32_t hi[3], double* out);
 
+/* Replace the H state (MOND_FIELD_H, what MOND_WARM_PREV starts from) by H
+ * (device float32, 3 compact planes of n_f^3, read before the call's work
+ * completes on the handle's stream; caller-owned). With the particle arrays
+ * this is all a run needs to resume: the deposit is exact and the rest of a
+ * step is deterministic, so a resumed run continues bit for bit. Enqueued;
+ * does not synchronise. Errors: MOND_EINVAL (null H). */
+int mond_pm_set_h_state(mond_pm_t h, const float* H);
+
 /* External field by a dipole layer (Sect. 5.3): every later solve adds the
  * density +mass/(n_f^2 s^3) on the last plane of the domain along `axis`
  * (0, 1, 2 for x, y, z) and -mass/(n_f^2 s^3) on the first plane, the planes

@@ -57,6 +57,7 @@ SIGNATURES = {
     "mond_pm_gather": (_I, [_P, _P]),
     "mond_pm_density": (_I, [_P, _I, _P]),
     "mond_pm_set_dipole_layer": (_I, [_P, _I, _D]),
+    "mond_pm_set_h_state": (_I, [_P, _P]),
     "mond_pm_shell_mass": (_I, [_P, _I, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_D)]),
     "mond_pm_box_mass": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(_D)]),
@@ -245,6 +246,37 @@ class MondPM:
         """Host tensors (pinned, contiguous) in and out; synchronises."""
         self._check(lib().mond_pm_step_host(self.h, float(dt), int(n_iter), int(warm), _ptr(cell_host),
                                             _ptr(offset_host), _ptr(vel_host)))
+
+    def set_h_state(self, H):
+        """Replace the warm-start H state by H (device float32 [3, n, n, n])."""
+        if H.dtype != self.torch.float32 or not H.is_contiguous() or H.numel() != 3 * self.nf ** 3:
+            raise ValueError("H must be a contiguous float32 tensor of 3 n^3 values")
+        self._check(lib().mond_pm_set_h_state(self.h, _ptr(H)))
+
+    def checkpoint(self, f, step: int = 0):
+        """Write what a resumed run needs with torch.save: the bound particle
+        arrays, the H state and the step count (synchronises)."""
+        torch = self.torch
+        H = self.get_field(FIELD_H)
+        cell, off, vel, mass = self.particles
+        state = {"nf": self.nf, "step": int(step), "cell": cell.cpu(), "offset": off.cpu(), "vel": vel.cpu(),
+                 "mass": mass.cpu(), "H": H.cpu()}
+        torch.save(state, f)
+
+    def restore(self, f) -> int:
+        """Load a checkpoint into the bound particle arrays and the H state;
+        returns its step count."""
+        torch = self.torch
+        state = torch.load(f)
+        if state["nf"] != self.nf or state["mass"].numel() != self.particles[3].numel():
+            raise ValueError("checkpoint of another mesh or particle count")
+        for dst, key in zip(self.particles, ("cell", "offset", "vel", "mass")):
+            dst.copy_(state[key].to(self.device))
+        H = state["H"].to(self.device).contiguous()
+        torch.cuda.synchronize(self.device)  # torch's copies before the handle's stream reads them
+        self.set_h_state(H)
+        self.sync()
+        return int(state["step"])
 
     def set_dipole_layer(self, axis: int, mass: float):
         """External field by a dipole layer of masses +-mass on the domain's end planes along axis (-1: none)."""

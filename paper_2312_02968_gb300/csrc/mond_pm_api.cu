@@ -1098,6 +1098,13 @@ int mond_pm_deposit(mond_pm_t h) {
   return do_deposit(h);
 }
 
+int mond_pm_set_h_state(mond_pm_t h, const float* H) {
+  if (!h) return MOND_EINVAL;
+  if (!H) return fail(h, MOND_EINVAL, "set_h_state: null H");
+  CK(cudaMemcpyAsync(h->w.Hs, H, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
+  return MOND_OK;
+}
+
 int mond_pm_set_dipole_layer(mond_pm_t h, int axis, double mass) {
   if (!h) return MOND_EINVAL;
   if (axis < -1 || axis > 2 || !std::isfinite(mass)) return fail(h, MOND_EINVAL, "dipole layer: axis -1..2, finite mass");
