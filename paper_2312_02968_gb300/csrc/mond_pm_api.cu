@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mond_pm.h"
 #include "internal.h"
 #include "launch.h"
@@ -20,6 +22,14 @@
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range around a public call (a no-op unless a profiler is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 struct Workspace {
   uint32_t* status;
@@ -1093,6 +1103,7 @@ int mond_pm_bind_particles(mond_pm_t h, int64_t N, int32_t* cell, float* offset,
 }
 
 int mond_pm_deposit(mond_pm_t h) {
+  Range nvtx_range("mond_pm_deposit");
   if (!h) return MOND_EINVAL;
   if (!h->cell && h->N > 0) return fail(h, MOND_ESTATE, "no particles bound");
   return do_deposit(h);
@@ -1125,6 +1136,7 @@ int mond_pm_set_density(mond_pm_t h, const float* rho) {
 }
 
 int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess) {
+  Range nvtx_range("mond_pm_solve_field");
   if (!h) return MOND_EINVAL;
   if (!h->have_dep) return fail(h, MOND_ESTATE, "solve_field before deposit");
   if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
@@ -1136,6 +1148,7 @@ int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess)
 }
 
 int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out) {
+  Range nvtx_range("mond_pm_smooth");
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "smooth before solve_field");
   int rk = ensure_khat(h);
@@ -1159,6 +1172,7 @@ int mond_pm_smooth(mond_pm_t h, float* accel_mesh_out) {
 }
 
 int mond_pm_gather_push(mond_pm_t h, double dt) {
+  Range nvtx_range("mond_pm_gather_push");
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "gather_push before solve_field");
   int rc = do_gather(h, nullptr, dt, 1, 1);
@@ -1170,12 +1184,14 @@ int mond_pm_gather_push(mond_pm_t h, double dt) {
 }
 
 int mond_pm_half_kick(mond_pm_t h, double dt) {
+  Range nvtx_range("mond_pm_half_kick");
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "half_kick before solve_field");
   return do_gather(h, nullptr, dt, 1, 0);
 }
 
 int mond_pm_gather(mond_pm_t h, float* g_out) {
+  Range nvtx_range("mond_pm_gather");
   if (!h) return MOND_EINVAL;
   if (!h->have_solve) return fail(h, MOND_ESTATE, "gather before solve_field");
   if (!g_out && h->N > 0) return fail(h, MOND_EINVAL, "g_out is NULL");
@@ -1246,6 +1262,7 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
 }  // namespace
 
 int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm) {
+  Range nvtx_range("mond_pm_step");
   if (!h) return MOND_EINVAL;
   if (h->use_graph && !h->timing) return step_graph(h, dt, n_iter, warm);
   const int rc = step_checks(h, n_iter, warm);
@@ -1319,6 +1336,7 @@ int mond_pm_batch_destroy(mond_pm_batch_t b) {
 }
 
 int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, int warm) {
+  Range nvtx_range("mond_pm_batch_step");
   if (!b || n_steps < 0) return MOND_EINVAL;
   const int n = (int)b->hs.size();
   for (auto h : b->hs) {
@@ -1460,6 +1478,7 @@ int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cel
 }
 
 int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out) {
+  Range nvtx_range("mond_pm_diagnostics");
   if (!h || !out) return MOND_EINVAL;
   memset(out, 0, sizeof *out);
   CK(cudaMemsetAsync(h->w.red, 0, sizeof(double) * 32, h->st));
@@ -1506,6 +1525,7 @@ int mond_pm_diagnostics(mond_pm_t h, mond_pm_diag* out) {
 }
 
 int mond_pm_density(mond_pm_t h, int which, float* out) {
+  Range nvtx_range("mond_pm_density");
   if (!h) return MOND_EINVAL;
   if (!out || ((uintptr_t)out & 15)) return fail(h, MOND_EINVAL, "out must be a 16-byte aligned device pointer");
   const float *g, *g2;

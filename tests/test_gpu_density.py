@@ -232,3 +232,26 @@ def test_dipole_layer_graph_recapture(B):
         h.close()
     # the second run changed the mass between steps: the replayed graph must see it
     assert not np.array_equal(out[0], out[1])
+
+
+def test_density_on_a_padded_grid(B):
+    # pad = 2: the physical 24^3 box in the middle of a 48^3 periodic domain;
+    # the densities cover the whole domain
+    n, pad, N = 24, 2, 4000
+    nf = n * pad
+    p = W.isothermal(nf, 1.0, N, 2.5, 0.2 * nf, seed=14)
+    dev = torch.device("cuda", 0)
+    h = B.MondPM(n, pad, float(n), 1.0, 1.0, 0, 1.0, N)
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    h.bind_particles(*t)
+    h.deposit()
+    h.solve_field(3)
+    gN = h.get_field(B.FIELD_GN).cpu().numpy().astype(np.float64)
+    acc = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    for kind in KINDS:
+        got = h.density(kind).cpu().numpy()
+        assert got.shape == (nf, nf, nf)
+        assert rel(got, oracle_density(kind, gN, acc, 1.0, 1.0)) < 2e-6
+    lo, hi = [nf // 4] * 3, [3 * nf // 4 - 1] * 3
+    assert h.box_mass(1, lo, hi) == pytest.approx(oracle.box_flux_mass(acc, 1.0, 1.0, lo, hi), rel=1e-6)
+    h.close()

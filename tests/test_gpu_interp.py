@@ -138,3 +138,24 @@ def test_state_errors(B, setup):
     with pytest.raises(B.MondError):  # Newton only: no smoothed mesh
         h.gather()
     h.close()
+
+
+def test_interpolating_gather_on_a_padded_grid(B):
+    n, pad, N, K = 24, 2, 3000, 3
+    nf = n * pad
+    p = W.isothermal(nf, 1.0, N, 2.5, 0.2 * nf, seed=15)
+    dev = torch.device("cuda", 0)
+    h = B.MondPM(n, pad, float(n), 1.0, 1.0, B.MU_DEEP, 1.5, N)
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    h.bind_particles(*t)
+    h.set_option(B.OPT_GATHER, 3)
+    h.deposit()
+    h.solve_field(K)
+    S = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    g = h.gather().cpu().numpy()
+    assert rel(g, oracle.interp_gather(3, S, p["cell"], p["offset"].astype(np.float64))) < 2e-6
+    dep, ka, _ = oracle.deposit_fixed(nf, 1.5, p["cell"], p["offset"], p["mass"])
+    _, rho = oracle.acc_to_rho(dep, ka, 1.0)
+    ref = oracle.solve(rho, 1.0, 1.0, 1.0, oracle.MU_DEEP, K, want=("acc",))["acc"]
+    assert rel(S, oracle.node_smoothed(1.5, ref)) < 1e-5
+    h.close()
