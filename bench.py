@@ -304,8 +304,23 @@ def run_learned(args, dev):
     finally:
         torch.cuda.synchronize()
         torch.cuda.set_stream(prev)
+    import math
+
+    stages = ev.pop("guess_stages_ms", {})
     plain4 = ev["plain4"]
     best = min((k for k in ev if k.startswith("guess")), key=lambda k: ev[k]["force_err_median"])
+    # the plain solve's error at each seeded solve's time (log-linear between the plain points)
+    pts = sorted((ev[k]["ms_per_solve"], math.log(ev[k]["force_err_median"])) for k in ev if k.startswith("plain"))
+
+    def plain_log_err(ms):
+        for (t0, e0), (t1, e1) in zip(pts, pts[1:]):
+            if ms <= t1:
+                return e0 + (e1 - e0) * (ms - t0) / (t1 - t0)
+        (t0, e0), (t1, e1) = pts[-2], pts[-1]
+        return e0 + (e1 - e0) * (ms - t0) / (t1 - t0)
+
+    gain = {k: math.exp(plain_log_err(ev[k]["ms_per_solve"])) / ev[k]["force_err_median"]
+            for k in ev if k.startswith("guess")}
     meets = [k for k in ev if ev[k]["force_err_median"] <= 1e-4]
     fastest_meeting = min(meets, key=lambda k: ev[k]["ms_per_solve"]) if meets else None
     return {"workload": "sphere mixtures (1-8 Plummer/Hernquist), 1e7 particles, 256^3, standard mu, sigma 1 px",
@@ -314,6 +329,8 @@ def run_learned(args, dev):
             "train": {k: tr[k] for k in ("pairs", "epochs", "batch", "lr", "s_pairs", "s_train")} |
                      {"loss_first": tr["loss"][0], "loss_last": tr["loss"][-1]},
             "solves": ev, "ref": "particle forces of the mean of iterates 40 and 41",
+            "guess_stages_ms": stages,
+            "error_ratio_plain_over_guess_at_equal_time": gain,
             "guess1_vs_plain4_speed": plain4["ms_per_solve"] / ev["guess1"]["ms_per_solve"],
             "best_guess": best, "fastest_at_1e-4": fastest_meeting}
 

@@ -58,6 +58,7 @@ def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_gu
     errs = {f"plain{k}": [] for k in ks_plain}
     errs.update({f"guess{k}": [] for k in ks_guess})
     times = {k: [] for k in errs}
+    stages = {}
     for sd in seeds:
         p, _ = sphere_mixture(h.nf, n_particles, sd)
         t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
@@ -105,9 +106,23 @@ def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_gu
                 run(f"plain{k}", lambda k=k: h.solve_field(k, B.WARM_NONE))
             for k in ks_guess:
                 run(f"guess{k}", lambda k=k: gs.solve(k))
+            if not stages:
+                # where a seeded solve's time goes (first system): each stage one graph replay
+                newton = replay_ms(graph_of(lambda: (h.deposit(), h.solve_field(0, B.WARM_NONE)))) - dep_ms
+                stages["newton"] = newton
+                stages["features"] = replay_ms(graph_of(
+                    lambda: S.features(gs.gN, h.nf, net.n, 1.0, gs.x, gs.scale, st)))
+                stages["forward"] = replay_ms(graph_of(lambda: net.forward(gs.x, gs.y)))
+                stages["upsample"] = replay_ms(graph_of(
+                    lambda: S.upsample(gs.y, h.nf, net.n, gs.scale, gs.H, st, gs.up_scratch)))
+                stages["solve1_from_guess"] = replay_ms(graph_of(lambda: (
+                    h.deposit(), h.solve_field(0, B.WARM_NONE), h.solve_field(1, B.WARM_GUESS_RAW, gs.H)))) \
+                    - dep_ms - newton
         h.sync()
-    return {k: {"force_err_median": float(np.median(errs[k])), "force_err_max": float(np.max(errs[k])),
-                "ms_per_solve": float(np.mean(times[k]))} for k in errs}
+    out = {k: {"force_err_median": float(np.median(errs[k])), "force_err_max": float(np.max(errs[k])),
+               "ms_per_solve": float(np.mean(times[k]))} for k in errs}
+    out["guess_stages_ms"] = stages
+    return out
 
 
 def main():
