@@ -77,3 +77,36 @@ def test_binary_circular_orbit_one_period(B):
     print(f"binary: separation {seps.min():.3f}..{seps.max():.3f} px, turn {(turn[-1] - turn[0]) / (2 * math.pi):.4f} "
           f"of 2 pi, L_z drift {L1 / L0 - 1:.2e}")
     h.close()
+
+
+def test_isothermal_sphere_stays_in_equilibrium(B):
+    """The bench's system (Sect. 4.3: 1e6 particles, 256^3, b = 8 px, deep
+    mu, K = 4, dt = 0.25) for 60 graph-replayed steps: the kinetic energy stays
+    at M v^2/2 = sqrt(G M a0)/3 (Eq. vsqsuare) to a few per cent, the total
+    momentum stays near its initial value and the deposited mass stays the
+    particles' mass times the ball's weight sum (R1: no renormalisation)."""
+    n, N, dt, K = 256, 1_000_000, 0.25, 4
+    p = W.isothermal(n, 1.0, N, 8.0, 0.4 * n, seed=1)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        h = B.MondPM(n, 1, float(n), 1.0, 1.0, B.MU_DEEP, 1.5, N, stream=st)
+        t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+    torch.cuda.synchronize()
+    h.bind_particles(*t)
+    h.set_option(B.OPT_USE_GRAPH, 1)
+    want = 1.0 / 3.0
+    d0 = h.diagnostics()
+    assert abs(d0["e_kin"] / want - 1) < 0.03  # the sampler's Maxwellian
+    P0 = np.array(d0["momentum"])
+    ek = []
+    for _ in range(6):
+        for _ in range(10):
+            h.step(dt, K, B.WARM_NONE)
+        d = h.diagnostics()
+        ek.append(d["e_kin"])
+        assert np.linalg.norm(np.array(d["momentum"]) - P0) < 5e-3 * math.sqrt(2 * d["e_kin"])
+        assert d["rho_mass"] == pytest.approx(d["mass"], rel=3e-3)
+    ek = np.array(ek)
+    print(f"isothermal: E_kin / (sqrt(GMa0)/3) over 60 steps: {np.round(ek / want, 4).tolist()}")
+    assert np.all(np.abs(ek / want - 1) < 0.06)
+    h.close()
