@@ -632,6 +632,23 @@ def main():
             roof = {"bound": "hbm", "kernel": dom["name"], "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_source": peak_src, "traffic": traffic,
                     "algorithmic_bytes_per_launch": algo, "ms_per_launch": per_launch_ms}
+        # the particle kernels are not HBM-bound: their tap rate, live, and the share
+        # of the L1/shared-memory pipe they use (ncu, profiles/particles.json)
+        r = int(math.ceil(4 * WL["sigma"])) + 1
+        taps = sum(1 for dz in range(-r, r + 1) for dy in range(-r, r + 1) for dx in range(-r, r + 1)
+                   if dx * dx + dy * dy + dz * dz < 16 * WL["sigma"] ** 2)
+        try:
+            with open(os.path.join(ROOT, "profiles", "particles.json")) as f:
+                pj = json.load(f)
+        except Exception:
+            pj = {}
+        part = {}
+        for s in stats:
+            if s["name"] in ("deposit", "gather_push"):
+                ms1 = s["ms"] / s["launches"]
+                part[s["name"]] = {"ms_per_launch": ms1, "taps_per_launch": taps * N,
+                                   "taps_per_s": taps * N / (ms1 / 1000.0),
+                                   "l1tex_pipe_frac_ncu": pj.get(s["name"], {}).get("l1tex_throughput_frac")}
         kern = [{"name": s["name"], "launches": s["launches"], "ms": round(s["ms"], 4),
                  "share": round(s["ms"] / sum(x["ms"] for x in stats), 4),
                  "GBps": round(s["bytes"] / (s["ms"] / 1000.0) / 1e9, 1) if s["ms"] > 0 else None} for s in stats]
@@ -646,7 +663,8 @@ def main():
                 "accuracy": acc_info,
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 36 * N,
                         "d2h_bytes_per_step": 36 * N},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "kernels": kern,
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "particle_kernels": part,
+                "kernels": kern,
                 "ms_per_step_event_timed": ms_timed_mode / args.steps,
                 "density": dens_info, "interp_gather": interp_info, "learned": learned, "ensemble": ensemble}
         if cpu:
