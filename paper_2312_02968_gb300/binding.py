@@ -166,6 +166,7 @@ class MondPM:
         self.torch = torch
         self.n, self.pad, self.nf = n, pad, n * pad
         self.box, self.s = box, box / n
+        self.kernel_width = float(kernel_width)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         nbytes = workspace_bytes(n, pad, kernel_width, max_particles)
@@ -350,12 +351,42 @@ class MondPM:
                  "bytes": float(arr[i].bytes)} for i in range(min(cnt.value, 32))]
 
 
-def autotune(h: MondPM, n_iter: int = 4, trials: int = 3):
+def tune_key(h: MondPM, n_iter: int) -> str:
+    """Key of a tuning result: the GPU, the FFT-domain side, the particle count
+    (rounded to a power of two), the kernel width and the iteration count."""
+    torch = h.torch
+    n = h.particles[3].numel() if getattr(h, "particles", None) else 0
+    return (f"{torch.cuda.get_device_name(h.device)}|nf={h.nf}|N~2^{max(n, 1).bit_length()}|"
+            f"sigma={h.kernel_width:g}|K={int(n_iter)}")
+
+
+def autotune(h: MondPM, n_iter: int = 4, trials: int = 3, cache: str | None = None):
     """Pick the work-item size and pass variant of one handle by timing
-    zero-length steps (mond_pm_autotune); returns (chunk, pipelined)."""
+    zero-length steps (mond_pm_autotune); returns (chunk, pipelined). With a
+    cache file (JSON), a result already stored for the same key is applied
+    without timing, and a new result is stored."""
+    import json
+    import os
+
+    key = tune_key(h, n_iter) if cache else None
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            chunk, pipelined = int(table[key]["chunk"]), int(table[key]["pipelined"])
+            h.set_option(OPT_CHUNK, chunk)
+            h.set_option(OPT_PIPELINED, pipelined)
+            return chunk, pipelined
     c = ctypes.c_int64()
     p = ctypes.c_int()
     h._check(lib().mond_pm_autotune(h.h, int(n_iter), int(trials), ctypes.byref(c), ctypes.byref(p)))
+    if cache:
+        table[key] = {"chunk": int(c.value), "pipelined": int(p.value)}
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
     return int(c.value), int(p.value)
 
 

@@ -113,3 +113,29 @@ def test_autotune_choices_give_identical_states(B):
     pb = b[0] + b[1].astype(np.float64)
     assert np.max(np.abs(pa - pb)) < 1e-4
     assert np.linalg.norm(a[2] - b[2]) <= 1e-5 * np.linalg.norm(a[2])
+
+
+def test_autotune_cache(B, tmp_path):
+    # a second handle of the same key takes the stored choice without timing
+    n = 32
+    p = W.isothermal(n, 1.0, 20000, 3.0, 10.0, seed=21)
+    cache = str(tmp_path / "tune.json")
+    st = torch.cuda.Stream()
+    hs = []
+    for _ in range(2):
+        with torch.cuda.stream(st):
+            h = B.MondPM(n, 1, float(n), 1.0, 1.0, 0, 1.0, len(p["mass"]), stream=st)
+            t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+        torch.cuda.synchronize()
+        h.bind_particles(*t)
+        hs.append((h, t))
+    first = B.autotune(hs[0][0], 2, 2, cache=cache)
+    import json
+
+    table = json.load(open(cache))
+    assert list(table.values()) == [{"chunk": first[0], "pipelined": first[1]}]
+    l0 = hs[1][0].kernel_launches()
+    second = B.autotune(hs[1][0], 2, 2, cache=cache)
+    assert second == first and hs[1][0].kernel_launches() == l0  # nothing was timed
+    for h, _ in hs:
+        h.close()
