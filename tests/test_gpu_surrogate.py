@@ -1,7 +1,7 @@
 """What the trained surrogate gains: a small network trained on the GPU by
 the library's own forward/backward kernels, on pairs the solver makes, seeds
 an iteration that then lands closer to the converged field than the same
-number of plain iterations from H = 0. The plain iteration is the judge."""
+number of plain iterations from H = 0; the plain iteration measures the error."""
 import numpy as np
 import pytest
 
