@@ -280,6 +280,52 @@ def run_interp(h, B, stream, t, init, steps, warmup):
     return res
 
 
+def run_scan(dev, steps):
+    """Step time against the particle count on two mesh sizes (the runtime
+    split of Sect. 5.2, Fig. 13: the transforms cost the same for any N, the
+    particle kernels grow linearly): isothermal spheres (b = n/32, deep mu,
+    sigma 1.5 px, K = 4), graph-replayed steps, then the same steps with
+    event-timed launches for the split."""
+    import numpy as np
+    import torch
+
+    from paper_2312_02968_gb300 import binding as B
+    from paper_2312_02968_gb300 import workloads as W
+
+    rows = []
+    for n, Ns in ((128, (1_000, 10_000, 100_000, 1_000_000)), (256, (1_000, 10_000, 100_000, 1_000_000, 10_000_000))):
+        for N in Ns:
+            p = W.isothermal(n, 1.0, N, n / 32.0, 0.4 * n, seed=3)
+            st = torch.cuda.Stream(device=dev)
+            with torch.cuda.stream(st):
+                h = B.MondPM(n, 1, float(n), 1.0, 1.0, B.MU_DEEP, 1.5, N, stream=st)
+                t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+            torch.cuda.synchronize()
+            h.bind_particles(*t)
+            h.set_option(B.OPT_USE_GRAPH, 1)
+            for _ in range(3):
+                h.step(0.25, 4, B.WARM_NONE)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(steps):
+                h.step(0.25, 4, B.WARM_NONE)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            h.set_option(B.OPT_TIMING, 1)
+            h.kernel_stats()
+            for _ in range(steps):
+                h.step(0.25, 4, B.WARM_NONE)
+            stats = h.kernel_stats()
+            h.close()
+            mesh = sum(s["ms"] for s in stats if s["name"][:5] in ("xpass", "ypass", "zpass")) / steps
+            part = sum(s["ms"] for s in stats if s["name"] in ("bin", "deposit", "gather_push")) / steps
+            rows.append({"n": n, "N": N, "ms_per_step": ms, "transforms_ms": mesh, "particles_ms": part,
+                         "particle_steps_per_s": N * 1000.0 / ms})
+    return rows
+
+
 def run_learned(args, dev):
     """Learned warm start (sphere mixtures, 256^3, standard mu, sigma 1 px,
     G = a0 = 1): train the FNO on solver-made pairs, then time and score
@@ -451,6 +497,7 @@ def main():
     ap.add_argument("--learned-fno", default="32,32,16,4", help="network grid side, width, modes, layers")
     ap.add_argument("--ensemble-systems", type=int, default=64, help="systems of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20)
+    ap.add_argument("--scan", action="store_true", help="also time steps against N on 128^3 and 256^3")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -607,7 +654,9 @@ def main():
     e2e_s = R.max_over_ranks(e2e_s, dist, dev)
     e2e_value = world * args.steps / e2e_s
 
-    learned = ensemble = None
+    learned = ensemble = scan = None
+    if rank == 0 and args.scan:
+        scan = run_scan(dev, args.steps)
     if rank == 0 and args.learned_pairs > 0:
         learned = run_learned(args, dev)
     if args.ensemble_systems > 0:
@@ -667,6 +716,8 @@ def main():
                 "kernels": kern,
                 "ms_per_step_event_timed": ms_timed_mode / args.steps,
                 "density": dens_info, "interp_gather": interp_info, "learned": learned, "ensemble": ensemble}
+        if scan is not None:
+            line["scan"] = scan
         if cpu:
             line["cpu_baseline"] = {"value": 1.0 / cpu["t_step"], "unit": "solves/s", "cores": cpu["cores"],
                                     "kind": "oracle",

@@ -401,7 +401,7 @@ cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
   const double S = spec_bytes(h), R = real_bytes(h);
   double bytes = 0;
   switch (mode) {
-    case passes::X_RHO: bytes = 2 * R + R + S; break;  // int64 in, FP32 density out, spectrum out
+    case passes::X_RHO: bytes = 2 * R + (a.rho_out ? R : 0) + S; break;  // int64 in, [FP32 density out,] spectrum out
     case passes::X_NU_FIRST: bytes = 6 * S + 3 * R + (a.H0 ? 3 * R : 0); break;
     case passes::X_NU: bytes = 6 * S + 3 * R + (a.Hs_out ? 3 * R * (a.red ? 2 : 1) : 0); break;
     case passes::X_MU: bytes = 6 * S + 3 * R; break;
@@ -726,7 +726,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     x.ncomp = 1;
     x.spec = W;
     x.dep = h->w.dep;
-    x.rho_out = h->w.rho;
+    x.rho_out = h->keep_phi ? h->w.rho : nullptr;  // the density plane is read only by the potential energy
     x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
     x.ext_axis1 = h->ext_axis + 1;
     x.ext_rho = (float)(h->ext_mass / ((double)h->nf * h->nf * h->s * h->s * h->s));
