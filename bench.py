@@ -260,6 +260,13 @@ def run_interp(h, B, stream, t, init, steps, warmup):
 
     K, dt = WL["K"], WL["dt"]
     res = {}
+    try:
+        return _run_interp(h, B, stream, t, init, steps, warmup, K, dt, res, torch)
+    finally:
+        h.set_option(B.OPT_GATHER, 0)  # the steps after this section use Eq. gi
+
+
+def _run_interp(h, B, stream, t, init, steps, warmup, K, dt, res, torch):
     for order in (1, 3):
         for k in t:
             t[k].copy_(init[k])
