@@ -146,6 +146,49 @@ __device__ __forceinline__ void stage(float2* s, int PS, int SS, int Ns, const f
   __syncthreads();
 }
 
+// As stage, for NC groups of NSEQ sequences: sequence l of group c starts at
+// s + c CS + l SS, so the groups (the components of a tile) share the
+// stage's two barriers.
+template <int N, int R, int DIR, int NSEQ, int NC, int NT>
+__device__ __forceinline__ void stage_c(float2* s, int PS, int SS, int CS, int Ns, const float2* tw, int twstride,
+                                        int tid) {
+  constexpr int NB = N / R;
+  constexpr int TOT = NB * NSEQ * NC;
+  constexpr int BPT = (TOT + NT - 1) / NT;
+  float2 v[BPT][R];
+  const int tstep = (N / (Ns * R)) * twstride;
+#pragma unroll
+  for (int b = 0; b < BPT; b++) {
+    int g = tid + b * NT;
+    if (TOT % NT == 0 || g < TOT) {
+      int q = g % (NSEQ * NC), j = g / (NSEQ * NC);
+      int k = j % Ns;
+      const float2* base = s + (q / NSEQ) * CS + (q % NSEQ) * SS;
+#pragma unroll
+      for (int r = 0; r < R; r++) v[b][r] = base[(j + r * NB) * PS];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; r++) v[b][r] = cmul(v[b][r], twid<DIR>(tw[r * k * tstep]));
+      }
+      dftR<R, DIR>(v[b]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; b++) {
+    int g = tid + b * NT;
+    if (TOT % NT == 0 || g < TOT) {
+      int q = g % (NSEQ * NC), j = g / (NSEQ * NC);
+      int k = j % Ns;
+      int o = (j / Ns) * Ns * R + k;
+      float2* base = s + (q / NSEQ) * CS + (q % NSEQ) * SS;
+#pragma unroll
+      for (int r = 0; r < R; r++) base[(o + r * Ns) * PS] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
 // Radix plans: product of the stage radices equals N.
 template <int N>
 struct Plan;
@@ -176,6 +219,16 @@ __device__ __forceinline__ void fft(float2* s, int PS, int SS, const float2* tw,
   stage<N, R0, DIR, NSEQ, NT>(s, PS, SS, 1, tw, twstride, tid);
   if constexpr (R1 > 1) stage<N, R1, DIR, NSEQ, NT>(s, PS, SS, R0, tw, twstride, tid);
   if constexpr (R2 > 1) stage<N, R2, DIR, NSEQ, NT>(s, PS, SS, R0 * R1, tw, twstride, tid);
+}
+
+// fft over NC groups of NSEQ sequences (group c at s + c CS), one pass of
+// barriers for all groups.
+template <int N, int DIR, int NSEQ, int NC, int NT>
+__device__ __forceinline__ void fft_c(float2* s, int PS, int SS, int CS, const float2* tw, int twstride, int tid) {
+  constexpr int R0 = Plan<N>::r0, R1 = Plan<N>::r1, R2 = Plan<N>::r2;
+  stage_c<N, R0, DIR, NSEQ, NC, NT>(s, PS, SS, CS, 1, tw, twstride, tid);
+  if constexpr (R1 > 1) stage_c<N, R1, DIR, NSEQ, NC, NT>(s, PS, SS, CS, R0, tw, twstride, tid);
+  if constexpr (R2 > 1) stage_c<N, R2, DIR, NSEQ, NC, NT>(s, PS, SS, CS, R0 * R1, tw, twstride, tid);
 }
 
 }  // namespace fftk

@@ -19,7 +19,8 @@
 
 namespace passes {
 
-constexpr int NT = 256;  // threads per CTA for every pass
+constexpr int NT = 256;   // threads per CTA of the y- and z-passes
+constexpr int NTX = 256;  // threads per CTA of the x-pass
 
 template <int N>
 struct XCfg {
@@ -157,7 +158,7 @@ __device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict
   using C = XCfg<N>;
   constexpr int SPL = C::H + 1;  // complex values of a line that are used (kx = 0..N/2)
   const float2* src = g + line0 * C::SP;
-  for (int i = tid; i < C::L * SPL; i += NT) {
+  for (int i = tid; i < C::L * SPL; i += NTX) {
     const int l = i / SPL, kk = i % SPL;
     tma::async_copy8(sm + kk * C::LP + l, src + (int64_t)l * C::SP + kk);
   }
@@ -168,7 +169,7 @@ __device__ __forceinline__ void x_store_spec(const float2* sm, float2* __restric
   using C = XCfg<N>;
   constexpr int Q = C::SP / 2;
   float4* dst = reinterpret_cast<float4*>(g + line0 * C::SP);
-  for (int i = tid; i < C::L * Q; i += NT) {
+  for (int i = tid; i < C::L * Q; i += NTX) {
     int l = i / Q, kk = (i % Q) * 2;
     float2 a = sm[kk * C::LP + l];
     float2 b = (kk + 1 <= C::H) ? sm[(kk + 1) * C::LP + l] : make_float2(0.f, 0.f);
@@ -180,11 +181,13 @@ __device__ __forceinline__ void x_store_spec(const float2* sm, float2* __restric
 // a length-N/2 inverse transform of Y then yields x[2j] + i x[2j+1].
 // The imaginary parts of X[0] and X[N/2] are dropped (real part of the inverse).
 template <int N>
-__device__ __forceinline__ void x_pre_c2r(float2* sm, const float2* tw, int tid) {
+__device__ __forceinline__ void x_pre_c2r(float2* sm0, int nc, const float2* tw, int tid) {
   using C = XCfg<N>;
   constexpr int NP = N / 4 + 1;  // pairs (k, N/2 - k), k = 0..N/4
-  for (int i = tid; i < NP * C::L; i += NT) {
-    int l = i % C::L, k = i / C::L;
+  constexpr int TILE = C::ROWS * C::LP;
+  for (int i = tid; i < NP * C::L * nc; i += NTX) {
+    float2* sm = sm0 + (i / (NP * C::L)) * TILE;  // component tile
+    int l = i % C::L, k = (i / C::L) % NP;
     if (k == 0) {
       float x0 = sm[0 * C::LP + l].x, xn = sm[C::H * C::LP + l].x;
       sm[0 * C::LP + l] = make_float2(x0 + xn, x0 - xn);
@@ -207,11 +210,13 @@ __device__ __forceinline__ void x_pre_c2r(float2* sm, const float2* tw, int tid)
 // Z = DFT_{N/2}(x[2j] + i x[2j+1]) -> X[k] = E[k] + W^k O[k], k = 0..N/2,
 // E = (Z[k] + conj Z[N/2-k])/2, O = (Z[k] - conj Z[N/2-k])/(2i), W = e^{-2 pi i/N}.
 template <int N>
-__device__ __forceinline__ void x_post_r2c(float2* sm, const float2* tw, int tid) {
+__device__ __forceinline__ void x_post_r2c(float2* sm0, int nc, const float2* tw, int tid) {
   using C = XCfg<N>;
   constexpr int NP = N / 4 + 1;
-  for (int i = tid; i < NP * C::L; i += NT) {
-    int l = i % C::L, k = i / C::L;
+  constexpr int TILE = C::ROWS * C::LP;
+  for (int i = tid; i < NP * C::L * nc; i += NTX) {
+    float2* sm = sm0 + (i / (NP * C::L)) * TILE;  // component tile
+    int l = i % C::L, k = (i / C::L) % NP;
     if (k == 0) {
       float2 z = sm[0 * C::LP + l];
       sm[0 * C::LP + l] = make_float2(z.x + z.y, 0.f);
@@ -236,8 +241,20 @@ __device__ __forceinline__ void x_post_r2c(float2* sm, const float2* tw, int tid
   __syncthreads();
 }
 
+// The half-length complex transforms of all nc component tiles of an x-pass
+// tile in one pass of barriers.
+template <int N, int DIR>
+__device__ __forceinline__ void xfft(float2* buf, int nc, const float2* tw, int tid) {
+  using C = XCfg<N>;
+  constexpr int TILE = C::ROWS * C::LP;
+  // two component tiles per pass of barriers (one radix-16 butterfly per thread), then the rest
+  int c = 0;
+  for (; c + 2 <= nc; c += 2) fftk::fft_c<C::H, DIR, C::L, 2, NTX>(buf + c * TILE, C::LP, 1, TILE, tw, 2, tid);
+  if (c < nc) fftk::fft_c<C::H, DIR, C::L, 1, NTX>(buf + c * TILE, C::LP, 1, TILE, tw, 2, tid);
+}
+
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
+__global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
   using C = XCfg<N>;
   extern __shared__ float2 smem[];
   float2* tw = smem;                       // N twiddles
@@ -245,7 +262,7 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
   constexpr int TILE = C::ROWS * C::LP;
   const int tid = threadIdx.x;
   const int64_t line0 = (int64_t)blockIdx.x * C::L;
-  for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+  for (int i = tid; i < N; i += NTX) tw[i] = a.tw[i];
   const int nc = (MODE == X_RHO) ? 1 : a.ncomp;
 
   constexpr bool INV = (MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_INV);
@@ -270,17 +287,15 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
     for (int c = 0; c < nc; c++) x_load_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
     tma::async_wait_all();
     __syncthreads();
-    for (int c = 0; c < nc; c++) {
-      x_pre_c2r<N>(buf + c * TILE, tw, tid);
-      fftk::fft<C::H, +1, C::L, NT>(buf + c * TILE, C::LP, 1, tw, 2, tid);
-    }
+    x_pre_c2r<N>(buf, nc, tw, tid);
+    xfft<N, +1>(buf, nc, tw, tid);
   }
 
   // Pointwise stage on real samples: point (j, l) holds x[2j], x[2j+1] of line l.
   const int64_t rbase = line0 * N;  // real index of the first sample of the tile
   float sq_dh = 0.f, sq_gn = 0.f;
   bool bad = false;
-  for (int i = tid; i < C::L * C::H; i += NT) {
+  for (int i = tid; i < C::L * C::H; i += NTX) {
     int j = i % C::H, l = i / C::H;
     int64_t ri = rbase + (int64_t)l * N + 2 * j;
     float2* const p0 = buf + j * C::LP + l;  // component c at p0 + c * TILE
@@ -398,10 +413,8 @@ __global__ void __launch_bounds__(NT) k_xpass(XArgs a, int64_t nlines) {
 
   if constexpr (FWD) {
     __syncthreads();
-    for (int c = 0; c < nc; c++) {
-      fftk::fft<C::H, -1, C::L, NT>(buf + c * TILE, C::LP, 1, tw, 2, tid);
-      x_post_r2c<N>(buf + c * TILE, tw, tid);
-    }
+    xfft<N, -1>(buf, nc, tw, tid);
+    x_post_r2c<N>(buf, nc, tw, tid);
     for (int c = 0; c < nc; c++) x_store_spec<N>(buf + c * TILE, a.spec + c * a.pstride, line0, tid);
   }
 }

@@ -27,7 +27,7 @@ cudaError_t launch_x(const XArgs& a, cudaStream_t st) {
   cudaError_t e = set_smem(k_xpass<N, MODE>, x_smem(4));
   if (e != cudaSuccess) return e;
   int64_t nlines = (int64_t)N * N;
-  k_xpass<N, MODE><<<(unsigned)(nlines / XCfg<N>::L), NT, sm, st>>>(a, nlines);
+  k_xpass<N, MODE><<<(unsigned)(nlines / XCfg<N>::L), NTX, sm, st>>>(a, nlines);
   return cudaGetLastError();
 }
 
