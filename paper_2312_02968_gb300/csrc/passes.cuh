@@ -587,7 +587,7 @@ namespace passes {
 // Tile geometry of the pipelined passes: P columns per tile (y: PY, z: PZ),
 // row boxes of at most 256 (the TMA box limit) dividing N.
 constexpr int pipe_py(int n) { return n >= 384 ? 8 : 16; }
-constexpr int pipe_pz(int n) { return n >= 384 ? 4 : (n >= 192 ? 8 : 16); }
+constexpr int pipe_pz(int n) { return n >= 256 ? 4 : (n >= 192 ? 8 : 16); }
 constexpr int pipe_box(int n) { return n <= 256 ? n : (n % 256 == 0 ? 256 : 128); }
 
 template <int N>
@@ -703,17 +703,17 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(const __grid_constant__ tma::
 // (4-D maps with the component as a dimension, so one FFT call transforms the
 // three components) and, for Z_NEWTON and Z_FINAL, a scalar region
 // [z row][column] for rho^ (input) or phi^ (output, component 3 of A).
-// threads per pipelined z-pass CTA: 384 = one radix-16 butterfly per thread
-// for the 3 x 8 sequences of a 256-point tile, so no thread holds two.
-template <int MODE>
-constexpr int zthreads() { return 384; }
+// threads per pipelined z-pass CTA: at N = 256, 192 = one radix-16 butterfly
+// per thread for the 3 x 4 sequences of a tile (four CTAs per SM); 384 elsewhere.
+template <int N, int MODE>
+constexpr int zthreads() { return N == 256 ? 192 : 384; }
 
 // SC: a separate scalar region per stage (needed only when phi is stored);
 // without it the Newton pass lands its scalar input in the last third of the
 // vector region and reads it into registers before the outputs overwrite it,
 // so that every mode runs with three-component stages (two CTAs per SM).
-template <int N, int MODE, bool SC, int NTZ = zthreads<MODE>()>
-__global__ void __launch_bounds__(NTZ, 2) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
+template <int N, int MODE, bool SC, int NTZ = zthreads<N, MODE>()>
+__global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_constant__ tma::TensorMap in_map,
                                                    const __grid_constant__ tma::TensorMap out_map,
                                                    const __grid_constant__ tma::TensorMap phi_map, PipeZArgs a) {
   using C = PipeCfg<N>;

@@ -103,7 +103,7 @@ cudaError_t launch_zpipe_sc(const tma::TensorMap& in, const tma::TensorMap& out,
   cudaError_t e = set_smem(k_zpass_pipe<N, MODE, SC>, sm);
   if (e != cudaSuccess) return e;
   static int grid = 0;
-  constexpr int nt = zthreads<MODE>();
+  constexpr int nt = zthreads<N, MODE>();
   if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE, SC>, sm, nt);
   const int ntiles = PipeCfg<N>::NBLKZ * N;
   k_zpass_pipe<N, MODE, SC><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
