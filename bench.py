@@ -10,8 +10,13 @@ solve, gather and leapfrog push.
 Prints one JSON line. ``value`` is time steps (each with one MOND force solve)
 per second with inputs resident in HBM; ``e2e`` is the same through host
 buffers; ``warm`` is the warm-started variant (previous H, one iteration);
-``roofline`` is the dominant kernel's achieved HBM bandwidth against the
-measured peak; ``cpu_baseline`` times the CPU oracle on a bounded sample.
+``roofline`` is the dominant HBM-bound kernel's achieved bandwidth against the
+measured peak and ``particle_kernels`` the deposit's and gather's tap rates;
+``cpu_baseline`` times the CPU oracle on a bounded sample. Side sections:
+``density`` (Eq. apparentdensity kernels), ``interp_gather`` (the
+mesh-interpolating gather), ``learned`` (training and evaluating the learned
+warm start), ``ensemble`` (64 systems as one graph per step) and, with
+``--scan``, step times against the particle count.
 ``--impl reference`` times the CPU oracle alone (the reference arm).
 Under torchrun each rank steps its own independent replica (the single-system
 solve does not shard); ``value`` sums the replicas.
