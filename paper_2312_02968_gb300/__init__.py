@@ -13,13 +13,15 @@ A time step of one system::
 
     p = W.isothermal(256, 1.0, 1_000_000, 8.0, 102.4, seed=1)   # cell, offset, vel, mass
     st = torch.cuda.Stream()
-    h = B.MondPM(256, 1, 256.0, 1.0, 1.0, B.MU_DEEP, 1.5, 1_000_000, stream=st)
-    t = [torch.from_numpy(p[k]).cuda() for k in ("cell", "offset", "vel", "mass")]
-    h.bind_particles(*t)
-    h.set_option(B.OPT_USE_GRAPH, 1)          # each step one CUDA graph launch
-    h.step(0.25, 4, B.WARM_NONE)              # deposit, 4 iterations, gather, kick, drift
-    h.step(0.25, 1, B.WARM_PREV)              # warm start from the previous H
-    print(h.diagnostics()["e_kin"], h.density(B.DENS_PHANTOM).sum().item())
+    with torch.cuda.stream(st):               # the handle and torch's copies on one stream
+        h = B.MondPM(256, 1, 256.0, 1.0, 1.0, B.MU_DEEP, 1.5, 1_000_000, stream=st)
+        t = [torch.from_numpy(p[k]).cuda() for k in ("cell", "offset", "vel", "mass")]
+        h.bind_particles(*t)
+        h.set_option(B.OPT_USE_GRAPH, 1)      # each step one CUDA graph launch
+        h.step(0.25, 4, B.WARM_NONE)          # deposit, 4 iterations, gather, kick, drift
+        h.step(0.25, 1, B.WARM_PREV)          # warm start from the previous H
+        phantom = h.density(B.DENS_PHANTOM)   # apparent minus baryonic density
+        print(h.diagnostics()["e_kin"], phantom.sum().item())
 
 Modules: ``binding`` (the handle, batches, the autotuner), ``surrogate`` and
 ``train_surrogate`` (the learned warm start), ``workloads`` (seeded initial
