@@ -158,9 +158,10 @@ __device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict
   using C = XCfg<N>;
   constexpr int SPL = C::H + 1;  // complex values of a line that are used (kx = 0..N/2)
   const float2* src = g + line0 * C::SP;
+  const uint64_t pol = tma::policy_evict_first();  // read once: keep L2 for the prefetched planes
   for (int i = tid; i < C::L * SPL; i += NTX) {
     const int l = i / SPL, kk = i % SPL;
-    tma::async_copy8(sm + kk * C::LP + l, src + (int64_t)l * C::SP + kk);
+    tma::async_copy8_stream(sm + kk * C::LP + l, src + (int64_t)l * C::SP + kk, pol);
   }
 }
 
