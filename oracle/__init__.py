@@ -99,7 +99,14 @@ def lib():
             L.ora_fft1.argtypes = [i32, P, i32]
             L.ora_fft3_raw.argtypes = [i32, P, i32]
             L.ora_solve.restype = i32
-            L.ora_solve.argtypes = [i32, f64, f64, f64, i32, i32, P, P, i32, P, P, P, P, P]
+            L.ora_solve.argtypes = [i32, f64, f64, f64, i32, i32, P, P, i32, P, P, P, P, P, P]
+            L.ora_solve_increment.restype = i32
+            L.ora_solve_increment.argtypes = [i32, f64, f64, f64, i32, i32, P, P, P, P, P, P, P, P]
+            L.ora_linearised.argtypes = [i32, i32, f64, P, P, P]
+            L.ora_ynu_prime.restype = f64
+            L.ora_ynu_prime.argtypes = [i32, f64]
+            L.ora_xmu_prime.restype = f64
+            L.ora_xmu_prime.argtypes = [i32, f64]
             L.ora_gather.argtypes = [i32, f64, P, i64, P, P, P]
             L.ora_push.argtypes = [i32, f64, f64, i64, P, P, P, P, i32]
             L.ora_particle_diag.argtypes = [i32, f64, i64, P, P, P, P, P]
@@ -218,7 +225,8 @@ def reset_transform_count() -> None:
 def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None,
           finish_h: bool = False, want=("gN", "H", "phi", "acc", "dH")):
     """Field solve (App. Flow steps 3-9). rho: [n,n,n] float64 (z,y,x).
-    Returns a dict of the requested outputs (vector fields as [3,n,n,n])."""
+    Returns a dict of the requested outputs (vector fields as [3,n,n,n]);
+    "gM" (not in the default) is the curl-free g_M of the last iteration."""
     rho = _c(rho, np.float64)
     n = rho.shape[0]
     out = {}
@@ -227,15 +235,52 @@ def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None
     phi = np.zeros((n, n, n)) if "phi" in want else None
     acc = np.zeros((3, n, n, n)) if "acc" in want else None
     dH = np.zeros(max(n_iter, 1)) if "dH" in want else None
+    gM = np.zeros((3, n, n, n)) if ("gM" in want and n_iter > 0) else None
     H0a = None if H0 is None else _c(H0, np.float64)
     rc = lib().ora_solve(n, float(s), float(G), float(a0), int(mu_kind), int(n_iter), _p(rho), _p(H0a),
-                         int(bool(finish_h)), _p(gN), _p(H), _p(phi), _p(acc), _p(dH))
+                         int(bool(finish_h)), _p(gN), _p(H), _p(phi), _p(acc), _p(dH), _p(gM))
     if rc != 0:
         raise RuntimeError(f"oracle solve failed: {rc}")
-    for k, v in (("gN", gN), ("H", H), ("phi", phi), ("acc", acc), ("dH", dH)):
+    for k, v in (("gN", gN), ("H", H), ("phi", phi), ("acc", acc), ("dH", dH), ("gM", gM)):
         if v is not None:
             out[k] = v
     return out
+
+
+def solve_increment(drho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, gN0, H0, gM0):
+    """Incremental solve (Sect. 5.2 (v)): field increments for the density
+    increment drho [n,n,n] about the base (g_N0, H0, g_M0), each [3,n,n,n],
+    with the nu and mu steps linearised about F0 = g_N0 + H0 and g_M0.
+    Returns dict dgN, dH, dgM, dacc ([3,n,n,n] each)."""
+    drho = _c(drho, np.float64)
+    n = drho.shape[0]
+    gN0, H0, gM0 = (_c(a, np.float64) for a in (gN0, H0, gM0))
+    out = {k: np.zeros((3, n, n, n)) for k in ("dgN", "dH", "dgM", "dacc")}
+    rc = lib().ora_solve_increment(n, float(s), float(G), float(a0), int(mu_kind), int(n_iter), _p(drho),
+                                   _p(gN0), _p(H0), _p(gM0), _p(out["dgN"]), _p(out["dH"]), _p(out["dgM"]),
+                                   _p(out["dacc"]))
+    if rc != 0:
+        raise RuntimeError(f"oracle incremental solve failed: {rc}")
+    return out
+
+
+def linearised(kind: int, which: int, a0: float, P, dv):
+    """The linearised nu (which = 0) or mu (which = 1) step of Sect. 5.2 (v)
+    about the point P applied to dv (3-vectors)."""
+    P = _c(P, np.float64)
+    dv = _c(dv, np.float64)
+    out = np.zeros(3)
+    lib().ora_linearised(int(kind), int(which), float(a0), _p(P), _p(dv), _p(out))
+    return out
+
+
+def delta_rho(acc1, acc0, kacc_val: int, s: float):
+    """Density increment of two fixed-point deposits with the same Kacc
+    (rule R1): float(double(acc1 - acc0) * 2^-Kacc / s^3), the integer
+    difference taken first so that it is exact."""
+    d = np.asarray(acc1).astype(np.int64) - np.asarray(acc0).astype(np.int64)
+    sc = np.ldexp(1.0, -int(kacc_val)) / (s * s * s)
+    return (d.astype(np.float64) * sc).astype(np.float32)
 
 
 def project_div(field, s: float):

@@ -40,6 +40,10 @@
  *   ora_gather         node-smoothed field at nodes; constant field; two-body force
  *   ora_push           Eq. motion on hand-checked numbers
  *   ora_particle_diag  two-body constants of motion on hand-made states
+ *   ora_solve_increment  Newtonian kind: equals the difference of two full
+ *                      solves; linear in drho; central difference of the full
+ *                      iteration about a converged base (error O(eps^2));
+ *                      ora_linearised against central differences of nu/mu
  */
 #include <complex.h>
 #include <math.h>
@@ -463,12 +467,14 @@ static void fd_grad(int n, double s, const double* f, double* g /* 3 planes */) 
  * the mu, H and divergence-free steps, so that H is fresh for a warm start).
  * Outputs (any may be NULL): gN (3 n^3), H (3 n^3, the last H formed), phi
  * (n^3), acc = -grad_FD phi (3 n^3), dH (n_iter doubles: ||H_j - H_{j-1}||_2
- * over ||H_j||_2, NaN where no H was formed).
+ * over ||H_j||_2, NaN where no H was formed), gM (3 n^3: the curl-free g_M of
+ * the last iteration, the point the mu step of an incremental solve is
+ * linearised about).
  * For K = 0 the potential is phi_N and acc = g_N.
  */
 int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, const double* rho,
               const double* H0, int finish_h, double* gN_out, double* H_out, double* phi_out,
-              double* acc_out, double* dH_out) {
+              double* acc_out, double* dH_out, double* gM_out) {
   int64_t tot = (int64_t)n * n * n;
   cplx* c1 = (cplx*)malloc(sizeof(cplx) * tot);       /* scalar spectrum */
   cplx* cv = (cplx*)malloc(sizeof(cplx) * 3 * tot);   /* vector spectrum */
@@ -543,10 +549,13 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
         }
     if (it == n_iter && !finish_h) {
       if (dH_out) dH_out[it - 1] = NAN;
+      if (gM_out)
+        for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, gM_out + a * tot);
       break;
     }
     /* g_M = F^-1(g_M^) */
     for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, V + a * tot);
+    if (it == n_iter && gM_out) memcpy(gM_out, V, sizeof(double) * 3 * tot);
     /* F = mu(|g_M|/a0) g_M (Eq. interpolation); H = F - g_N (Eq. helmholtz) */
     memcpy(Hprev, H, sizeof(double) * 3 * tot);
     for (int64_t j = 0; j < tot; j++) {
@@ -593,6 +602,163 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
   if (H_out) memcpy(H_out, H, sizeof(double) * 3 * tot);
   if (phi_out) memcpy(phi_out, phi, sizeof(double) * tot);
   free(c1); free(cv); free(gN); free(H); free(Hprev); free(V); free(phi); free(phih);
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Incremental solve: the linearised nu and mu steps of Sect. 5.2 (v)        */
+/* ------------------------------------------------------------------------ */
+
+/* y nu'(y) and x mu'(x) for each kind (derivatives of the functions above):
+ * deep      y nu' = -1/(2 sqrt y)                 x mu' = x
+ * simple    y nu' = -1/(2 y sqrt(1/4 + 1/y))      x mu' = x/(1+x)^2
+ * standard  y nu' = -1/(nu(y) y sqrt(y^2 + 4))    x mu' = x/(1+x^2)^(3/2)
+ * Newton    0                                     0 */
+double ora_ynu_prime(int kind, double y) {
+  switch (kind) {
+    case ORA_MU_DEEP: return -0.5 / sqrt(y);
+    case ORA_MU_SIMPLE: return -1.0 / (2.0 * y * sqrt(0.25 + 1.0 / y));
+    case ORA_MU_STANDARD: return -1.0 / (ora_nu(kind, y) * y * sqrt(y * y + 4.0));
+    default: return 0.0;
+  }
+}
+double ora_xmu_prime(int kind, double x) {
+  switch (kind) {
+    case ORA_MU_DEEP: return x;
+    case ORA_MU_SIMPLE: return x / ((1.0 + x) * (1.0 + x));
+    case ORA_MU_STANDARD: return x / pow(1.0 + x * x, 1.5);
+    default: return 0.0;
+  }
+}
+
+/* Linearisation of v -> f(|v|/a0) v about the point P, applied to dv:
+ * f(p) dv + f'(p) (P.dv)/(a0 |P|) P = f(p) dv + p f'(p) (u.dv) u, with
+ * p = |P|/a0 and u = P/|P| (Sect. 5.2 (v)). The identity for the Newtonian
+ * kind; 0 where P = 0 otherwise (the zero-field reading of the nu step).
+ * which = 0: f = nu; 1: f = mu. */
+void ora_linearised(int kind, int which, double a0, const double* P, const double* dv, double* out) {
+  double m = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+  if (kind == ORA_MU_NEWTON || !(m > 0)) {
+    for (int a = 0; a < 3; a++) out[a] = kind == ORA_MU_NEWTON ? dv[a] : 0.0;
+    return;
+  }
+  double p = m / a0;
+  double f = which == 0 ? ora_nu(kind, p) : ora_mu(kind, p);
+  double fp = which == 0 ? ora_ynu_prime(kind, p) : ora_xmu_prime(kind, p);
+  double ud = (P[0] * dv[0] + P[1] * dv[1] + P[2] * dv[2]) / m;
+  for (int a = 0; a < 3; a++) out[a] = f * dv[a] + fp * ud * P[a] / m;
+}
+
+/*
+ * Incremental field solve (Sect. 5.2 (v)): the increments of the fields for a
+ * density increment drho about a base state (g_N0, H0, g_M0), with the nu and
+ * mu steps linearised about F0 = g_N0 + H0 and g_M0:
+ *   dg_N = Newton(drho)                       (App. Flow steps 3-6)
+ *   dH = 0; for j = 1..K:
+ *     dF   = dg_N + dH
+ *     dg_M = Jnu(F0) dF,  curl-free part      (Eq. inverse linearised, Eq. rotg)
+ *     dF   = Jmu(g_M0) dg_M                   (Eq. interpolation linearised)
+ *     dH   = div-free part of dF - dg_N       (Eq. helmholtz, Eq. divH)
+ *   dphi^ = i A k.dg_M^ of the last iteration; dacc = -grad_FD dphi
+ * The last iteration always finishes dH, so that the base can be moved on:
+ * g_N1 = g_N0 + dg_N, H1 = H0 + dH, g_M1 = g_M0 + dg_M, acc1 = acc0 + dacc.
+ * Outputs (any may be NULL): dgN, dH, dgM (the last curl-free dg_M), dacc,
+ * all 3 n^3. n_iter >= 1.
+ */
+int ora_solve_increment(int n, double s, double G, double a0, int mu_kind, int n_iter, const double* drho,
+                        const double* gN0, const double* H0, const double* gM0, double* dgN_out,
+                        double* dH_out, double* dgM_out, double* dacc_out) {
+  if (n_iter < 1) return ORA_EINVAL;
+  int64_t tot = (int64_t)n * n * n;
+  cplx* c1 = (cplx*)malloc(sizeof(cplx) * tot);
+  cplx* cv = (cplx*)malloc(sizeof(cplx) * 3 * tot);
+  double* dgN = (double*)malloc(sizeof(double) * 3 * tot);
+  double* dH = (double*)calloc(3 * tot, sizeof(double));
+  double* V = (double*)malloc(sizeof(double) * 3 * tot);
+  double* phi = (double*)malloc(sizeof(double) * tot);
+  cplx* phih = (cplx*)malloc(sizeof(cplx) * tot);
+  if (!c1 || !cv || !dgN || !dH || !V || !phi || !phih) return ORA_ENOMEM;
+
+  /* dg_N = -grad_FD F^-1(-4 pi G A F(drho)) */
+  for (int64_t j = 0; j < tot; j++) c1[j] = drho[j];
+  fwd3(n, s, c1);
+  for (int l = 0; l < n; l++)
+    for (int jy = 0; jy < n; jy++)
+      for (int i = 0; i < n; i++) {
+        double k[3];
+        kvec(n, s, i, jy, l, k);
+        int64_t j = idx3(n, i, jy, l);
+        c1[j] = -4.0 * M_PI * G * invlap(k) * c1[j];
+      }
+  inv3_real(n, s, c1, phi);
+  fd_grad(n, s, phi, dgN);
+  for (int64_t j = 0; j < 3 * tot; j++) dgN[j] = -dgN[j];
+
+  for (int it = 1; it <= n_iter; it++) {
+    /* dg_M = Jnu(F0) (dg_N + dH) */
+    for (int64_t j = 0; j < tot; j++) {
+      double F0[3], dF[3], o[3];
+      for (int a = 0; a < 3; a++) {
+        F0[a] = gN0[a * tot + j] + H0[a * tot + j];
+        dF[a] = dgN[a * tot + j] + dH[a * tot + j];
+      }
+      ora_linearised(mu_kind, 0, a0, F0, dF, o);
+      for (int a = 0; a < 3; a++) V[a * tot + j] = o[a];
+    }
+    /* curl-free part; the potential increment of this iteration */
+    for (int a = 0; a < 3; a++) {
+      for (int64_t j = 0; j < tot; j++) cv[a * tot + j] = V[a * tot + j];
+      fwd3(n, s, cv + a * tot);
+    }
+    for (int l = 0; l < n; l++)
+      for (int jy = 0; jy < n; jy++)
+        for (int i = 0; i < n; i++) {
+          double k[3];
+          kvec(n, s, i, jy, l, k);
+          int64_t j = idx3(n, i, jy, l);
+          double A = invlap(k);
+          cplx kg = k[0] * cv[j] + k[1] * cv[tot + j] + k[2] * cv[2 * tot + j];
+          cplx ph = I * A * kg;
+          phih[j] = ph;
+          for (int a = 0; a < 3; a++) cv[a * tot + j] = -I * k[a] * ph;
+        }
+    for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, V + a * tot);
+    if (it == n_iter && dgM_out) memcpy(dgM_out, V, sizeof(double) * 3 * tot);
+    /* dH = div-free part of Jmu(g_M0) dg_M - dg_N */
+    for (int64_t j = 0; j < tot; j++) {
+      double P[3], dv[3], o[3];
+      for (int a = 0; a < 3; a++) {
+        P[a] = gM0[a * tot + j];
+        dv[a] = V[a * tot + j];
+      }
+      ora_linearised(mu_kind, 1, a0, P, dv, o);
+      for (int a = 0; a < 3; a++) dH[a * tot + j] = o[a] - dgN[a * tot + j];
+    }
+    for (int a = 0; a < 3; a++) {
+      for (int64_t j = 0; j < tot; j++) cv[a * tot + j] = dH[a * tot + j];
+      fwd3(n, s, cv + a * tot);
+    }
+    for (int l = 0; l < n; l++)
+      for (int jy = 0; jy < n; jy++)
+        for (int i = 0; i < n; i++) {
+          double k[3];
+          kvec(n, s, i, jy, l, k);
+          int64_t j = idx3(n, i, jy, l);
+          double A = invlap(k);
+          cplx kh = k[0] * cv[j] + k[1] * cv[tot + j] + k[2] * cv[2 * tot + j];
+          for (int a = 0; a < 3; a++) cv[a * tot + j] -= k[a] * A * kh;
+        }
+    for (int a = 0; a < 3; a++) inv3_real(n, s, cv + a * tot, dH + a * tot);
+  }
+  /* dacc = -grad_FD F^-1(dphi^) */
+  inv3_real(n, s, phih, phi);
+  if (dacc_out) {
+    fd_grad(n, s, phi, dacc_out);
+    for (int64_t j = 0; j < 3 * tot; j++) dacc_out[j] = -dacc_out[j];
+  }
+  if (dgN_out) memcpy(dgN_out, dgN, sizeof(double) * 3 * tot);
+  if (dH_out) memcpy(dH_out, dH, sizeof(double) * 3 * tot);
+  free(c1); free(cv); free(dgN); free(dH); free(V); free(phi); free(phih);
   return ORA_OK;
 }
 
