@@ -14,7 +14,7 @@ buffers; ``warm`` is the warm-started variant (previous H, one iteration);
 measured peak and ``particle_kernels`` the deposit's and gather's tap rates;
 ``cpu_baseline`` times the CPU oracle on a bounded sample. Side sections:
 ``density`` (Eq. apparentdensity kernels), ``interp_gather`` (the
-mesh-interpolating gather), ``learned`` (training and evaluating the learned
+mesh-interpolating gather), ``increment`` (the incremental solve), ``learned`` (training and evaluating the learned
 warm start), ``ensemble`` (64 systems as one graph per step) and, with
 ``--scan``, step times against the particle count.
 ``--impl reference`` times the CPU oracle alone (the reference arm).
@@ -301,6 +301,45 @@ def _run_interp(h, B, stream, t, init, steps, warmup, K, dt, res, torch):
     h.sync()
     res["note"] = "same workload and K; node-smoothed mesh made by the final pass, interpolated at the particles"
     return res
+
+
+def run_increment(h, B, stream, t, init, steps, warmup):
+    """The incremental solve (Sect. 5.2 item v, MOND_WARM_INCREMENT): after one
+    full K-iteration step, graph-replayed steps whose solve is one iteration of
+    the linearised steps on the deposit's change; steps per second, and the
+    force error of the last incremental solve against the converged field of
+    the same density (as the plain and warm errors)."""
+    import torch
+
+    K, dt = WL["K"], WL["dt"]
+    try:
+        h.enable_increment(True)
+        for k in t:
+            t[k].copy_(init[k])
+        h.step(dt, K, B.WARM_NONE)  # the base
+        for _ in range(warmup):
+            h.step(dt, 1, B.WARM_INCREMENT)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            h.step(dt, 1, B.WARM_INCREMENT)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        h.deposit()
+        h.solve_field(1, B.WARM_INCREMENT)
+        g_inc = h.gather().double()
+        h.solve_field(REF_ITERS, B.WARM_NONE)
+        g_a = h.gather().double()
+        h.solve_field(REF_ITERS + 1, B.WARM_NONE)
+        g_ref = 0.5 * (g_a + h.gather().double())
+        err = float(torch.linalg.norm(g_inc - g_ref) / torch.linalg.norm(g_ref))
+        h.sync()
+        return {"mode": "incremental, 1 iteration", "steps_per_s": 1000.0 / ms, "ms_per_step": ms,
+                "force_rel_err": err, "incremental_steps_since_full_solve": warmup + steps + 1}
+    finally:
+        h.enable_increment(False)
 
 
 def run_scan(dev, steps):
@@ -662,6 +701,10 @@ def main():
     if rank == 0:
         interp_info = optional(run_interp, h, B, stream, t, init, args.steps, args.warmup)
 
+    inc_info = None
+    if rank == 0:
+        inc_info = optional(run_increment, h, B, stream, t, init, args.steps, args.warmup)
+
     # ---- end to end through host buffers -------------------------------------
     cell_h = init["cell"].cpu().pin_memory()
     off_h = init["offset"].cpu().pin_memory()
@@ -738,7 +781,7 @@ def main():
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "particle_kernels": part,
                 "kernels": kern,
                 "ms_per_step_event_timed": ms_timed_mode / args.steps,
-                "density": dens_info, "interp_gather": interp_info, "learned": learned, "ensemble": ensemble}
+                "density": dens_info, "interp_gather": interp_info, "increment": inc_info, "learned": learned, "ensemble": ensemble}
         if scan is not None:
             line["scan"] = scan
         if cpu:

@@ -53,8 +53,13 @@ enum { MOND_MU_DEEP = 0, MOND_MU_SIMPLE = 1, MOND_MU_STANDARD = 2, MOND_MU_NEWTO
 
 /* Initial H of the iteration: zero (App. Flow step 7), the H of the previous
  * solve (Sect. 5.2 item iv), a caller-supplied guess projected onto its
- * divergence-free part, or a caller-supplied guess used as given. */
-enum { MOND_WARM_NONE = 0, MOND_WARM_PREV = 1, MOND_WARM_GUESS = 2, MOND_WARM_GUESS_RAW = 3 };
+ * divergence-free part, or a caller-supplied guess used as given.
+ * MOND_WARM_INCREMENT is the incremental solve of Sect. 5.2 item v: the
+ * fields' increments for the change of the deposit since the base state, with
+ * the nu and mu steps linearised about that state (see
+ * mond_pm_set_increment_workspace). */
+enum { MOND_WARM_NONE = 0, MOND_WARM_PREV = 1, MOND_WARM_GUESS = 2, MOND_WARM_GUESS_RAW = 3,
+       MOND_WARM_INCREMENT = 4 };
 
 /* Mesh fields readable with mond_pm_get_field. */
 enum {
@@ -64,7 +69,9 @@ enum {
   MOND_FIELD_PHI = 3,    /* MOND potential phi of the last solve, 1 plane (needs MOND_OPT_KEEP_PHI) */
   MOND_FIELD_ACC = 4,    /* acceleration mesh a = -grad_FD phi of the last solve, 3 planes (node-smoothed
                             when the solve ran with MOND_OPT_GATHER 1 or 3) */
-  MOND_FIELD_SMOOTH = 5  /* node-smoothed acceleration of the last mond_pm_smooth, 3 planes */
+  MOND_FIELD_SMOOTH = 5, /* node-smoothed acceleration of the last mond_pm_smooth, 3 planes */
+  MOND_FIELD_GM = 6      /* base g_M of an incremental solve: the curl-free g_M of the last iteration of the
+                            last solve, 3 planes (needs the increment workspace; MOND_ESTATE otherwise) */
 };
 
 /* Error codes. */
@@ -181,8 +188,36 @@ int mond_pm_set_density(mond_pm_t h, const float* rho);
  * solve can start from it. The Newtonian field is computed once
  * per density: a solve on the density of the previous solve (no deposit or
  * mond_pm_set_density in between) starts from the stored g_N.
+ * MOND_WARM_INCREMENT (n_iter >= 1) runs the incremental solve (Sect. 5.2
+ * item v) on the deposit's change since the base: the density increment is the
+ * difference of the two int64 accumulators (exact), converted by the density
+ * rule; dg_N is its Newtonian field; then n_iter iterations of
+ * dF = dg_N + dH, dg_M = curl-free part of Jnu(F0) dF,
+ * dH = divergence-free part of Jmu(g_M0) dg_M - dg_N, with
+ * J f(P) d = f(p) d + p f'(p) (u.d) u (p = |P|/a0, u = P/|P|; the identity for
+ * the Newtonian kind, 0 where P = 0), F0 = g_N + H and g_M0 of the base. The
+ * last iteration adds the increments of the acceleration mesh (and phi), g_N,
+ * g_M and H to the base, which becomes this solve's state.
+ * MOND_ESTATE when no base is valid (see mond_pm_set_increment_workspace).
  * 0 <= n_iter <= 64. */
 int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess);
+
+/* Workspace of the incremental solve (Sect. 5.2 item v): the base deposit
+ * (int64, n_f^3), the base g_M and the increment's g_N (float32, 3 planes
+ * each). mond_pm_increment_workspace_bytes gives its size for a grid
+ * (MOND_EINVAL for a bad grid). mond_pm_set_increment_workspace attaches ws
+ * (device memory, 256-byte aligned, caller-owned, unused by the handle once
+ * detached; NULL detaches); errors: MOND_EINVAL (misaligned), MOND_ENOMEM
+ * (too small). While one is attached, every solve with n_iter >= 1 (other than
+ * MOND_WARM_GUESS_RAW, and not on a density set with mond_pm_set_density) also
+ * completes the H update, stores the curl-free g_M of its last iteration and
+ * copies the deposit: the base of the next MOND_WARM_INCREMENT solve. The base
+ * is dropped by mond_pm_set_density, mond_pm_set_h_state,
+ * mond_pm_set_dipole_layer, a Newtonian or MOND_WARM_GUESS_RAW solve, and
+ * attaching; an incremental solve needs the Kacc, MOND_OPT_GATHER and
+ * MOND_OPT_KEEP_PHI of its base. */
+int mond_pm_increment_workspace_bytes(mond_pm_grid grid, size_t* bytes);
+int mond_pm_set_increment_workspace(mond_pm_t h, void* ws, size_t bytes);
 
 /* Node-smoothed acceleration: the periodic discrete convolution of the
  * acceleration mesh with the ball-truncated Gaussian of Eq. gi, i.e. the force
@@ -256,7 +291,7 @@ int mond_pm_half_kick(mond_pm_t h, double dt);
 int mond_pm_gather(mond_pm_t h, float* g_out);
 
 /* One time step: deposit, solve_field(n_iter, warm, NULL), gather_push(dt).
- * warm: MOND_WARM_NONE or MOND_WARM_PREV. */
+ * warm: MOND_WARM_NONE, MOND_WARM_PREV or MOND_WARM_INCREMENT. */
 int mond_pm_step(mond_pm_t h, double dt, int n_iter, int warm);
 
 /* ---- batches of independent systems -------------------------------------
@@ -278,7 +313,7 @@ typedef struct mond_pm_batch* mond_pm_batch_t;
 int mond_pm_batch_create(int n, const mond_pm_t* handles, void* stream, mond_pm_batch_t* out);
 
 /* Enqueue n_steps graph launches of one step (deposit, solve_field(n_iter,
- * warm NONE or PREV), gather_push(dt)) of every member on the batch stream.
+ * warm NONE, PREV or INCREMENT), gather_push(dt)) of every member on the batch stream.
  * Does not synchronise. */
 int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, int warm);
 

@@ -40,6 +40,15 @@ What pins each function (tests in ``tests/test_oracle_*.py``):
   interp_gather   reproduces linear (order 1) and quadratic (order 3)
                   fields exactly; node values at zero offset; convergence
                   orders 2 and 3 against Eq. gi on smooth fields.
+  linearised      central differences of v -> nu(|v|/a0) v and
+                  v -> mu(|v|/a0) v for every kind; y nu'(y), x mu'(x)
+                  against central differences of nu and mu.
+  solve_increment Newtonian kind: equals the difference of two full solves;
+                  linear in the density increment; about a converged base,
+                  the central difference of the full iteration with error
+                  falling fourfold as the step halves (Sect. 5.2 (v)).
+  delta_rho       the integer difference of two deposits is the deposit of
+                  the moved particles' new minus old positions, exactly.
 """
 from __future__ import annotations
 

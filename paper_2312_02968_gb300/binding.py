@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmondpm.so")
 
 MU_DEEP, MU_SIMPLE, MU_STANDARD, MU_NEWTON = 0, 1, 2, 3
-WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW = 0, 1, 2, 3
-FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH = 0, 1, 2, 3, 4, 5
+WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW, WARM_INCREMENT = 0, 1, 2, 3, 4
+FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH, FIELD_GM = 0, 1, 2, 3, 4, 5, 6
 DENS_BARYONIC, DENS_APPARENT, DENS_PHANTOM = 0, 1, 2
 OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK, OPT_GATHER = 1, 2, 3, 4, 5, 6, 7
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
@@ -58,6 +58,8 @@ SIGNATURES = {
     "mond_pm_density": (_I, [_P, _I, _P]),
     "mond_pm_set_dipole_layer": (_I, [_P, _I, _D]),
     "mond_pm_set_h_state": (_I, [_P, _P]),
+    "mond_pm_increment_workspace_bytes": (_I, [Grid, ctypes.POINTER(ctypes.c_size_t)]),
+    "mond_pm_set_increment_workspace": (_I, [_P, _P, ctypes.c_size_t]),
     "mond_pm_shell_mass": (_I, [_P, _I, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_D)]),
     "mond_pm_box_mass": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(_D)]),
@@ -248,6 +250,21 @@ class MondPM:
         self._check(lib().mond_pm_step_host(self.h, float(dt), int(n_iter), int(warm), _ptr(cell_host),
                                             _ptr(offset_host), _ptr(vel_host)))
 
+    def enable_increment(self, on: bool = True):
+        """Attach (or detach) the workspace of the incremental solve
+        (WARM_INCREMENT, Sect. 5.2 item v); later solves keep its base state."""
+        lib().mond_pm_sync(self.h)  # nothing in flight may still use a released workspace
+        if not on:
+            self._check(lib().mond_pm_set_increment_workspace(self.h, None, 0))
+            self.inc_workspace = None
+            return
+        n = ctypes.c_size_t()
+        self._check(lib().mond_pm_increment_workspace_bytes(Grid(self.n, self.pad), ctypes.byref(n)))
+        ws = self.torch.empty(n.value + 256, dtype=self.torch.uint8, device=self.device)
+        aligned = (ws.data_ptr() + 255) & ~255
+        self._check(lib().mond_pm_set_increment_workspace(self.h, ctypes.c_void_p(aligned), n.value))
+        self.inc_workspace = ws
+
     def set_h_state(self, H):
         """Replace the warm-start H state by H (device float32 [3, n, n, n])."""
         if H.dtype != self.torch.float32 or not H.is_contiguous() or H.numel() != 3 * self.nf ** 3:
@@ -315,7 +332,7 @@ class MondPM:
 
     def get_field(self, which: int, out=None):
         torch = self.torch
-        planes = 3 if which in (FIELD_GN, FIELD_H, FIELD_ACC, FIELD_SMOOTH) else 1
+        planes = 3 if which in (FIELD_GN, FIELD_H, FIELD_ACC, FIELD_SMOOTH, FIELD_GM) else 1
         shape = (planes, self.nf, self.nf, self.nf) if planes == 3 else (self.nf, self.nf, self.nf)
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device=self.device)

@@ -249,12 +249,15 @@ __global__ void k_dep_sum(int64_t n3, const uint64_t* dep, unsigned long long* o
 
 void mond_pm_set_create_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
+// x-pass classes follow passes::XMode (KC_X_RHO + mode)
 enum KClass {
-  KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_X_NU_REAL, KC_Y_FWD, KC_Y_INV,
-  KC_Z_NEWTON, KC_Z_CURL, KC_Z_DIV, KC_Z_FINAL, KC_Z_SMOOTH, KC_BIN, KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_COUNT
+  KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_X_NU_REAL, KC_X_DRHO, KC_X_DNU_FIRST,
+  KC_X_DNU, KC_X_DMU, KC_Y_FWD, KC_Y_INV, KC_Z_NEWTON, KC_Z_CURL, KC_Z_DIV, KC_Z_FINAL, KC_Z_SMOOTH, KC_BIN,
+  KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_COUNT
 };
 const char* const kKName[KC_COUNT] = {"xpass_rho", "xpass_nu_first", "xpass_nu", "xpass_mu", "xpass_inv",
-                                      "xpass_fwd", "xpass_nu_real", "ypass_fwd", "ypass_inv", "zpass_newton",
+                                      "xpass_fwd", "xpass_nu_real", "xpass_drho", "xpass_dnu_first",
+                                      "xpass_dnu", "xpass_dmu", "ypass_fwd", "ypass_inv", "zpass_newton",
                                       "zpass_curl",
                                       "zpass_div", "zpass_final", "zpass_smooth", "bin", "deposit",
                                       "gather_push", "other"};
@@ -290,6 +293,15 @@ struct mond_pm {
   int ext_axis = -1;          // external-field dipole layer (mond_pm_set_dipole_layer), -1 none
   double ext_mass = 0.0;
   bool acc_smoothed = false;  // w.acc holds the node-smoothed field (final pass with the smoothing spectrum)
+  // incremental solve (mond_pm_set_increment_workspace): the base deposit, the
+  // base g_M and the increment's Newton field, in a caller-owned buffer
+  struct IncWs {
+    uint64_t* dep0 = nullptr;
+    float* gM0 = nullptr;
+    float* dgN = nullptr;
+  } inc;
+  bool inc_valid = false;  // the base (dep0, gN, Hs, gM0, acc) is that of the last solve
+  int inc_kacc = 0, inc_gather = 0, inc_keep_phi = 0;
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
@@ -301,11 +313,12 @@ struct mond_pm {
     double ext_mass;
     int64_t N;
     const void* cell;
+    const void* inc;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
              track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
              gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
-             cell == o.cell;
+             cell == o.cell && inc == o.inc;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -404,10 +417,14 @@ cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
     case passes::X_RHO: bytes = 2 * R + (a.rho_out ? R : 0) + S; break;  // int64 in, [FP32 density out,] spectrum out
     case passes::X_NU_FIRST: bytes = 6 * S + 3 * R + (a.H0 ? 3 * R : 0); break;
     case passes::X_NU: bytes = 6 * S + 3 * R + (a.Hs_out ? 3 * R * (a.red ? 2 : 1) : 0); break;
-    case passes::X_MU: bytes = 6 * S + 3 * R; break;
-    case passes::X_INV: bytes = a.ncomp * (S + R * (a.real_out2 ? 2 : 1)); break;
+    case passes::X_MU: bytes = 6 * S + 3 * R + (a.gM_out ? 3 * R : 0); break;
+    case passes::X_INV: bytes = a.ncomp * (S + R * ((a.real_out2 ? 2 : 1) + (a.accumulate ? 1 : 0))); break;
     case passes::X_FWD: bytes = a.ncomp * (S + R); break;
     case passes::X_NU_REAL: bytes = 3 * S + 3 * R + (a.H0 ? 3 * R : 0); break;
+    case passes::X_DRHO: bytes = 6 * R + S; break;  // two int64 deposits in, the base out, spectrum out
+    case passes::X_DNU_FIRST: bytes = 6 * S + 9 * R; break;  // dg_N out, g_N and H0 in
+    case passes::X_DNU: bytes = 6 * S + 9 * R; break;        // dg_N, g_N and H0 in
+    case passes::X_DMU: bytes = 6 * S + 6 * R + (a.base_update ? 9 * R : 0); break;
   }
   Timed tm(h, KC_X_RHO + mode, bytes);
   switch (h->nf) {
@@ -719,6 +736,10 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   const int nout = h->keep_phi ? 4 : 3;
   float2* W = h->w.W;
   float2* A = h->w.A;
+  // with an increment workspace, a solve also leaves the base of the next
+  // incremental solve: the finished H, the curl-free g_M it came from, the deposit
+  const bool base = h->inc.dep0 && K >= 1 && !h->density_given && warm != MOND_WARM_GUESS_RAW;
+  h->inc_valid = false;
   // the Newton field is reused when the density has not changed since the last solve
   const bool reuse = h->gn_valid && K > 0;
   if (!reuse) {
@@ -815,7 +836,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       xi.real_out = h->w.acc;
       PK(xpass(h, passes::X_INV, xi));
       h->acc_smoothed = h->gather_mode != 0;
-      if (warm == MOND_WARM_NONE || warm == MOND_WARM_GUESS_RAW) break;  // no H state to carry on
+      if ((warm == MOND_WARM_NONE || warm == MOND_WARM_GUESS_RAW) && !base) break;  // no H state to carry on
     }
     PK(zpass(h, passes::Z_CURL, W, W, 3));
     PK(ypass(h, +1, W, 3));
@@ -823,6 +844,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     xm.ncomp = 3;
     xm.spec = W;
     xm.gN = h->w.gN;
+    xm.gM_out = (last && base) ? h->inc.gM0 : nullptr;
     PK(xpass(h, passes::X_MU, xm));
     PK(ypass(h, -1, W, 3));
     PK(zpass(h, passes::Z_DIV, W, W, 3));
@@ -845,6 +867,107 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     xv.red = h->track_dh ? h->w.red + 32 + 2 * (j - 1) : nullptr;
     PK(xpass(h, passes::X_NU, xv));
   }
+  if (base) {
+    CK(cudaMemcpyAsync(h->inc.dep0, h->w.dep, sizeof(uint64_t) * h->n3, cudaMemcpyDeviceToDevice, h->st));
+    h->inc_valid = true;
+    h->inc_kacc = h->kacc;
+    h->inc_gather = h->gather_mode;
+    h->inc_keep_phi = h->keep_phi;
+  }
+  h->last_iters = K;
+  h->have_solve = true;
+  h->have_fields = true;
+  return MOND_OK;
+}
+
+// Why an incremental solve cannot run now (nullptr: it can).
+const char* inc_unready(const mond_pm* h) {
+  if (!h->inc.dep0) return "no increment workspace attached";
+  if (!h->inc_valid) return "no base state: run a full solve (n_iter >= 1) with the increment workspace attached";
+  if (h->density_given) return "the density was set directly; increments need deposits";
+  if (h->kacc != h->inc_kacc) return "the fixed-point scale changed since the base deposit (particle masses)";
+  if (h->gather_mode != h->inc_gather) return "MOND_OPT_GATHER changed since the base solve";
+  if (h->keep_phi != h->inc_keep_phi) return "MOND_OPT_KEEP_PHI changed since the base solve";
+  return nullptr;
+}
+
+// Incremental solve (Sect. 5.2 v): the density increment of the new deposit
+// against the base deposit, its Newton field dg_N, then K iterations of the
+// linearised steps about the base (F0 = g_N + H, g_M0) on the increments; the
+// last iteration adds the increments of the acceleration mesh (and phi), g_N,
+// g_M and H to the base, which becomes the state of this solve.
+int do_solve_increment(mond_pm* h, int K) {
+  const int nout = h->keep_phi ? 4 : 3;
+  float2* W = h->w.W;
+  float2* A = h->w.A;
+  passes::XArgs x{};
+  x.ncomp = 1;
+  x.spec = W;
+  x.dep = h->w.dep;
+  x.dep0 = h->inc.dep0;
+  x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
+  PK(xpass(h, passes::X_DRHO, x));
+  PK(ypass(h, -1, W, 1));
+  PK(zpass(h, passes::Z_NEWTON, W, W, 3));
+  PK(ypass(h, +1, W, 3));
+  passes::XArgs xn{};
+  xn.ncomp = 3;
+  xn.spec = W;
+  xn.gN_out = h->inc.dgN;
+  xn.gN = h->w.gN;
+  xn.H0 = h->w.Hs;
+  PK(xpass(h, passes::X_DNU_FIRST, xn));
+  h->inc_valid = false;  // until the base has moved on
+  for (int j = 1; j <= K; j++) {
+    PK(ypass(h, -1, W, 3));
+    const bool last = (j == K);
+    if (last) {
+      if (h->gather_mode) {
+        int rk = ensure_khat(h);
+        if (rk) return rk;
+      }
+      PK(zpass(h, passes::Z_FINAL, W, A, nout));
+      PK(ypass(h, +1, A, nout));
+      passes::XArgs xi{};
+      xi.ncomp = nout;
+      xi.spec = A;
+      xi.real_out = h->w.acc;
+      xi.accumulate = 1;
+      PK(xpass(h, passes::X_INV, xi));
+    }
+    PK(zpass(h, passes::Z_CURL, W, W, 3));
+    PK(ypass(h, +1, W, 3));
+    passes::XArgs xm{};
+    xm.ncomp = 3;
+    xm.spec = W;
+    xm.dgN = h->inc.dgN;
+    xm.gM0 = h->inc.gM0;
+    xm.base_update = last ? 1 : 0;
+    xm.gN_upd = h->w.gN;
+    PK(xpass(h, passes::X_DMU, xm));
+    PK(ypass(h, -1, W, 3));
+    PK(zpass(h, passes::Z_DIV, W, W, 3));
+    PK(ypass(h, +1, W, 3));
+    if (last) {
+      passes::XArgs xi{};
+      xi.ncomp = 3;
+      xi.spec = W;
+      xi.real_out = h->w.Hs;
+      xi.accumulate = 1;
+      PK(xpass(h, passes::X_INV, xi));
+      break;
+    }
+    passes::XArgs xv{};
+    xv.ncomp = 3;
+    xv.spec = W;
+    xv.dgN = h->inc.dgN;
+    xv.gN = h->w.gN;
+    xv.H0 = h->w.Hs;
+    PK(xpass(h, passes::X_DNU, xv));
+  }
+  h->inc_valid = true;
+  h->acc_smoothed = h->gather_mode != 0;
+  h->gn_valid = true;
   h->last_iters = K;
   h->have_solve = true;
   h->have_fields = true;
@@ -1113,6 +1236,33 @@ int mond_pm_set_h_state(mond_pm_t h, const float* H) {
   if (!h) return MOND_EINVAL;
   if (!H) return fail(h, MOND_EINVAL, "set_h_state: null H");
   CK(cudaMemcpyAsync(h->w.Hs, H, sizeof(float) * 3 * h->n3, cudaMemcpyDeviceToDevice, h->st));
+  h->inc_valid = false;  // H is part of the base of an incremental solve
+  return MOND_OK;
+}
+
+int mond_pm_increment_workspace_bytes(mond_pm_grid grid, size_t* bytes) {
+  if (!bytes) return MOND_EINVAL;
+  const int nf = grid.n * (grid.pad == 2 ? 2 : 1);
+  if (grid.n <= 0 || (grid.pad != 1 && grid.pad != 2) || !size_supported(nf)) return MOND_EINVAL;
+  const size_t n3 = (size_t)nf * nf * nf;
+  *bytes = sizeof(uint64_t) * n3 + 2 * sizeof(float) * 3 * n3 + 3 * 256;
+  return MOND_OK;
+}
+
+int mond_pm_set_increment_workspace(mond_pm_t h, void* ws, size_t bytes) {
+  if (!h) return MOND_EINVAL;
+  h->inc = mond_pm::IncWs{};
+  h->inc_valid = false;
+  if (!ws) return MOND_OK;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(h, MOND_EINVAL, "increment workspace must be 256-byte aligned");
+  const size_t n3 = (size_t)h->n3;
+  const size_t b0 = (sizeof(uint64_t) * n3 + 255) / 256 * 256;
+  const size_t b1 = (sizeof(float) * 3 * n3 + 255) / 256 * 256;
+  if (bytes < b0 + 2 * b1) return fail(h, MOND_ENOMEM, "increment workspace: %zu bytes, need %zu", bytes, b0 + 2 * b1);
+  char* p = static_cast<char*>(ws);
+  h->inc.dep0 = reinterpret_cast<uint64_t*>(p);
+  h->inc.gM0 = reinterpret_cast<float*>(p + b0);
+  h->inc.dgN = reinterpret_cast<float*>(p + b0 + b1);
   return MOND_OK;
 }
 
@@ -1121,7 +1271,8 @@ int mond_pm_set_dipole_layer(mond_pm_t h, int axis, double mass) {
   if (axis < -1 || axis > 2 || !std::isfinite(mass)) return fail(h, MOND_EINVAL, "dipole layer: axis -1..2, finite mass");
   h->ext_axis = axis;
   h->ext_mass = axis >= 0 ? mass : 0.0;
-  h->gn_valid = false;  // the solved density changes
+  h->gn_valid = false;   // the solved density changes
+  h->inc_valid = false;  // and with it the base of an incremental solve
   return MOND_OK;
 }
 
@@ -1130,6 +1281,7 @@ int mond_pm_set_density(mond_pm_t h, const float* rho) {
   CK(cudaMemcpyAsync(h->w.rho, rho, sizeof(float) * h->n3, cudaMemcpyDeviceToDevice, h->st));
   h->density_given = true;
   h->gn_valid = false;
+  h->inc_valid = false;
   h->have_dep = true;
   h->have_solve = false;
   return MOND_OK;
@@ -1140,10 +1292,14 @@ int mond_pm_solve_field(mond_pm_t h, int n_iter, int warm, const float* H_guess)
   if (!h) return MOND_EINVAL;
   if (!h->have_dep) return fail(h, MOND_ESTATE, "solve_field before deposit");
   if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
-  if (warm < 0 || warm > 3) return fail(h, MOND_EINVAL, "bad warm mode %d", warm);
+  if (warm < 0 || warm > 4) return fail(h, MOND_EINVAL, "bad warm mode %d", warm);
   if ((warm == MOND_WARM_GUESS || warm == MOND_WARM_GUESS_RAW) && !H_guess)
     return fail(h, MOND_EINVAL, "a guess warm start needs H_guess");
   if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
+  if (warm == MOND_WARM_INCREMENT) {
+    if (const char* why = inc_unready(h)) return fail(h, MOND_ESTATE, "incremental solve: %s", why);
+    return do_solve_increment(h, n_iter);
+  }
   return do_solve(h, n_iter, warm, H_guess);
 }
 
@@ -1215,8 +1371,11 @@ bool capturable(cudaStream_t st) { return st != nullptr && st != cudaStreamLegac
 int step_checks(mond_pm_t h, int n_iter, int warm) {
   if (!h->cell && h->N > 0) return fail(h, MOND_ESTATE, "no particles bound");
   if (n_iter < 0 || n_iter > 64) return fail(h, MOND_EINVAL, "n_iter must be in 0..64");
-  if (warm != MOND_WARM_NONE && warm != MOND_WARM_PREV) return fail(h, MOND_EINVAL, "step takes warm NONE or PREV");
+  if (warm != MOND_WARM_NONE && warm != MOND_WARM_PREV && warm != MOND_WARM_INCREMENT)
+    return fail(h, MOND_EINVAL, "step takes warm NONE, PREV or INCREMENT");
   if (warm != MOND_WARM_NONE && n_iter == 0) return fail(h, MOND_EINVAL, "a warm start needs n_iter >= 1");
+  if (warm == MOND_WARM_INCREMENT)
+    if (const char* why = inc_unready(h)) return fail(h, MOND_ESTATE, "incremental step: %s", why);
   if (h->gather_mode && n_iter == 0) return fail(h, MOND_EINVAL, "the interpolating gather needs n_iter >= 1");
   return MOND_OK;
 }
@@ -1229,7 +1388,8 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   int rc = step_checks(h, n_iter, warm);
   if (rc) return rc;
   const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
-                              h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell};
+                              h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell,
+                              h->inc.dep0};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -1346,7 +1506,7 @@ int mond_pm_batch_step(mond_pm_batch_t b, double dt, int n_steps, int n_iter, in
   std::vector<mond_pm::GraphKey> keys;
   for (auto h : b->hs)
     keys.push_back({dt, n_iter, warm, h->keep_phi, h->track_dh, h->pipelined, h->chunk, h->gather_mode, h->ext_axis,
-                    h->ext_mass, h->N, h->cell});
+                    h->ext_mass, h->N, h->cell, h->inc.dep0});
   bool same = b->gexec && keys.size() == b->keys.size();
   for (size_t i = 0; same && i < keys.size(); i++) same = keys[i] == b->keys[i];
   if (!same) {
@@ -1609,6 +1769,11 @@ int mond_pm_get_field(mond_pm_t h, int which, float* dst) {
     case MOND_FIELD_SMOOTH:
       if (!h->have_smooth) return fail(h, MOND_ESTATE, "no smooth() yet");
       src = h->w.smooth;
+      planes = 3;
+      break;
+    case MOND_FIELD_GM:
+      if (!h->inc_valid) return fail(h, MOND_ESTATE, "no base g_M: attach an increment workspace and solve");
+      src = h->inc.gM0;
       planes = 3;
       break;
     default: return fail(h, MOND_EINVAL, "unknown field %d", which);

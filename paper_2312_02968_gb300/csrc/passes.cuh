@@ -47,7 +47,12 @@ enum XMode {
   X_MU = 3,        // C2R g_M, F = mu(g_M) g_M, H = F - g_N, R2C
   X_INV = 4,       // C2R -> real planes
   X_FWD = 5,       // real planes -> R2C
-  X_NU_REAL = 6    // stored g_N (real) + H0, g_M = nu(F) F, R2C (reuses the last Newton solve)
+  X_NU_REAL = 6,   // stored g_N (real) + H0, g_M = nu(F) F, R2C (reuses the last Newton solve)
+  // incremental solve (Sect. 5.2 v): increments about a base state, nu and mu linearised
+  X_DRHO = 7,      // two int64 deposits -> FP32 density increment (integer difference), base := new; R2C
+  X_DNU_FIRST = 8, // C2R dg_N (store), dg_M = Jnu(g_N + H0) dg_N, R2C
+  X_DNU = 9,       // C2R dH, dg_M = Jnu(g_N + H0) (dg_N + dH), R2C
+  X_DMU = 10       // C2R dg_M, dH = Jmu(g_M0) dg_M - dg_N (optionally move the base on), R2C
 };
 
 // z-pass modes
@@ -75,6 +80,13 @@ struct XArgs {
   int ext_axis1;         // X_RHO, X_FWD of a density: 1 + axis of the external-field dipole layer, 0 none
   float ext_rho;         // its density: +ext_rho on the last plane along that axis, -ext_rho on the first
   double* red;           // dH reduction slots (2 doubles) or null
+  float* gM_out;         // X_MU: store the curl-free g_M it reads (the mu base of an incremental solve)
+  uint64_t* dep0;        // X_DRHO: base accumulator (read, then overwritten by dep)
+  const float* dgN;      // X_DNU, X_DMU: density increment's Newton field (3 real planes)
+  float* gM0;            // X_DMU: base g_M (3 real planes; += dg_M when base_update)
+  float* gN_upd;         // X_DMU with base_update: g_N += dg_N
+  int base_update;       // X_DMU: move the base on (last iteration)
+  int accumulate;        // X_INV: real_out += the transformed planes
   const float2* tw;      // twiddles, N entries
   uint32_t* status;
   int mu_kind;
@@ -128,6 +140,58 @@ __device__ __forceinline__ float mu_factor(int kind, float gm, float a0) {
       return x / sqrtf(1.0f + x * x);
     default: return 1.0f;
   }
+}
+
+// y nu'(y) at y = Fm/a0 given nu = nu_factor(kind, Fm, a0) > 0, and x mu'(x)
+// at x = gm/a0 given mu = mu_factor(kind, gm, a0) (the derivatives of the
+// functions above, for the linearised steps of Sect. 5.2 v).
+__device__ __forceinline__ float ynu_prime(int kind, float Fm, float a0, float nu) {
+  switch (kind) {
+    case 0: return -0.5f * nu;                                    // deep: -1/(2 sqrt y)
+    case 1: return -0.5f * a0 / (Fm * (nu - 0.5f));               // simple: -1/(2 y sqrt(1/4 + 1/y))
+    case 2: {                                                     // standard: -1/(nu y sqrt(y^2 + 4))
+      float y = Fm / a0;
+      return -1.0f / (nu * y * sqrtf(y * y + 4.0f));
+    }
+    default: return 0.0f;
+  }
+}
+__device__ __forceinline__ float xmu_prime(int kind, float gm, float a0, float mu) {
+  float x = gm / a0;
+  switch (kind) {
+    case 0: return x;                                             // deep
+    case 1: return x / ((1.0f + x) * (1.0f + x));                 // simple
+    case 2: {                                                     // standard: x/(1+x^2)^{3/2} = mu/(1+x^2)
+      float r = x > 1.0f ? __frcp_rn(x * x) : 1.0f;
+      return x > 1.0f ? mu * r / (1.0f + r) : mu / (1.0f + x * x);
+    }
+    default: return 0.0f;
+  }
+}
+
+// Linearised step about the point P (3 components) applied to d, in place:
+// d <- f(p) d + p f'(p) (u.d) u, p = |P|/a0, u = P/|P|, f = nu (MU = false)
+// or mu (MU = true). The identity for the Newtonian kind; 0 where P = 0.
+template <bool MU>
+__device__ __forceinline__ void linearised(int kind, float a0, const float* P, float* d) {
+  if (kind == 3) return;
+  const float m = sqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+  if (!(m > 0.0f)) {
+    d[0] = d[1] = d[2] = 0.0f;
+    return;
+  }
+  float f, fp;
+  if constexpr (MU) {
+    f = mu_factor(kind, m, a0);
+    fp = xmu_prime(kind, m, a0, f);
+  } else {
+    f = nu_factor(kind, m, a0);
+    fp = ynu_prime(kind, m, a0, f);
+  }
+  const float im = __frcp_rn(m);
+  const float ud = (P[0] * d[0] + P[1] * d[1] + P[2] * d[2]) * im;
+  const float c = fp * ud * im;
+  for (int a = 0; a < 3; a++) d[a] = f * d[a] + c * P[a];
 }
 
 // ---------------------------------------------------------------------------
@@ -264,11 +328,12 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
   const int tid = threadIdx.x;
   const int64_t line0 = (int64_t)blockIdx.x * C::L;
   for (int i = tid; i < N; i += NTX) tw[i] = a.tw[i];
-  const int nc = (MODE == X_RHO) ? 1 : a.ncomp;
+  const int nc = (MODE == X_RHO || MODE == X_DRHO) ? 1 : a.ncomp;
 
-  constexpr bool INV = (MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_INV);
+  constexpr bool INC = (MODE == X_DNU_FIRST || MODE == X_DNU || MODE == X_DMU);  // incremental, 3 components
+  constexpr bool INV = (MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_INV || INC);
   constexpr bool FWD = (MODE == X_RHO || MODE == X_NU_FIRST || MODE == X_NU || MODE == X_MU || MODE == X_FWD ||
-                        MODE == X_NU_REAL);
+                        MODE == X_NU_REAL || MODE == X_DRHO || INC);
 
   if (tid == 0) {
     // the real-space planes the pointwise stage reads, brought into L2 while
@@ -282,6 +347,12 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
         if (a.H0) tma::prefetch_l2(a.H0 + o, rb);
       if constexpr (MODE == X_NU)
         if (a.Hs_out && a.red) tma::prefetch_l2(a.Hs_out + o, rb);
+      if constexpr (MODE == X_DNU_FIRST || MODE == X_DNU) {
+        tma::prefetch_l2(a.gN + o, rb);
+        tma::prefetch_l2(a.H0 + o, rb);
+      }
+      if constexpr (MODE == X_DNU || MODE == X_DMU) tma::prefetch_l2(a.dgN + o, rb);
+      if constexpr (MODE == X_DMU) tma::prefetch_l2(a.gM0 + o, rb);
     }
   }
   if constexpr (INV) {
@@ -311,6 +382,78 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
         r1 += e.y;
       }
       *p0 = make_float2(r0, r1);
+    } else if constexpr (MODE == X_DRHO) {
+      // increment of two deposits: the int64 difference first (exact), then the
+      // density rule; the new deposit becomes the base
+      ulonglong2 u = *reinterpret_cast<const ulonglong2*>(a.dep + ri);
+      ulonglong2* bp = reinterpret_cast<ulonglong2*>(a.dep0 + ri);
+      ulonglong2 u0 = *bp;
+      *bp = u;
+      float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)(u.x - u0.x)), a.rho_scale));
+      float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)(u.y - u0.y)), a.rho_scale));
+      *p0 = make_float2(r0, r1);
+    } else if constexpr (INC) {
+      const int64_t P3 = (int64_t)N * N * N;
+      float v[3][2], dg[3][2], bs[3][2];
+      for (int c = 0; c < 3; c++) {
+        float2 t = p0[c * TILE];
+        v[c][0] = t.x;
+        v[c][1] = t.y;
+      }
+      if constexpr (MODE == X_DNU_FIRST) {
+        // input is dg_N: store it; dF = dg_N
+        for (int c = 0; c < 3; c++)
+          *reinterpret_cast<float2*>(a.gN_out + c * P3 + ri) = make_float2(v[c][0], v[c][1]);
+      } else {
+        for (int c = 0; c < 3; c++) {
+          float2 t = *reinterpret_cast<const float2*>(a.dgN + c * P3 + ri);
+          dg[c][0] = t.x;
+          dg[c][1] = t.y;
+        }
+      }
+      if constexpr (MODE == X_DNU)
+        for (int c = 0; c < 3; c++) {  // dF = dg_N + dH
+          v[c][0] += dg[c][0];
+          v[c][1] += dg[c][1];
+        }
+      // the linearisation point: F0 = g_N + H0 (nu steps) or g_M0 (mu step)
+      for (int c = 0; c < 3; c++) {
+        float2 t;
+        if constexpr (MODE == X_DMU) {
+          t = *reinterpret_cast<const float2*>(a.gM0 + c * P3 + ri);
+        } else {
+          t = *reinterpret_cast<const float2*>(a.gN + c * P3 + ri);
+          float2 h0 = *reinterpret_cast<const float2*>(a.H0 + c * P3 + ri);
+          t.x += h0.x;
+          t.y += h0.y;
+        }
+        bs[c][0] = t.x;
+        bs[c][1] = t.y;
+      }
+      if constexpr (MODE == X_DMU) {
+        if (a.base_update) {
+          // g_M0 += dg_M, g_N += dg_N: the base moves on to the new state
+          for (int c = 0; c < 3; c++) {
+            *reinterpret_cast<float2*>(a.gM0 + c * P3 + ri) =
+                make_float2(bs[c][0] + v[c][0], bs[c][1] + v[c][1]);
+            float* gp = a.gN_upd + c * P3 + ri;
+            float2 g = *reinterpret_cast<const float2*>(gp);
+            *reinterpret_cast<float2*>(gp) = make_float2(g.x + dg[c][0], g.y + dg[c][1]);
+          }
+        }
+      }
+      for (int e = 0; e < 2; e++) {
+        float P[3] = {bs[0][e], bs[1][e], bs[2][e]};
+        float d[3] = {v[0][e], v[1][e], v[2][e]};
+        linearised<MODE == X_DMU>(a.mu_kind, a.a0, P, d);
+        for (int c = 0; c < 3; c++) {
+          float o = d[c];
+          if constexpr (MODE == X_DMU) o -= dg[c][e];  // dH = dF - dg_N
+          bad |= !isfinite(o);
+          v[c][e] = o;
+        }
+      }
+      for (int c = 0; c < 3; c++) p0[c * TILE] = make_float2(v[c][0], v[c][1]);
     } else if constexpr (MODE == X_FWD) {
       for (int c = 0; c < nc; c++) p0[c * TILE] = *reinterpret_cast<const float2*>(a.real_in + (int64_t)c * N * N * N + ri);
       if (a.ext_axis1) {
@@ -322,7 +465,13 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
       for (int c = 0; c < nc; c++) {
         float2 v = p0[c * TILE];
         bad |= !(isfinite(v.x) && isfinite(v.y));
-        *reinterpret_cast<float2*>(a.real_out + (int64_t)c * N * N * N + ri) = v;
+        float2* dst = reinterpret_cast<float2*>(a.real_out + (int64_t)c * N * N * N + ri);
+        if (a.accumulate) {
+          const float2 o = *dst;
+          v.x += o.x;
+          v.y += o.y;
+        }
+        *dst = v;
         if (a.real_out2) *reinterpret_cast<float2*>(a.real_out2 + (int64_t)c * N * N * N + ri) = v;
       }
     } else {
@@ -363,6 +512,11 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
           gn[c][0] = t.x;
           gn[c][1] = t.y;
         }
+      }
+      if constexpr (MODE == X_MU) {
+        if (a.gM_out)
+          for (int c = 0; c < 3; c++)
+            *reinterpret_cast<float2*>(a.gM_out + (int64_t)c * N * N * N + ri) = make_float2(v[c][0], v[c][1]);
       }
       if constexpr (MODE == X_NU) {
         // input is H after the divergence-free projection

@@ -22,7 +22,7 @@ size_t z_smem(int ntiles) { return sizeof(float2) * (2 * N + (size_t)ntiles * N 
 
 template <int MODE>
 cudaError_t launch_x(const XArgs& a, cudaStream_t st) {
-  int nc = (MODE == X_RHO) ? 1 : a.ncomp;
+  int nc = (MODE == X_RHO || MODE == X_DRHO) ? 1 : a.ncomp;
   size_t sm = x_smem(nc);
   cudaError_t e = set_smem(k_xpass<N, MODE>, x_smem(4));
   if (e != cudaSuccess) return e;
@@ -54,6 +54,10 @@ cudaError_t CAT(mond_xpass_, MOND_N)(int mode, const passes::XArgs& a, cudaStrea
     case X_INV: return launch_x<X_INV>(a, st);
     case X_FWD: return launch_x<X_FWD>(a, st);
     case X_NU_REAL: return launch_x<X_NU_REAL>(a, st);
+    case X_DRHO: return launch_x<X_DRHO>(a, st);
+    case X_DNU_FIRST: return launch_x<X_DNU_FIRST>(a, st);
+    case X_DNU: return launch_x<X_DNU>(a, st);
+    case X_DMU: return launch_x<X_DMU>(a, st);
   }
   return cudaErrorInvalidValue;
 }
