@@ -283,7 +283,8 @@ class MondPM:
 
     def restore(self, f) -> int:
         """Load a checkpoint into the bound particle arrays and the H state;
-        returns its step count."""
+        returns its step count. Replacing H drops the base of the incremental
+        solve: a run of WARM_INCREMENT steps resumes with one full step."""
         torch = self.torch
         state = torch.load(f)
         if state["nf"] != self.nf or state["mass"].numel() != self.particles[3].numel():

@@ -86,6 +86,30 @@ def test_batch_of_uneven_systems_matches_individual_steps(B):
     batch.close()
 
 
+def test_batch_of_incremental_steps_matches_individual_steps(B):
+    # members with an increment workspace: one full step, then incremental
+    # steps (Sect. 5.2 v), in one graph per step against each stepped alone
+    sizes = [(64, 20000, 31, B.MU_DEEP), (96, 30000, 32, B.MU_STANDARD)]
+    ref, bat = [], []
+    for n, N, sd, mu in sizes:
+        ref.append(system(B, n, N, sd, mu, torch.cuda.Stream()))
+        bat.append(system(B, n, N, sd, mu, torch.cuda.Stream()))
+    for h, _ in ref + bat:
+        h.enable_increment(True)
+    for h, _ in ref:
+        h.step(0.5, 4, B.WARM_NONE)
+        for _ in range(3):
+            h.step(0.5, 1, B.WARM_INCREMENT)
+        h.sync()
+    batch = B.Batch([h for h, _ in bat])
+    batch.step(0.5, n_steps=1, n_iter=4)
+    batch.step(0.5, n_steps=3, n_iter=1, warm=B.WARM_INCREMENT)
+    batch.sync()
+    for (h, t), (hr, tr) in zip(bat, ref):
+        assert same(state(t), state(tr))
+    batch.close()
+
+
 def test_autotune_choices_give_identical_states(B):
     s = torch.cuda.Stream()
     h, t = system(B, 96, 40000, 21, B.MU_DEEP, s)

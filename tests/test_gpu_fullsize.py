@@ -7,7 +7,8 @@ replayed from a CUDA graph.
 - the K = 4 acceleration mesh, to the 1e-5 relative L2 bar;
 - after one graph-replayed step, a seeded sample of 20000 particles: the
   velocity change against the oracle's Eq. gi at the oracle's mesh, and the
-  positions after the drift.
+  positions after the drift;
+- one incremental solve (Sect. 5.2 v) against the oracle's increment.
 """
 import numpy as np
 import pytest
@@ -19,6 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 N_MESH, N_PART, SIGMA, K, DT = 256, 1_000_000, 1.5, 4, 0.25
+BASE = {}  # the oracle's finished K = 4 solve of the workload (filled by the setup fixture)
 
 
 def rel(a, b):
@@ -39,7 +41,9 @@ def setup():
     p = W.isothermal(N_MESH, 1.0, N_PART, 8.0, 0.4 * N_MESH, seed=1)
     acc, ka, _ = oracle.deposit_fixed(N_MESH, SIGMA, p["cell"], p["offset"], p["mass"])
     _, rho = oracle.acc_to_rho(acc, ka, 1.0)
-    ref = oracle.solve(rho, 1.0, 1.0, 1.0, 0, K, want=("acc",))
+    # finished, so that the same solve is also the base of the incremental step
+    ref = oracle.solve(rho, 1.0, 1.0, 1.0, 0, K, finish_h=True, want=("acc", "gN", "H", "gM"))
+    BASE.update(ref)
     return B, p, acc, ka, ref["acc"]
 
 
@@ -84,6 +88,43 @@ def test_fullsize_graph_step_sample(setup):
     pos = t[0].cpu().numpy()[idx] + t[1].cpu().numpy()[idx].astype(np.float64)
     d = np.abs(((pos - pos_ref) + N_MESH / 2) % N_MESH - N_MESH / 2)
     assert d.max() < 1e-4
+
+
+def test_fullsize_incremental_solve(setup):
+    """The incremental solve (Sect. 5.2 v) at the bench's size: the K = 4 solve
+    of the workload is the base, the whole sphere then moves 3 px along x, and
+    one linearised iteration on that deposit increment is compared with the
+    oracle's increment from the oracle's own base: the total acceleration mesh
+    to 1e-5 and the increment itself to 1e-5 |a| / |da|."""
+    B, p, acc0, ka, a_ref = setup
+    base = BASE
+    q = {k: v.copy() for k, v in p.items()}
+    q["cell"][:, 0] += 3
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        h = B.MondPM(N_MESH, 1, float(N_MESH), 1.0, 1.0, B.MU_DEEP, SIGMA, N_PART, stream=st)
+        t = [torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("cell", "offset", "vel", "mass")]
+    torch.cuda.synchronize()
+    h.bind_particles(*t)
+    h.enable_increment(True)
+    h.deposit()
+    h.solve_field(K, B.WARM_NONE)
+    a0 = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    assert rel(h.get_field(B.FIELD_GM).cpu().numpy(), base["gM"]) < 1e-5
+    with torch.cuda.stream(st):
+        t[0].copy_(torch.from_numpy(q["cell"]))
+    h.deposit()
+    h.solve_field(1, B.WARM_INCREMENT)
+    a1 = h.get_field(B.FIELD_ACC).cpu().numpy().astype(np.float64)
+    acc1, _, _ = oracle.deposit_fixed(N_MESH, SIGMA, q["cell"], q["offset"], q["mass"], ka)
+    drho = oracle.delta_rho(acc1, acc0, ka, 1.0)
+    inc = oracle.solve_increment(drho, 1.0, 1.0, 1.0, 0, 1, base["gN"], base["H"], base["gM"])
+    want = a_ref + inc["dacc"]
+    assert rel(a1, want) < 1e-5
+    ratio = np.linalg.norm(want) / np.linalg.norm(inc["dacc"])
+    assert ratio < 20
+    assert rel(a1 - a0, inc["dacc"]) < 1e-5 * ratio
+    h.close()
 
 
 def test_ring_config_at_512_against_eq_ringforce():
