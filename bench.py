@@ -55,7 +55,12 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region: sampling starts before the warm-up (the tool takes a moment to
+    come up), every line is stamped on arrival, and only the lines that
+    arrive between window() and stop() are kept (one interval's grace)."""
+
+    INTERVAL_MS = 50
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,11 +70,12 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.w0 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -78,20 +84,29 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def window(self):
+        """The timed region begins now."""
+        self.w0 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        w1 = time.perf_counter() + self.INTERVAL_MS / 1000.0
+        time.sleep(self.INTERVAL_MS / 1000.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         time.sleep(0.05)
+        w0 = self.w0 if self.w0 is not None else float("-inf")
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if not (w0 <= ts <= w1):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -104,7 +119,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": self.INTERVAL_MS}
 
 
 def make_workload(rank: int):
@@ -610,14 +625,15 @@ def main():
     K, dt = WL["K"], WL["dt"]
     h.set_option(B.OPT_USE_GRAPH, 0 if args.no_graph else 1)
 
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(args.warmup):
         h.step(dt, K, B.WARM_NONE)
     h.sync()
 
     # ---- timed region: plain 4-iteration steps (one CUDA graph per step) -------
-    sampler = ClockSampler(local)
     barrier()
-    sampler.start()
+    sampler.window()
     l0 = h.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
