@@ -68,7 +68,7 @@ def oracle_rho(p, n, sigma, s, kacc=None):
 
 
 @pytest.mark.parametrize("n,pad,mu,a0,K0,K", [(32, 1, 0, 1.0, 4, 1), (32, 1, 2, 0.02, 4, 3), (16, 2, 1, 0.05, 3, 2),
-                                              (48, 1, 3, 1.0, 2, 2)])
+                                              (48, 1, 3, 1.0, 2, 2), (96, 1, 0, 1.0, 3, 2)])
 def test_increment_matches_oracle(B, n, pad, mu, a0, K0, K):
     nf, sigma, s = n * pad, 1.5, 1.0
     p = W.isothermal(nf, s, 3000, nf / 10, 0.3 * nf, seed=nf + K)
