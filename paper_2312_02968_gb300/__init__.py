@@ -23,13 +23,13 @@ A time step of one system::
         phantom = h.density(B.DENS_PHANTOM)   # apparent minus baryonic density
         print(h.diagnostics()["e_kin"], phantom.sum().item())
 
+Modules: ``binding`` (the handle, batches, the autotuner), ``surrogate`` and
+``train_surrogate`` (the learned warm start), ``workloads`` (seeded initial
+conditions), ``replicas`` (host logic of runs on several GPUs), ``build``.
+
 Other warm starts: ``MOND_WARM_GUESS`` from the learned surrogate, and the
 incremental solve of Sect. 5.2 (v) -- ``h.enable_increment()`` attaches its
 workspace, a full step then keeps the base state, and ``h.step(dt, 1,
 B.WARM_INCREMENT)`` iterates the linearised steps on the deposit's change.
-
-Modules: ``binding`` (the handle, batches, the autotuner), ``surrogate`` and
-``train_surrogate`` (the learned warm start), ``workloads`` (seeded initial
-conditions), ``replicas`` (host logic of runs on several GPUs), ``build``.
 """
 __all__ = ["binding", "workloads"]
