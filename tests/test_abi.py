@@ -53,6 +53,21 @@ def test_workspace_bytes_host_only(lib):
             B.workspace_bytes(bad[0], bad[1], bad[2], 10)
 
 
+def test_increment_workspace_bytes_host_only(lib):
+    # the base deposit (int64) and two float32 vector fields, plus alignment slack
+    from paper_2312_02968_gb300 import binding as B
+
+    n = ctypes.c_size_t()
+    for side, pad in ((256, 1), (64, 2), (96, 1)):
+        assert lib.mond_pm_increment_workspace_bytes(B.Grid(side, pad), ctypes.byref(n)) == 0
+        n3 = (side * pad) ** 3
+        assert 32 * n3 <= n.value <= 32 * n3 + 1024
+    for bad in ((100, 1), (256, 3), (1024, 1), (0, 1)):
+        assert lib.mond_pm_increment_workspace_bytes(B.Grid(*bad), ctypes.byref(n)) == -1
+    assert lib.mond_pm_increment_workspace_bytes(B.Grid(64, 1), None) == -1
+    assert lib.mond_pm_set_increment_workspace(None, None, 0) == -1
+
+
 def test_create_rejects_bad_arguments_without_touching_the_device(lib):
     from paper_2312_02968_gb300 import binding as B
 
