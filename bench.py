@@ -342,6 +342,21 @@ def run_increment(h, B, stream, t, init, steps, warmup):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        # a few more with every launch event-timed: the incremental x-passes
+        # against the measured copy peak
+        peak, _ = load_peaks()
+        h.set_option(B.OPT_TIMING, 1)
+        h.kernel_stats()
+        for _ in range(5):
+            h.step(dt, 1, B.WARM_INCREMENT)
+        stats = h.kernel_stats()
+        h.set_option(B.OPT_TIMING, 0)
+        passes = {}
+        for st in stats:
+            if st["name"].startswith(("xpass_d", "xpass_inv")) and st["launches"]:
+                per = st["ms"] / st["launches"]
+                gbps = st["bytes"] / st["launches"] / (per / 1000.0) / 1e9
+                passes[st["name"]] = {"ms_per_launch": per, "GBps": gbps, "frac_of_peak": gbps / peak}
         h.deposit()
         h.solve_field(1, B.WARM_INCREMENT)
         g_inc = h.gather().double()
@@ -352,7 +367,7 @@ def run_increment(h, B, stream, t, init, steps, warmup):
         err = float(torch.linalg.norm(g_inc - g_ref) / torch.linalg.norm(g_ref))
         h.sync()
         return {"mode": "incremental, 1 iteration", "steps_per_s": 1000.0 / ms, "ms_per_step": ms,
-                "force_rel_err": err, "incremental_steps_since_full_solve": warmup + steps + 1}
+                "force_rel_err": err, "incremental_steps_since_full_solve": warmup + steps + 6, "passes": passes}
     finally:
         h.enable_increment(False)
 
