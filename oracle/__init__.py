@@ -11,7 +11,9 @@ What pins each function (tests in ``tests/test_oracle_*.py``):
   axis_lut        Poisson-summation normalisation of the sampled Gaussian.
   deposit_fixed   vs the direct FP64 Eq. smooth (error bound of the rule);
                   Fourier transform of one particle = exp(-sigma^2 k^2/2)
-                  (App. Fourier); mass conservation; order independence.
+                  (App. Fourier); mass conservation; order independence;
+                  the integer rule tap by tap (a hand-worked particle, and
+                  every tap of single particles recomputed from the rule).
   fft1/fft3       vs the plain DFT; round trip; Parseval; numpy.fft.
   mu/nu           mu(x) x = y <=> nu(y) y = x for every kind (Sect. 2.1).
   solve           transform count 42 for K = 4 and 2 for Newton (Sect. 5.2,
@@ -19,8 +21,14 @@ What pins each function (tests in ``tests/test_oracle_*.py``):
                   solve of a point mass; curl/div invariants; deep-MOND
                   point-mass field sqrt(G M a0)/r (Sect. 2); two-body force
                   (Eq. twobodyforce); ring force (Eq. ringforce); isothermal
-                  field (Eq. g); residual of the discretised AQUAL equation at
-                  the converged fixed point; convergence rate (Sect. 2.1).
+                  field (Eq. g); the low-k residual of the discretised AQUAL
+                  equation falls tenfold in three iterations; convergence
+                  rate (Sect. 2.1); in FP64 the iterates end in a period-2
+                  cycle at the zero of the field (reading R14).
+  aqual_solve     the exact solution of the discretised AQUAL equation is a
+                  fixed point of the iteration (odd grids, every kind); a
+                  brute-force scipy minimisation of the same energy on 8^3
+                  and 9^3 agrees; Newtonian closed form A (k.kappa) phi_N^.
   gather          particle at a node sees the node-smoothed field; constant
                   field reproduces the ball weight sum; two-body force.
   push            Eq. motion on hand-checked numbers; circular orbit period.
@@ -121,12 +129,16 @@ def lib():
             L.ora_particle_diag.argtypes = [i32, f64, i64, P, P, P, P, P]
             L.ora_transform_count.restype = ctypes.c_longlong
             L.ora_num_threads.restype = i32
+            L.ora_set_num_threads.restype = i32
+            L.ora_set_num_threads.argtypes = [i32]
             L.ora_project_div.argtypes = [i32, f64, P, P]
             L.ora_field_density.argtypes = [i32, f64, f64, P, P]
             L.ora_box_flux_mass.restype = f64
             L.ora_box_flux_mass.argtypes = [i32, f64, f64, P, P, P]
             L.ora_shell_mass.argtypes = [i32, f64, P, P, f64, i32, P]
             L.ora_interp_gather.argtypes = [i32, i32, P, i64, P, P, P]
+            L.ora_aqual_solve.restype = i32
+            L.ora_aqual_solve.argtypes = [i32, f64, f64, f64, i32, P, P, f64, i32, P, P, P]
             _lib = L
         return _lib
 
@@ -141,6 +153,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return lib().ora_num_threads()
+
+
+def set_num_threads(t: int) -> int:
+    """Threads of the oracle's parallel loops from now on; returns the count."""
+    return lib().ora_set_num_threads(int(t))
 
 
 def mu(kind: int, x: float) -> float:
@@ -254,6 +271,27 @@ def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None
         if v is not None:
             out[k] = v
     return out
+
+
+def aqual_solve(rho, s: float, G: float, a0: float, mu_kind: int, phi0=None, tol: float = 1e-9,
+                max_iter: int = 400):
+    """The exact solution of the discretised AQUAL equation (the field the
+    iteration of Sect. 2.1 would reach if it converged): the minimiser of the
+    convex mesh energy sum a0^2 Psi(|D phi|/a0) + g_N . D phi (Psi' = mu(x) x),
+    by preconditioned L-BFGS from phi0 (default zero). Returns dict phi,
+    acc = -grad_FD phi ([3,n,n,n]), iterations, rel_grad (|grad E| over
+    |D^T g_N| at the end) and evals."""
+    rho = _c(rho, np.float64)
+    n = rho.shape[0]
+    phi = np.zeros((n, n, n))
+    acc = np.zeros((3, n, n, n))
+    info = np.zeros(3)
+    p0 = None if phi0 is None else _c(phi0, np.float64)
+    rc = lib().ora_aqual_solve(n, float(s), float(G), float(a0), int(mu_kind), _p(rho), _p(p0), float(tol),
+                               int(max_iter), _p(phi), _p(acc), _p(info))
+    if rc != 0:
+        raise RuntimeError(f"oracle AQUAL solve failed: {rc}")
+    return {"phi": phi, "acc": acc, "iterations": int(info[0]), "rel_grad": float(info[1]), "evals": int(info[2])}
 
 
 def solve_increment(drho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, gN0, H0, gM0):

@@ -35,8 +35,13 @@
  *                      Newtonian closed form; spectral Poisson of a point mass;
  *                      curl/div invariants; deep-MOND point mass sqrt(GMa0)/r
  *                      (Sect. 2); Eq. twobodyforce; Eq. ringforce; Eq. g of the
- *                      isothermal sphere; discretised AQUAL residual at the fixed
- *                      point; convergence rate (Sect. 2.1)
+ *                      isothermal sphere; low-k AQUAL residual falls tenfold in
+ *                      three iterations; convergence rate (Sect. 2.1); the FP64
+ *                      period-2 cycle at the zero of the field
+ *   ora_aqual_solve    a fixed point of the iteration (odd grids); brute-force
+ *                      minimisation of the same energy; Newtonian closed form
+ *   ora_deposit_fixed  (integer rule) a hand-worked particle; every tap of single
+ *                      particles recomputed from the rule
  *   ora_gather         node-smoothed field at nodes; constant field; two-body force
  *   ora_push           Eq. motion on hand-checked numbers
  *   ora_particle_diag  two-body constants of motion on hand-made states
@@ -71,6 +76,18 @@ int ora_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
 #else
+  return 1;
+#endif
+}
+
+/* Threads of the OpenMP loops from now on (timing of the oracle at a given
+ * thread count); returns the count in force. */
+int ora_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+  return omp_get_max_threads();
+#else
+  (void)t;
   return 1;
 #endif
 }
@@ -990,4 +1007,250 @@ void ora_interp_gather(int n, int order, const double* S, int64_t N, const int32
         }
     for (int a = 0; a < 3; a++) out[3 * i + a] = g[a];
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact solution of the discretised AQUAL equation (Sect. 2.1, Eq. PDE)     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The iteration of Sect. 2.1 stops at its K-th iterate; this function finds
+ * the field that iteration would reach if it converged: the potential phi
+ * whose spectral gradient u = D phi satisfies the AQUAL equation on the mesh,
+ *
+ *   D^T [ mu(|u|/a0) u + g_N ] = 0,           (div of mu(|g|/a0) g = div g_N)
+ *
+ * with g = -u the MOND acceleration and g_N the Newtonian field of the
+ * solve (App. Flow steps 3-6, here from ora_solve with K = 0). D_a is the
+ * spectral derivative i k_a with the Nyquist term dropped (the real-part
+ * convention of the odd operators), D^T its transpose (-div). The equation
+ * is the stationarity condition of the convex energy
+ *
+ *   E(phi) = sum_cells [ a0^2 Psi(|D phi|/a0) + g_N . D phi ],
+ *   Psi(x) = integral_0^x mu(t) t dt,
+ *
+ * (the mesh form of the AQUAL Lagrangian), whose gradient is
+ * D^T [mu(|u|/a0) u + g_N]. Psi is convex for every interpolation function
+ * here (x mu(x) increases), so E has one minimiser up to a constant in phi.
+ * It is found by limited-memory BFGS (8 pairs) with the inverse spectral
+ * Laplacian (D^T D)^-1 as the initial inverse Hessian and an Armijo
+ * backtracking line search, starting from phi0 (NULL: zero), until
+ * |grad E| <= tol |D^T g_N| or the line search can no longer lower E.
+ * Outputs: phi (n^3), acc = -grad_FD phi (3 n^3, the acceleration mesh the
+ * method would form from it, App. Flow step 9), info[0] = iterations,
+ * info[1] = final relative gradient, info[2] = energy evaluations.
+ */
+static double psi_mu(int kind, double x) {
+  double x2 = x * x;
+  switch (kind) {
+    case ORA_MU_DEEP: return x2 * x / 3.0;
+    case ORA_MU_SIMPLE: /* x^2/2 - x + ln(1+x), by its series where that cancels */
+      if (x < 1e-2) return x2 * x * (1.0 / 3.0 - x / 4.0 + x2 / 5.0 - x2 * x / 6.0 + x2 * x2 / 7.0);
+      return 0.5 * x2 - x + log1p(x);
+    case ORA_MU_STANDARD: /* (x sqrt(1+x^2) - asinh x) / 2 */
+      if (x < 1e-2) return x2 * x * (1.0 / 3.0 - x2 / 10.0 + 3.0 * x2 * x2 / 56.0);
+      return 0.5 * (x * sqrt(1.0 + x2) - asinh(x));
+    case ORA_MU_NEWTON: return 0.5 * x2;
+  }
+  return NAN;
+}
+
+/* The wave number of odd operators: k_a, with 0 on axis a's Nyquist index. */
+static inline void kvec_odd(int n, double s, int i, int j, int l, double* k) {
+  kvec(n, s, i, j, l, k);
+  if (n % 2 == 0) {
+    if (i == n / 2) k[0] = 0.0;
+    if (j == n / 2) k[1] = 0.0;
+    if (l == n / 2) k[2] = 0.0;
+  }
+}
+
+/* u = D phi (3 planes). c: n^3 complex scratch. */
+static void aq_grad(int n, double s, const double* phi, double* u, cplx* c, cplx* c2) {
+  int64_t tot = (int64_t)n * n * n;
+  for (int64_t j = 0; j < tot; j++) c[j] = phi[j];
+  fwd3(n, s, c);
+  for (int a = 0; a < 3; a++) {
+    for (int l = 0; l < n; l++)
+      for (int jy = 0; jy < n; jy++)
+        for (int i = 0; i < n; i++) {
+          double k[3];
+          kvec_odd(n, s, i, jy, l, k);
+          int64_t j = idx3(n, i, jy, l);
+          c2[j] = I * k[a] * c[j];
+        }
+    inv3_real(n, s, c2, u + a * tot);
+  }
+}
+
+/* out = D^T w = -sum_a D_a w_a (w: 3 planes). */
+static void aq_gradT(int n, double s, const double* w, double* out, cplx* c, cplx* c2) {
+  int64_t tot = (int64_t)n * n * n;
+  for (int64_t j = 0; j < tot; j++) c2[j] = 0;
+  for (int a = 0; a < 3; a++) {
+    for (int64_t j = 0; j < tot; j++) c[j] = w[a * tot + j];
+    fwd3(n, s, c);
+    for (int l = 0; l < n; l++)
+      for (int jy = 0; jy < n; jy++)
+        for (int i = 0; i < n; i++) {
+          double k[3];
+          kvec_odd(n, s, i, jy, l, k);
+          int64_t j = idx3(n, i, jy, l);
+          c2[j] += -I * k[a] * c[j];
+        }
+  }
+  inv3_real(n, s, c2, out);
+}
+
+/* out = (D^T D)^+ g: divide the spectrum by |k_odd|^2 (0 where that is 0). */
+static void aq_precond(int n, double s, const double* g, double* out, cplx* c) {
+  int64_t tot = (int64_t)n * n * n;
+  for (int64_t j = 0; j < tot; j++) c[j] = g[j];
+  fwd3(n, s, c);
+  for (int l = 0; l < n; l++)
+    for (int jy = 0; jy < n; jy++)
+      for (int i = 0; i < n; i++) {
+        double k[3];
+        kvec_odd(n, s, i, jy, l, k);
+        double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        int64_t j = idx3(n, i, jy, l);
+        c[j] = kk > 0 ? c[j] / kk : 0;
+      }
+  inv3_real(n, s, c, out);
+}
+
+/* Compensated (Neumaier) summation: the energy differences the line search
+ * compares shrink with the square of the gradient, far below the rounding
+ * error of a plain sum over n^3 terms. */
+typedef struct {
+  double s, c;
+} aq_sum;
+static inline void aq_add(aq_sum* a, double v) {
+  double t = a->s + v;
+  if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+  else a->c += (v - t) + a->s;
+  a->s = t;
+}
+
+static double aq_dot(int64_t m, const double* a, const double* b) {
+  aq_sum t = {0, 0};
+  for (int64_t j = 0; j < m; j++) aq_add(&t, a[j] * b[j]);
+  return t.s + t.c;
+}
+
+/* E(phi) and its gradient. u, w: 3-plane scratch. */
+static double aq_energy(int n, double s, double a0, int kind, const double* gN, const double* phi, double* grad,
+                        double* u, double* w, cplx* c, cplx* c2) {
+  int64_t tot = (int64_t)n * n * n;
+  aq_grad(n, s, phi, u, c, c2);
+  aq_sum e = {0, 0};
+  for (int64_t j = 0; j < tot; j++) {
+    double um = 0;
+    for (int a = 0; a < 3; a++) {
+      um += u[a * tot + j] * u[a * tot + j];
+      aq_add(&e, gN[a * tot + j] * u[a * tot + j]);
+    }
+    um = sqrt(um);
+    aq_add(&e, a0 * a0 * psi_mu(kind, um / a0));
+    double m = ora_mu(kind, um / a0);
+    for (int a = 0; a < 3; a++) w[a * tot + j] = m * u[a * tot + j] + gN[a * tot + j];
+  }
+  aq_gradT(n, s, w, grad, c, c2);
+  return e.s + e.c;
+}
+
+#define AQ_M 8
+int ora_aqual_solve(int n, double s, double G, double a0, int mu_kind, const double* rho, const double* phi0,
+                    double tol, int max_iter, double* phi_out, double* acc_out, double* info) {
+  int64_t tot = (int64_t)n * n * n;
+  double* gN = (double*)malloc(sizeof(double) * 3 * tot);
+  double* u = (double*)malloc(sizeof(double) * 3 * tot);
+  double* w = (double*)malloc(sizeof(double) * 3 * tot);
+  double* x = (double*)malloc(sizeof(double) * tot);
+  double* g = (double*)malloc(sizeof(double) * tot);
+  double* xn = (double*)malloc(sizeof(double) * tot);
+  double* gn = (double*)malloc(sizeof(double) * tot);
+  double* q = (double*)malloc(sizeof(double) * tot);
+  double* z = (double*)malloc(sizeof(double) * tot);
+  double* S = (double*)malloc(sizeof(double) * AQ_M * tot);
+  double* Y = (double*)malloc(sizeof(double) * AQ_M * tot);
+  cplx* c = (cplx*)malloc(sizeof(cplx) * tot);
+  cplx* c2 = (cplx*)malloc(sizeof(cplx) * tot);
+  if (!gN || !u || !w || !x || !g || !xn || !gn || !q || !z || !S || !Y || !c || !c2) return ORA_ENOMEM;
+  int rc = ora_solve(n, s, G, a0, mu_kind, 0, rho, NULL, 0, gN, NULL, NULL, NULL, NULL, NULL);
+  if (rc != ORA_OK) return rc;
+  /* scale of the gradient: |D^T g_N| */
+  aq_gradT(n, s, gN, q, c, c2);
+  double g0 = sqrt(aq_dot(tot, q, q));
+  if (phi0) memcpy(x, phi0, sizeof(double) * tot);
+  else memset(x, 0, sizeof(double) * tot);
+  double e = aq_energy(n, s, a0, mu_kind, gN, x, g, u, w, c, c2);
+  int evals = 1, it = 0, m = 0, head = 0;
+  double rel = g0 > 0 ? sqrt(aq_dot(tot, g, g)) / g0 : 0.0;
+  double rho_k[AQ_M], alpha[AQ_M];
+  while (rel > tol && it < max_iter) {
+    /* two-loop recursion: z = H g with H0 = gamma (D^T D)^+ */
+    memcpy(q, g, sizeof(double) * tot);
+    for (int t = 0; t < m; t++) {
+      int b = (head - 1 - t + AQ_M) % AQ_M;
+      alpha[b] = rho_k[b] * aq_dot(tot, S + b * tot, q);
+      for (int64_t j = 0; j < tot; j++) q[j] -= alpha[b] * Y[b * tot + j];
+    }
+    aq_precond(n, s, q, z, c);
+    if (m > 0) {
+      int b = (head - 1 + AQ_M) % AQ_M;
+      aq_precond(n, s, Y + b * tot, xn, c);
+      double gam = aq_dot(tot, S + b * tot, Y + b * tot) / aq_dot(tot, Y + b * tot, xn);
+      for (int64_t j = 0; j < tot; j++) z[j] *= gam;
+    }
+    for (int t = m - 1; t >= 0; t--) {
+      int b = (head - 1 - t + AQ_M) % AQ_M;
+      double beta = rho_k[b] * aq_dot(tot, Y + b * tot, z);
+      for (int64_t j = 0; j < tot; j++) z[j] += S[b * tot + j] * (alpha[b] - beta);
+    }
+    /* direction -z; backtracking until E falls by the Armijo fraction */
+    double gd = -aq_dot(tot, g, z), step = 1.0, en = 0;
+    int ok = 0;
+    if (gd < 0) {
+      for (int tries = 0; tries < 30; tries++, step *= 0.5) {
+        for (int64_t j = 0; j < tot; j++) xn[j] = x[j] - step * z[j];
+        en = aq_energy(n, s, a0, mu_kind, gN, xn, gn, u, w, c, c2);
+        evals++;
+        if (en <= e + 1e-4 * step * gd) {
+          ok = 1;
+          break;
+        }
+      }
+    }
+    if (!ok) break; /* E can no longer be lowered at this precision */
+    double sy = 0;
+    for (int64_t j = 0; j < tot; j++) {
+      S[head * tot + j] = xn[j] - x[j];
+      Y[head * tot + j] = gn[j] - g[j];
+    }
+    sy = aq_dot(tot, S + head * tot, Y + head * tot);
+    if (sy > 0) {
+      rho_k[head] = 1.0 / sy;
+      head = (head + 1) % AQ_M;
+      if (m < AQ_M) m++;
+    }
+    memcpy(x, xn, sizeof(double) * tot);
+    memcpy(g, gn, sizeof(double) * tot);
+    e = en;
+    it++;
+    rel = g0 > 0 ? sqrt(aq_dot(tot, g, g)) / g0 : 0.0;
+  }
+  if (phi_out) memcpy(phi_out, x, sizeof(double) * tot);
+  if (acc_out) {
+    fd_grad(n, s, x, acc_out);
+    for (int64_t j = 0; j < 3 * tot; j++) acc_out[j] = -acc_out[j];
+  }
+  if (info) {
+    info[0] = it;
+    info[1] = rel;
+    info[2] = evals;
+  }
+  free(gN); free(u); free(w); free(x); free(g); free(xn); free(gn); free(q); free(z); free(S); free(Y);
+  free(c); free(c2);
+  return ORA_OK;
 }

@@ -38,6 +38,16 @@ def _pack(pos_px, vel, mass, n_f):
     }
 
 
+def displaced(p: dict, n_f: int, s: float, t: float):
+    """The particle set p with every position moved along its velocity for a
+    time t (vel * t / s pixels; t < 0 gives nearby earlier configurations, a
+    sequence of densities for warm-started solves). Cells and offsets are
+    recomputed; velocities and masses are kept."""
+    pos = p["cell"].astype(np.float64) - n_f / 2 + p["offset"].astype(np.float64)
+    pos = pos + p["vel"].astype(np.float64) * (t / s)
+    return _pack(pos, p["vel"], p["mass"], n_f)
+
+
 def uniform_random(n_f: int, N: int, seed: int, margin: int = 0, mass_range=(0.5, 1.5)):
     """Particles uniform in the domain (less a margin), random masses, small velocities."""
     rng = np.random.default_rng(seed)
