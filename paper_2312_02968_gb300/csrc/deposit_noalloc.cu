@@ -15,11 +15,22 @@
 // changes. Calls whose work overlaps on the GPU (for example two streams
 // without ordering between them) race on the shared scratch and give wrong
 // results; order them on one stream or synchronise between them.
+//
+// On the host, one mutex covers a whole call: the per-device bookkeeping and
+// the host staging copy of the table are shared by every thread, so calls from
+// several host threads are serialised while they enqueue (their GPU work can
+// still overlap, see above). The set-up of a device is keyed on the identity
+// of its current CUDA context: after cudaDeviceReset the module is loaded
+// again with fresh __device__ arrays, and the next call resolves their
+// addresses and uploads the table again.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/mond_pm.h"
 #include "common.cuh"
@@ -41,6 +52,7 @@ __device__ __align__(256) int g_scratch_emax[64];  // [0]: largest biased mass e
 
 struct DevScratch {
   bool ready = false;
+  unsigned long long ctx_id = 0;  // CUDA context the addresses below belong to
   unsigned long long* acc = nullptr;
   uint32_t* lut = nullptr;
   uint32_t* ball = nullptr;
@@ -51,6 +63,33 @@ struct DevScratch {
 DevScratch g_dev[kMaxDevices];
 uint32_t g_host_lut[kMaxLutWords];  // host staging, no heap allocation
 uint32_t g_host_ball[kMaxBall];
+std::mutex g_mu;  // guards g_dev and the staging arrays for the whole host part of a call
+
+// Identity of the calling thread's current CUDA context, through driver entry
+// points the runtime hands out (no link-time dependence on the driver
+// library). Returns false where it cannot be had.
+bool current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+  }
+  CUcontext ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 int reach(double sigma) {
   double lim = 16.0 * sigma * sigma;
@@ -148,12 +187,19 @@ extern "C" int mond_pm_deposit_noalloc(int32_t n_f, double s, double kernel_widt
     return set_error("deposit_noalloc: kernel width %g outside 0.75..2", kernel_width);
   if (!(s > 0) || N < 0 || N >= ((int64_t)1 << 31) || !rho_out || (N > 0 && (!cell || !offset || !mass)))
     return set_error("deposit_noalloc: bad pixel width, particle count or pointer");
+  std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return set_error("deposit_noalloc: no usable current device");
   DevScratch& d = g_dev[dev];
+  unsigned long long ctx_id = 0;
+  // A context that is not yet initialised, or one other than the set-up's
+  // (the device was reset since), needs the set-up below: new arrays, no
+  // table in them yet.
+  if (!current_context_id(&ctx_id) || ctx_id != d.ctx_id) d.ready = false;
   if (!d.ready) {
-    // first call on this device: device addresses of the scratch arrays
+    // first call on this device (or its context): device addresses of the scratch arrays
+    d.lut_sigma = -1.0;
     if (cudaGetSymbolAddress((void**)&d.acc, g_scratch_acc) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.lut, g_scratch_lut) != cudaSuccess ||
         cudaGetSymbolAddress((void**)&d.ball, g_scratch_ball) != cudaSuccess ||
@@ -161,6 +207,8 @@ extern "C" int mond_pm_deposit_noalloc(int32_t n_f, double s, double kernel_widt
       mond_pm_set_create_error("deposit_noalloc: cudaGetSymbolAddress failed");
       return MOND_ECUDA;
     }
+    // the runtime has made the context current by now
+    if (!current_context_id(&d.ctx_id)) d.ctx_id = 0;  // unknown: set up again on every call
     d.ready = true;
   }
   cudaError_t e = cudaSuccess;
