@@ -99,7 +99,7 @@ enum {
                              0: one tile per CTA with plain loads (same results) */
   MOND_OPT_CHUNK = 6,     /* particles per deposit/gather work item: a power of two in 256..4096
                              (default 2048; same results) */
-  MOND_OPT_GATHER = 7     /* force at the particles. 0 (default): Eq. gi, the ball sum at each particle.
+  MOND_OPT_GATHER = 7,    /* force at the particles. 0 (default): Eq. gi, the ball sum at each particle.
                              1 or 3: the mesh-interpolating gather -- the final pass of a solve (n_iter >= 1)
                              also multiplies the acceleration spectrum by the smoothing spectrum, so that
                              MOND_FIELD_ACC holds the node-smoothed field of mond_pm_smooth, and the force
@@ -107,6 +107,19 @@ enum {
                              that field at its position: an approximation of Eq. gi whose error the caller
                              measures against variant 0. A gather whose variant disagrees with the mesh
                              the last solve made fails with MOND_ESTATE. */
+  MOND_OPT_TEST_LOST_LOAD = 8, /* tests of the bounded device waits only. value t + 1 (t >= 0): in the next
+                             pipelined y-pass the tile copy of tile t is never issued, so the wait for it
+                             gives up after a short bound, the CTA waits for the copy it did issue and
+                             stops, and the next synchronising call returns MOND_ETIMEOUT (the fields of
+                             that solve are invalid; the handle stays usable). One-shot: cleared by that
+                             launch. 0: off. Needs MOND_OPT_PIPELINED 1 and no graph replay. */
+  MOND_OPT_CYCLE_MEAN = 9     /* value 1: a solve with n_iter >= 2 (plain or warm-started, not incremental)
+                             takes as its potential the mean of the potentials of its last two iterations'
+                             curl-free steps, phi^ = (phi^_{K-1} + phi^_K)/2. Near zeros of the field the
+                             iteration of Sect. 2.1 ends in a period-2 cycle (its iterates alternate about
+                             the solution of the discretised equation); the mean is the cycle's midpoint.
+                             Not in the paper. Costs one half-spectrum plane written and read. Needs
+                             MOND_OPT_PIPELINED 1 (default 0) */
 };
 
 /* Per kernel class: launches, device time between the events around each
@@ -393,8 +406,12 @@ int mond_pm_kernel_stats(mond_pm_t h, mond_pm_kstat* out, int cap, int* count);
  * else returns MOND_EINVAL with a message in mond_pm_last_error(NULL).
  * The first call on a device, and any call that changes kernel_width, sets
  * the scratch up and synchronises cuda_stream; make that call before any
- * stream capture. Every call shares the scratch: calls whose work overlaps on
- * the GPU race and give wrong results, so order them on one stream. */
+ * stream capture. The set-up is tied to the device's current CUDA context:
+ * after cudaDeviceReset the next call sets the scratch up again (and
+ * synchronises). Every call shares the scratch: calls whose work overlaps on
+ * the GPU race and give wrong results, so order them on one stream. On the
+ * host, calls from several threads are serialised by a lock for as long as
+ * they enqueue work; that does not order their GPU work. */
 int mond_pm_deposit_noalloc(int32_t n_f, double s, double kernel_width, int64_t N, const int32_t* cell,
                             const float* offset, const float* mass, float* rho_out, void* cuda_stream);
 

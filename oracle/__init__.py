@@ -117,6 +117,8 @@ def lib():
             L.ora_fft3_raw.argtypes = [i32, P, i32]
             L.ora_solve.restype = i32
             L.ora_solve.argtypes = [i32, f64, f64, f64, i32, i32, P, P, i32, P, P, P, P, P, P]
+            L.ora_solve_ex.restype = i32
+            L.ora_solve_ex.argtypes = [i32, f64, f64, f64, i32, i32, P, P, i32, i32, P, P, P, P, P, P]
             L.ora_solve_increment.restype = i32
             L.ora_solve_increment.argtypes = [i32, f64, f64, f64, i32, i32, P, P, P, P, P, P, P, P]
             L.ora_linearised.argtypes = [i32, i32, f64, P, P, P]
@@ -249,10 +251,12 @@ def reset_transform_count() -> None:
 
 
 def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None,
-          finish_h: bool = False, want=("gN", "H", "phi", "acc", "dH")):
+          finish_h: bool = False, want=("gN", "H", "phi", "acc", "dH"), mean_last2: bool = False):
     """Field solve (App. Flow steps 3-9). rho: [n,n,n] float64 (z,y,x).
     Returns a dict of the requested outputs (vector fields as [3,n,n,n]);
-    "gM" (not in the default) is the curl-free g_M of the last iteration."""
+    "gM" (not in the default) is the curl-free g_M of the last iteration.
+    mean_last2: the potential is the mean of the last two iterations' (the
+    midpoint of the period-2 cycle of reading R14; n_iter >= 2)."""
     rho = _c(rho, np.float64)
     n = rho.shape[0]
     out = {}
@@ -263,8 +267,9 @@ def solve(rho, s: float, G: float, a0: float, mu_kind: int, n_iter: int, H0=None
     dH = np.zeros(max(n_iter, 1)) if "dH" in want else None
     gM = np.zeros((3, n, n, n)) if ("gM" in want and n_iter > 0) else None
     H0a = None if H0 is None else _c(H0, np.float64)
-    rc = lib().ora_solve(n, float(s), float(G), float(a0), int(mu_kind), int(n_iter), _p(rho), _p(H0a),
-                         int(bool(finish_h)), _p(gN), _p(H), _p(phi), _p(acc), _p(dH), _p(gM))
+    rc = lib().ora_solve_ex(n, float(s), float(G), float(a0), int(mu_kind), int(n_iter), _p(rho), _p(H0a),
+                            int(bool(finish_h)), int(bool(mean_last2)), _p(gN), _p(H), _p(phi), _p(acc), _p(dH),
+                            _p(gM))
     if rc != 0:
         raise RuntimeError(f"oracle solve failed: {rc}")
     for k, v in (("gN", gN), ("H", H), ("phi", phi), ("acc", acc), ("dH", dH), ("gM", gM)):
@@ -434,12 +439,12 @@ def particle_diag(n: int, s: float, cell, off, vel, mass):
 
 
 def step(n: int, s: float, G: float, a0: float, mu_kind: int, sigma: float, n_iter: int, dt: float,
-         cell, off, vel, mass, H0=None, finish_h: bool = False):
+         cell, off, vel, mass, H0=None, finish_h: bool = False, mean_last2: bool = False):
     """One time step in the order deposit -> solve -> gather -> kick -> drift.
     Returns (cell, off float64, vel float64, g, fields dict, kacc)."""
     acc, ka, _ = deposit_fixed(n, sigma, cell, off, mass)
     _, rho64 = acc_to_rho(acc, ka, s)
-    f = solve(rho64, s, G, a0, mu_kind, n_iter, H0=H0, finish_h=finish_h)
+    f = solve(rho64, s, G, a0, mu_kind, n_iter, H0=H0, finish_h=finish_h, mean_last2=mean_last2)
     g = gather(sigma, f["acc"], cell, off)
     c2, o2, v2 = push(n, s, dt, g, cell, np.asarray(off, np.float64), vel)
     return c2, o2, v2, g, f, ka

@@ -489,9 +489,24 @@ static void fd_grad(int n, double s, const double* f, double* g /* 3 planes */) 
  * linearised about).
  * For K = 0 the potential is phi_N and acc = g_N.
  */
+int ora_solve_ex(int n, double s, double G, double a0, int mu_kind, int n_iter, const double* rho,
+                 const double* H0, int finish_h, int mean_last2, double* gN_out, double* H_out, double* phi_out,
+                 double* acc_out, double* dH_out, double* gM_out);
+
 int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, const double* rho,
               const double* H0, int finish_h, double* gN_out, double* H_out, double* phi_out,
               double* acc_out, double* dH_out, double* gM_out) {
+  return ora_solve_ex(n, s, G, a0, mu_kind, n_iter, rho, H0, finish_h, 0, gN_out, H_out, phi_out, acc_out, dH_out,
+                      gM_out);
+}
+
+/* As ora_solve; with mean_last2 != 0 and n_iter >= 2 the potential of step 9
+ * is the mean of the potentials of the last two iterations' curl-free steps,
+ * phi^ = (phi^_{K-1} + phi^_K) / 2: the midpoint of the period-2 cycle the
+ * iteration enters near zeros of the field (reading R14). */
+int ora_solve_ex(int n, double s, double G, double a0, int mu_kind, int n_iter, const double* rho,
+                 const double* H0, int finish_h, int mean_last2, double* gN_out, double* H_out, double* phi_out,
+                 double* acc_out, double* dH_out, double* gM_out) {
   int64_t tot = (int64_t)n * n * n;
   cplx* c1 = (cplx*)malloc(sizeof(cplx) * tot);       /* scalar spectrum */
   cplx* cv = (cplx*)malloc(sizeof(cplx) * 3 * tot);   /* vector spectrum */
@@ -501,7 +516,9 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
   double* V = (double*)malloc(sizeof(double) * 3 * tot); /* F, then g_M */
   double* phi = (double*)malloc(sizeof(double) * tot);
   cplx* phih = (cplx*)malloc(sizeof(cplx) * tot);
-  if (!c1 || !cv || !gN || !H || !Hprev || !V || !phi || !phih) return ORA_ENOMEM;
+  cplx* phih_prev = (mean_last2 && n_iter >= 2) ? (cplx*)malloc(sizeof(cplx) * tot) : NULL;
+  if (!c1 || !cv || !gN || !H || !Hprev || !V || !phi || !phih || (mean_last2 && n_iter >= 2 && !phih_prev))
+    return ORA_ENOMEM;
 
   /* step 3: rho^ = F(rho) */
   for (int64_t j = 0; j < tot; j++) c1[j] = rho[j];
@@ -564,6 +581,7 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
           phih[j] = ph;
           for (int a = 0; a < 3; a++) cv[a * tot + j] = -I * k[a] * ph;
         }
+    if (phih_prev && it == n_iter - 1) memcpy(phih_prev, phih, sizeof(cplx) * tot);
     if (it == n_iter && !finish_h) {
       if (dH_out) dH_out[it - 1] = NAN;
       if (gM_out)
@@ -609,6 +627,8 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
       dH_out[it - 1] = den > 0 ? sqrt(num / den) : 0.0;
     }
   }
+  if (phih_prev)
+    for (int64_t j = 0; j < tot; j++) phih[j] = 0.5 * (phih[j] + phih_prev[j]);
   /* step 9: phi = F^-1(phi^); acceleration mesh = -grad_FD phi (Sect. 3.2) */
   inv3_real(n, s, phih, phi);
   if (acc_out) {
@@ -618,7 +638,7 @@ int ora_solve(int n, double s, double G, double a0, int mu_kind, int n_iter, con
   if (gN_out) memcpy(gN_out, gN, sizeof(double) * 3 * tot);
   if (H_out) memcpy(H_out, H, sizeof(double) * 3 * tot);
   if (phi_out) memcpy(phi_out, phi, sizeof(double) * tot);
-  free(c1); free(cv); free(gN); free(H); free(Hprev); free(V); free(phi); free(phih);
+  free(c1); free(cv); free(gN); free(H); free(Hprev); free(V); free(phi); free(phih); free(phih_prev);
   return ORA_OK;
 }
 
@@ -1071,6 +1091,7 @@ static void aq_grad(int n, double s, const double* phi, double* u, cplx* c, cplx
   for (int64_t j = 0; j < tot; j++) c[j] = phi[j];
   fwd3(n, s, c);
   for (int a = 0; a < 3; a++) {
+#pragma omp parallel for
     for (int l = 0; l < n; l++)
       for (int jy = 0; jy < n; jy++)
         for (int i = 0; i < n; i++) {
@@ -1090,6 +1111,7 @@ static void aq_gradT(int n, double s, const double* w, double* out, cplx* c, cpl
   for (int a = 0; a < 3; a++) {
     for (int64_t j = 0; j < tot; j++) c[j] = w[a * tot + j];
     fwd3(n, s, c);
+#pragma omp parallel for
     for (int l = 0; l < n; l++)
       for (int jy = 0; jy < n; jy++)
         for (int i = 0; i < n; i++) {
@@ -1107,6 +1129,7 @@ static void aq_precond(int n, double s, const double* g, double* out, cplx* c) {
   int64_t tot = (int64_t)n * n * n;
   for (int64_t j = 0; j < tot; j++) c[j] = g[j];
   fwd3(n, s, c);
+#pragma omp parallel for
   for (int l = 0; l < n; l++)
     for (int jy = 0; jy < n; jy++)
       for (int i = 0; i < n; i++) {
@@ -1132,9 +1155,23 @@ static inline void aq_add(aq_sum* a, double v) {
   a->s = t;
 }
 
+/* Sum of a[j] b[j] over m = n^3 terms: compensated partial sums per plane
+ * (in parallel), combined in plane order, so that the result does not depend
+ * on the number of threads. */
 static double aq_dot(int64_t m, const double* a, const double* b) {
+  int64_t nz = 1;
+  while (nz * nz * nz < m) nz++;
+  int64_t per = m / nz;
+  double* part = (double*)malloc(sizeof(double) * (size_t)nz);
+#pragma omp parallel for
+  for (int64_t z = 0; z < nz; z++) {
+    aq_sum t = {0, 0};
+    for (int64_t j = z * per; j < (z + 1) * per; j++) aq_add(&t, a[j] * b[j]);
+    part[z] = t.s + t.c;
+  }
   aq_sum t = {0, 0};
-  for (int64_t j = 0; j < m; j++) aq_add(&t, a[j] * b[j]);
+  for (int64_t z = 0; z < nz; z++) aq_add(&t, part[z]);
+  free(part);
   return t.s + t.c;
 }
 
@@ -1143,18 +1180,27 @@ static double aq_energy(int n, double s, double a0, int kind, const double* gN, 
                         double* u, double* w, cplx* c, cplx* c2) {
   int64_t tot = (int64_t)n * n * n;
   aq_grad(n, s, phi, u, c, c2);
-  aq_sum e = {0, 0};
-  for (int64_t j = 0; j < tot; j++) {
-    double um = 0;
-    for (int a = 0; a < 3; a++) {
-      um += u[a * tot + j] * u[a * tot + j];
-      aq_add(&e, gN[a * tot + j] * u[a * tot + j]);
+  const int64_t plane = (int64_t)n * n;
+  double* part = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp parallel for
+  for (int z = 0; z < n; z++) {
+    aq_sum e = {0, 0};
+    for (int64_t j = z * plane; j < (z + 1) * plane; j++) {
+      double um = 0;
+      for (int a = 0; a < 3; a++) {
+        um += u[a * tot + j] * u[a * tot + j];
+        aq_add(&e, gN[a * tot + j] * u[a * tot + j]);
+      }
+      um = sqrt(um);
+      aq_add(&e, a0 * a0 * psi_mu(kind, um / a0));
+      double m = ora_mu(kind, um / a0);
+      for (int a = 0; a < 3; a++) w[a * tot + j] = m * u[a * tot + j] + gN[a * tot + j];
     }
-    um = sqrt(um);
-    aq_add(&e, a0 * a0 * psi_mu(kind, um / a0));
-    double m = ora_mu(kind, um / a0);
-    for (int a = 0; a < 3; a++) w[a * tot + j] = m * u[a * tot + j] + gN[a * tot + j];
+    part[z] = e.s + e.c;
   }
+  aq_sum e = {0, 0};
+  for (int z = 0; z < n; z++) aq_add(&e, part[z]);
+  free(part);
   aq_gradT(n, s, w, grad, c, c2);
   return e.s + e.c;
 }
@@ -1194,6 +1240,7 @@ int ora_aqual_solve(int n, double s, double G, double a0, int mu_kind, const dou
     for (int t = 0; t < m; t++) {
       int b = (head - 1 - t + AQ_M) % AQ_M;
       alpha[b] = rho_k[b] * aq_dot(tot, S + b * tot, q);
+#pragma omp parallel for
       for (int64_t j = 0; j < tot; j++) q[j] -= alpha[b] * Y[b * tot + j];
     }
     aq_precond(n, s, q, z, c);
@@ -1201,11 +1248,13 @@ int ora_aqual_solve(int n, double s, double G, double a0, int mu_kind, const dou
       int b = (head - 1 + AQ_M) % AQ_M;
       aq_precond(n, s, Y + b * tot, xn, c);
       double gam = aq_dot(tot, S + b * tot, Y + b * tot) / aq_dot(tot, Y + b * tot, xn);
+#pragma omp parallel for
       for (int64_t j = 0; j < tot; j++) z[j] *= gam;
     }
     for (int t = m - 1; t >= 0; t--) {
       int b = (head - 1 - t + AQ_M) % AQ_M;
       double beta = rho_k[b] * aq_dot(tot, Y + b * tot, z);
+#pragma omp parallel for
       for (int64_t j = 0; j < tot; j++) z[j] += S[b * tot + j] * (alpha[b] - beta);
     }
     /* direction -z; backtracking until E falls by the Armijo fraction */
@@ -1213,6 +1262,7 @@ int ora_aqual_solve(int n, double s, double G, double a0, int mu_kind, const dou
     int ok = 0;
     if (gd < 0) {
       for (int tries = 0; tries < 30; tries++, step *= 0.5) {
+#pragma omp parallel for
         for (int64_t j = 0; j < tot; j++) xn[j] = x[j] - step * z[j];
         en = aq_energy(n, s, a0, mu_kind, gN, xn, gn, u, w, c, c2);
         evals++;
@@ -1224,6 +1274,7 @@ int ora_aqual_solve(int n, double s, double G, double a0, int mu_kind, const dou
     }
     if (!ok) break; /* E can no longer be lowered at this precision */
     double sy = 0;
+#pragma omp parallel for
     for (int64_t j = 0; j < tot; j++) {
       S[head * tot + j] = xn[j] - x[j];
       Y[head * tot + j] = gn[j] - g[j];

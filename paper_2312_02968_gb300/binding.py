@@ -18,6 +18,8 @@ WARM_NONE, WARM_PREV, WARM_GUESS, WARM_GUESS_RAW, WARM_INCREMENT = 0, 1, 2, 3, 4
 FIELD_RHO, FIELD_GN, FIELD_H, FIELD_PHI, FIELD_ACC, FIELD_SMOOTH, FIELD_GM = 0, 1, 2, 3, 4, 5, 6
 DENS_BARYONIC, DENS_APPARENT, DENS_PHANTOM = 0, 1, 2
 OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK, OPT_GATHER = 1, 2, 3, 4, 5, 6, 7
+OPT_TEST_LOST_LOAD = 8  # tests of the bounded device waits only
+OPT_CYCLE_MEAN = 9
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
 

@@ -303,6 +303,8 @@ struct mond_pm {
   bool inc_valid = false;  // the base (dep0, gN, Hs, gM0, acc) is that of the last solve
   int inc_kacc = 0, inc_gather = 0, inc_keep_phi = 0;
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
+  int lost_tile = -1;  // MOND_OPT_TEST_LOST_LOAD: tile of the next pipelined y-pass whose copy is not issued
+  int cycle_mean = 0;  // MOND_OPT_CYCLE_MEAN
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
   // mond_pm_step for the key below, replayed with one cudaGraphLaunch
@@ -314,11 +316,12 @@ struct mond_pm {
     int64_t N;
     const void* cell;
     const void* inc;
+    int cycle_mean;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
              track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
              gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
-             cell == o.cell && inc == o.inc;
+             cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -442,6 +445,8 @@ cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
     p.ncomp = ncomp;
     p.tw = h->w.tw;
     p.status = h->w.status;
+    p.lost_tile = h->lost_tile;  // fault injection of the bounded-wait tests (one-shot)
+    h->lost_tile = -1;
     const tma::TensorMap& m = spec == h->w.W ? h->map_wy : h->map_ay;
     Timed tm(h, dir < 0 ? KC_Y_FWD : KC_Y_INV, 2.0 * ncomp * spec_bytes(h));
     switch (h->nf) {
@@ -466,7 +471,7 @@ cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
+cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout, int mean = 0) {
   passes::ZArgs a{};
   a.in = in;
   a.out = out;
@@ -481,7 +486,8 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
   a.coef = (float)(4.0 * M_PI * h->G);
   int nin = (mode == passes::Z_NEWTON) ? 1 : 3;
   int nwr = (mode == passes::Z_NEWTON || mode == passes::Z_FINAL) ? nout : 3;
-  double zb = (nin + nwr) * spec_bytes(h) + (a.khat && mode != passes::Z_NEWTON ? 0.5 * real_bytes(h) : 0.0);
+  double zb = (nin + nwr) * spec_bytes(h) + (a.khat && mode != passes::Z_NEWTON ? 0.5 * real_bytes(h) : 0.0) +
+              (mean ? spec_bytes(h) : 0.0);  // the kept potential, written (Z_CURL) or read (Z_FINAL)
   int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : mode == passes::Z_DIV ? KC_Z_DIV
            : mode == passes::Z_FINAL ? KC_Z_FINAL : KC_Z_SMOOTH;
   Timed tm(h, zc, zb);
@@ -495,6 +501,7 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
     p.norm = a.norm;
     p.coef = a.coef;
     p.status = h->w.status;
+    p.mean = mean;
     // input: rho^ (component 0 of W) for Newton, else three components;
     // output: three components, phi^ separately as component 3 of A
     const tma::TensorMap& mi =
@@ -508,6 +515,7 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout) {
     }
     return cudaErrorInvalidValue;
   }
+  if (mean) return cudaErrorInvalidValue;  // the mean of the last two iterations needs the pipelined passes
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_zpass_##k(mode, a, h->st);
@@ -528,6 +536,11 @@ int read_status(mond_pm* h) {
   CK(cudaMemcpyAsync(&st, h->w.status, sizeof st, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   if (st) CK(cudaMemsetAsync(h->w.status, 0, sizeof(uint32_t), h->st));
+  if (st & (ST_TIMEOUT | ST_NAN)) {
+    // the fields of the work since the last check are not to be reused
+    h->gn_valid = false;
+    h->inc_valid = false;
+  }
   if (st & ST_TIMEOUT) return fail(h, MOND_ETIMEOUT, "a bounded device wait gave up");
   if (st & ST_NAN) return fail(h, MOND_ENAN, "a non-finite value appeared in a field or a particle");
   if (st & ST_DOMAIN) return fail(h, MOND_EDOMAIN, "a particle's cell or offset was outside the domain and was skipped");
@@ -734,6 +747,9 @@ int ensure_khat(mond_pm* h) {
 // Field solve: the pass sequence of the iteration (see mond_pm_solve_field).
 int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   const int nout = h->keep_phi ? 4 : 3;
+  // MOND_OPT_CYCLE_MEAN: the final potential is the mean of the last two iterations'
+  const bool mean2 = h->cycle_mean && K >= 2;
+  if (mean2 && !h->pipelined) return fail(h, MOND_ESTATE, "MOND_OPT_CYCLE_MEAN needs MOND_OPT_PIPELINED 1");
   float2* W = h->w.W;
   float2* A = h->w.A;
   // with an increment workspace, a solve also leaves the base of the next
@@ -828,7 +844,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
         int rk = ensure_khat(h);
         if (rk) return rk;
       }
-      PK(zpass(h, passes::Z_FINAL, W, A, nout));
+      PK(zpass(h, passes::Z_FINAL, W, A, nout, mean2 ? 2 : 0));
       PK(ypass(h, +1, A, nout));
       passes::XArgs xi{};
       xi.ncomp = nout;
@@ -838,7 +854,9 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       h->acc_smoothed = h->gather_mode != 0;
       if ((warm == MOND_WARM_NONE || warm == MOND_WARM_GUESS_RAW) && !base) break;  // no H state to carry on
     }
-    PK(zpass(h, passes::Z_CURL, W, W, 3));
+    // with the mean of the last two iterations, the curl-free step before the
+    // last keeps its potential in the scalar slot of A (unused until Z_FINAL)
+    PK(zpass(h, passes::Z_CURL, W, W, 3, (mean2 && j == K - 1) ? 1 : 0));
     PK(ypass(h, +1, W, 3));
     passes::XArgs xm{};
     xm.ncomp = 3;
@@ -1185,6 +1203,15 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_PIPELINED:
       h->pipelined = value ? 1 : 0;
       return MOND_OK;
+    case MOND_OPT_CYCLE_MEAN:
+      h->cycle_mean = value ? 1 : 0;
+      return MOND_OK;
+    case MOND_OPT_TEST_LOST_LOAD:
+      if (value < 0 || value > (1 << 30)) return fail(h, MOND_EINVAL, "lost-load tile out of range");
+      if (value && (h->use_graph || !h->pipelined))
+        return fail(h, MOND_ESTATE, "the lost-load test needs MOND_OPT_PIPELINED 1 and MOND_OPT_USE_GRAPH 0");
+      h->lost_tile = (int)value - 1;
+      return MOND_OK;
     case MOND_OPT_GATHER:
       if (value != 0 && value != 1 && value != 3) return fail(h, MOND_EINVAL, "gather variant must be 0, 1 or 3");
       h->gather_mode = (int)value;
@@ -1389,7 +1416,7 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   if (rc) return rc;
   const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
                               h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell,
-                              h->inc.dep0};
+                              h->inc.dep0, h->cycle_mean};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);

@@ -756,14 +756,26 @@ struct PipeCfg {
   static constexpr int NBLKZ = (NX + PZ - 1) / PZ;
 };
 
+// Polls after which the wait for a tile whose load was never issued gives
+// up (the fault-injection hook below).
+constexpr uint32_t kLostLoadWaitLimit = 1024;
+
 struct PipeYArgs {
   int ncomp;  // components to transform (tiles = NBLKY * N * ncomp)
   const float2* tw;
   uint32_t* status;
+  // Fault injection for tests of the bounded waits: the load of this tile is
+  // never issued, so its wait runs out (-1: none).
+  int lost_tile = -1;
 };
 
 struct PipeZArgs {
   int nout;  // Z_NEWTON / Z_FINAL outputs (3 or 4)
+  // mean of the last two iterations' potentials: 1 = this Z_CURL also writes
+  // its A k'.g (the potential's spectrum over i, before the inverse z
+  // transform) to the scalar slot of the final spectra; 2 = this Z_FINAL
+  // reads it back and takes the mean with its own. Needs the scalar region.
+  int mean;
   const float* kv;
   const float* kp;
   const float2* tw;
@@ -776,10 +788,14 @@ struct PipeZArgs {
 // Common ring driver. LoadF(tile, stage_ptr, bar) issues the loads of a tile
 // and returns the bytes expected; ComputeF(tile, stage_ptr) transforms it in
 // place; StoreF(tile, stage_ptr) issues its stores (called by thread 0 after
-// the proxy fence). Returns false when a bounded wait gave up.
+// the proxy fence). When a bounded wait gives up, the CTA waits (bounded, at
+// the full limit) for the one load it has issued into the other stage, so that
+// no copy into its shared memory is in flight when it leaves, and stops.
+// lost_tile (tests only): that tile's load is not issued and its wait gives
+// up after kLostLoadWaitLimit polls; every other wait keeps the full limit.
 template <typename LoadF, typename ComputeF, typename StoreF>
 __device__ __forceinline__ void pipe_run(int ntiles, float2* stage0, int stage_elems, uint64_t* bars, uint32_t* status,
-                                         LoadF load, ComputeF compute, StoreF store) {
+                                         LoadF load, ComputeF compute, StoreF store, int lost_tile = -1) {
   const int tid = threadIdx.x;
   const int cnt = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (tid == 0) {
@@ -788,7 +804,7 @@ __device__ __forceinline__ void pipe_run(int ntiles, float2* stage0, int stage_e
     tma::fence_barrier_init();
   }
   __syncthreads();
-  if (tid == 0 && cnt > 0) {
+  if (tid == 0 && cnt > 0 && (int)blockIdx.x != lost_tile) {
     const uint32_t bytes = load(blockIdx.x, stage0, &bars[0]);
     (void)bytes;
   }
@@ -798,9 +814,10 @@ __device__ __forceinline__ void pipe_run(int ntiles, float2* stage0, int stage_e
     const int tile = blockIdx.x + i * gridDim.x;
     if (tid == 0 && i + 1 < cnt) {
       tma::bulk_wait_read<0>();  // the other stage's store has finished reading it
-      load(tile + gridDim.x, stage0 + (s ^ 1) * stage_elems, &bars[s ^ 1]);
+      if (tile + (int)gridDim.x != lost_tile) load(tile + gridDim.x, stage0 + (s ^ 1) * stage_elems, &bars[s ^ 1]);
     }
-    const bool ok = tma::mbar_wait(&bars[s], (uint32_t)((i >> 1) & 1), status);
+    const bool ok = tma::mbar_wait(&bars[s], (uint32_t)((i >> 1) & 1), status,
+                                   tile == lost_tile ? kLostLoadWaitLimit : tma::kWaitLimit);
     if (__syncthreads_or(!ok)) {
       // give up: wait (bounded) for the load already issued into the other stage
       if (tid == 0 && i + 1 < cnt) tma::mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1), status);
@@ -850,7 +867,7 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(const __grid_constant__ tma::
     coords(t, x, zz);
     for (int b = 0; b < C::NBOX; b++) tma::store_3d(&map, x, b * C::BOX, zz, src + b * C::BOX * P);
   };
-  pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
+  pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store, a.lost_tile);
 }
 
 // z-pass over the tile of (column block, y): forward z, the spectral
@@ -891,6 +908,8 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
     kp[i] = a.kp[i];
   }
   const int ntiles = C::NBLKZ * N;
+  const bool mean_in = SC && MODE == Z_FINAL && a.mean == 2;   // previous potential read back
+  const bool mean_out = SC && MODE == Z_CURL && a.mean == 1;   // this iteration's potential kept
   auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
     const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
     if constexpr (MODE == Z_NEWTON) {
@@ -899,9 +918,13 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
         tma::load_4d(dst + SOFF + b * C::BOX * P, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
       return N * P * 8;
     } else {
-      tma::mbar_expect_tx(bar, 3 * N * P * 8);
+      const uint32_t bytes = (mean_in ? 4 : 3) * N * P * 8;
+      tma::mbar_expect_tx(bar, bytes);
       for (int b = 0; b < C::NBOX; b++) tma::load_4d(dst + b * C::BOX * VP, &in_map, blk * 2 * P, 0, y, b * C::BOX, bar);
-      return 3 * N * P * 8;
+      if (mean_in)
+        for (int b = 0; b < C::NBOX; b++)
+          tma::load_4d(dst + SOFF + b * C::BOX * P, &phi_map, blk * 2 * P, 3, y, b * C::BOX, bar);
+      return bytes;
     }
   };
   auto compute = [&](int t, float2* st) {
@@ -957,7 +980,8 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
           float2 S = make_float2(0.f, 0.f);
           for (int b = 0; b < 3; b++)
             if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
-          const float2 aS = cscale(S, A * a.norm);
+          float2 aS = cscale(S, A * a.norm);
+          if (mean_in) aS = cscale(cadd(aS, *sc), 0.5f);  // the midpoint of the last two iterations
           // times the smoothing spectrum when the mesh is to hold the node-smoothed field
           const float fk = a.khat ? a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] : 1.0f;
           const float2 aK = cscale(aS, fk);
@@ -966,6 +990,13 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
           v[2 * P] = cscale(aK, kp[row]);
           if constexpr (SC) *sc = cmul_i<1>(aS);
         } else {
+          if (mean_out) {
+            // the potential this curl-free step implies, as Z_FINAL forms it: A sum_b k'_b g_b
+            float2 S = make_float2(0.f, 0.f);
+            for (int b = 0; b < 3; b++)
+              if (!n3[b]) S = cadd(S, cscale(gg[b], k3[b]));
+            *sc = cscale(S, A * a.norm);
+          }
           // P_ab = k_a k_b A, off-diagonal terms dropped when exactly one of a, b is on its Nyquist plane
           for (int aa = 0; aa < 3; aa++) {
             float2 acc = make_float2(0.f, 0.f);
@@ -984,7 +1015,7 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
     const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
     const tma::TensorMap* m = SCALAR ? &out_map : &in_map;
     for (int b = 0; b < C::NBOX; b++) tma::store_4d(m, blk * 2 * P, 0, y, b * C::BOX, src + b * C::BOX * VP);
-    if (phi)
+    if (phi || mean_out)
       for (int b = 0; b < C::NBOX; b++)
         tma::store_4d(&phi_map, blk * 2 * P, 3, y, b * C::BOX, src + N * VP + b * C::BOX * P);
   };

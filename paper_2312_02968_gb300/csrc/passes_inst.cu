@@ -117,8 +117,11 @@ cudaError_t launch_zpipe_sc(const tma::TensorMap& in, const tma::TensorMap& out,
 template <int MODE>
 cudaError_t launch_zpipe(const tma::TensorMap& in, const tma::TensorMap& out, const tma::TensorMap& phi,
                          const PipeZArgs& a, cudaStream_t st) {
-  // a separate scalar region only when the potential is stored
-  if ((MODE == Z_NEWTON || MODE == Z_FINAL) && a.nout > 3) return launch_zpipe_sc<MODE, true>(in, out, phi, a, st);
+  // a separate scalar region only when the potential is stored, or kept for
+  // the mean of the last two iterations
+  if constexpr (MODE == Z_NEWTON || MODE == Z_FINAL || MODE == Z_CURL) {
+    if (((MODE != Z_CURL) && a.nout > 3) || a.mean) return launch_zpipe_sc<MODE, true>(in, out, phi, a, st);
+  }
   return launch_zpipe_sc<MODE, false>(in, out, phi, a, st);
 }
 }  // namespace

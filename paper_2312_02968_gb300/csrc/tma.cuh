@@ -70,10 +70,12 @@ __device__ __forceinline__ void async_copy4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+// Wait for the phase with the given parity to complete; false on timeout
+// (after `limit` polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status,
+                                          uint32_t limit = kWaitLimit) {
   const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < kWaitLimit; it++) {
+  for (uint32_t it = 0; it < limit; it++) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -150,3 +150,42 @@ def test_resume_from_checkpoint_is_bit_identical(B, warm):
     for a, b in zip(full, [x.cpu().numpy() for x in t2[:3]]):
         assert np.array_equal(a, b)
     h2.close()
+
+
+@pytest.mark.parametrize("tile", [0, 400])
+def test_lost_tile_copy_times_out_and_the_handle_recovers(B, tile):
+    """A bounded device wait that runs out, made without a fault: the test
+    hook keeps one tile copy of the next pipelined y-pass from being issued
+    (tile 0: the first copy of a CTA; tile 400 of 640 on 128^3: a later one,
+    with the CTA's next copy already in flight, which it waits for before it
+    stops). The wait for the lost copy gives up after a short bound, the
+    solve's next synchronising call reports MOND_ETIMEOUT, and the next solve
+    on the same handle matches the oracle."""
+    import time
+
+    n = 128
+    p = W.isothermal(n, 1.0, 20000, 4.0, 40.0, seed=8)
+    h, _ = make(B, n, p)
+    h.deposit()
+    h.solve_field(2)
+    h.sync()
+    with pytest.raises(B.MondError):
+        h.set_option(B.OPT_USE_GRAPH, 1)
+        h.set_option(B.OPT_TEST_LOST_LOAD, tile + 1)  # not with graph replay
+    h.set_option(B.OPT_USE_GRAPH, 0)
+    h.set_option(B.OPT_TEST_LOST_LOAD, tile + 1)
+    t0 = time.perf_counter()
+    h.deposit()
+    h.solve_field(2)
+    with pytest.raises(B.MondError) as e:
+        h.sync()
+    assert e.value.code == -7  # MOND_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    # the hook was one-shot and the status was read and cleared
+    h.deposit()
+    h.solve_field(2)
+    a = h.get_field(B.FIELD_ACC).cpu().numpy()
+    rho = h.get_field(B.FIELD_RHO).cpu().numpy().astype(np.float64)
+    ref = oracle.solve(rho, 1.0, 1.0, 1.0, 0, 2, want=("acc",))["acc"]
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 1e-5
+    h.close()

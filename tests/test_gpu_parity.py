@@ -363,3 +363,37 @@ def test_pipelined_passes_match_unpipelined(B, n, mu, K):
         out.append(f)
     for a, b in zip(out[0], out[1]):
         assert rel(a.numpy(), b.numpy()) < TOL
+
+
+@pytest.mark.parametrize("n,mu,K,keep_phi,warm", [(32, 0, 2, 1, False), (64, 0, 4, 0, False), (48, 2, 3, 1, False),
+                                                  (32, 0, 2, 1, True), (128, 0, 4, 0, False)])
+def test_cycle_mean_matches_oracle(B, n, mu, K, keep_phi, warm):
+    """MOND_OPT_CYCLE_MEAN: the potential is the mean of the last two
+    iterations' (the midpoint of the period-2 cycle of reading R14), the
+    oracle's mean_last2, for plain and previous-H warm-started solves, with
+    and without the potential plane; 128^3 spans several z-pass tiles."""
+    p = W.isothermal(n, 1.0, 6000, n / 12, 0.4 * n, seed=n + 3 * K)
+    sigma = 1.5
+    h, _ = make(B, n, 1, p, sigma, mu=mu, a0=1.0 if mu == 0 else 0.05)
+    h.set_option(B.OPT_KEEP_PHI, keep_phi)
+    h.set_option(B.OPT_CYCLE_MEAN, 1)
+    h.deposit()
+    H0 = None
+    if warm:
+        h.solve_field(3)
+        H0 = h.get_field(B.FIELD_H).cpu().numpy().astype(np.float64)
+        h.solve_field(K, B.WARM_PREV)
+    else:
+        h.solve_field(K)
+    acc, ka, _ = oracle.deposit_fixed(n, sigma, p["cell"], p["offset"], p["mass"])
+    rho = oracle.acc_to_rho(acc, ka, 1.0)[0].astype(np.float64)
+    ref = oracle.solve(rho, 1.0, 1.0, 1.0 if mu == 0 else 0.05, mu, K, H0=H0, finish_h=warm, mean_last2=True)
+    assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), ref["acc"]) < TOL
+    if keep_phi:
+        assert rel(h.get_field(B.FIELD_PHI).cpu().numpy(), ref["phi"]) < TOL
+    plain = oracle.solve(rho, 1.0, 1.0, 1.0 if mu == 0 else 0.05, mu, K, H0=H0, finish_h=warm, want=("acc",))
+    assert rel(plain["acc"], ref["acc"]) > 10 * TOL  # the option changes the result
+    if not warm:  # off again: the plain solve
+        h.set_option(B.OPT_CYCLE_MEAN, 0)
+        h.solve_field(K)
+        assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), plain["acc"]) < TOL
