@@ -390,6 +390,16 @@ int64_t mond_pm_kernel_launches(mond_pm_t h);
  * statistics. Synchronises. */
 int mond_pm_kernel_stats(mond_pm_t h, mond_pm_kstat* out, int cap, int* count);
 
+/* A measurement of the device, not a step of the method: the throughput of
+ * no-return shared-memory atomic adds of `bits` = 32 or 64 bits, each thread
+ * of a full grid (every SM at its occupancy) adding to its own words of
+ * shared memory (no bank conflicts, no contention). The deposit accumulates
+ * its tiles with such adds (two 32-bit adds per tap), so this is the peak of
+ * its roofline. Runs on cuda_stream and synchronises it; writes adds per
+ * second to *adds_per_s. MOND_EINVAL for other widths, MOND_ECUDA on a CUDA
+ * error. */
+int mond_pm_probe_smem_atomics(int bits, void* cuda_stream, double* adds_per_s);
+
 /* Mass deposit for callers that cannot allocate device memory.
  * The paper has no counterpart; this entry point exists because some callers
  * cannot call cudaMalloc (a host framework that owns every device

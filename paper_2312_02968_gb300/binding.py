@@ -76,6 +76,7 @@ SIGNATURES = {
     "mond_pm_kernel_launches": (_I64, [_P]),
     "mond_pm_kernel_stats": (_I, [_P, ctypes.POINTER(KStat), _I, ctypes.POINTER(_I)]),
     "mond_pm_deposit_noalloc": (_I, [ctypes.c_int32, _D, _D, _I64, _P, _P, _P, _P, _P]),
+    "mond_pm_probe_smem_atomics": (_I, [_I, _P, ctypes.POINTER(_D)]),
     "mond_pm_batch_create": (_I, [_I, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
     "mond_pm_batch_step": (_I, [_P, _D, _I, _I, _I]),
     "mond_pm_batch_sync": (_I, [_P]),
@@ -155,6 +156,19 @@ def deposit_noalloc(n_f: int, s: float, kernel_width: float, cell, offset, mass,
                                        _ptr(offset), _ptr(mass), _ptr(rho_out), ctypes.c_void_p(st.cuda_stream))
     if rc != 0:
         raise MondError(rc, lib().mond_pm_last_error(None).decode())
+
+
+def probe_smem_atomics(bits: int = 32, stream=None) -> float:
+    """Measured no-return shared-memory atomic adds per second on the current
+    device (the deposit's roofline peak); a measurement, not the method."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    rc = lib().mond_pm_probe_smem_atomics(int(bits), ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    if rc != 0:
+        raise MondError(rc, "shared-memory atomic probe failed")
+    return out.value
 
 
 class MondPM:

@@ -52,7 +52,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "deposit_noalloc.cu"), "-o",
                                       os.path.join(OUT, "deposit_noalloc.o")], os.path.join(OUT, "deposit_noalloc.o")),
             ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "fno.cu"), "-o", os.path.join(OUT, "fno.o")],
-             os.path.join(OUT, "fno.o"))]
+             os.path.join(OUT, "fno.o")),
+            ([nvcc] + ARCH + FLAGS + ["-c", os.path.join(SRC, "probe.cu"), "-o", os.path.join(OUT, "probe.o")],
+             os.path.join(OUT, "probe.o"))]
     for n in SIZES:
         o = os.path.join(OUT, f"passes_{n}.o")
         jobs.append(([nvcc] + ARCH + FLAGS + [f"-DMOND_N={n}", "-c", os.path.join(SRC, "passes_inst.cu"), "-o", o], o))

@@ -7,6 +7,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Under pytest-xdist every worker loads its own copy of the oracle's OpenMP
+# runtime; give each its share of the cores (before the library is loaded), or
+# the spinning thread teams oversubscribe the host many times over.
+if os.environ.get("PYTEST_XDIST_WORKER"):
+    _workers = int(os.environ.get("PYTEST_XDIST_WORKER_COUNT", "1"))
+    os.environ.setdefault("OMP_NUM_THREADS", str(max(1, (os.cpu_count() or 1) // max(1, _workers))))
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
