@@ -585,6 +585,41 @@ def run_scan(dev, steps):
     return rows
 
 
+def run_cufft(dev, stream, steps, transforms_ms_per_solve):
+    """Timing-only comparator, off the product path: cuFFT (through torch.fft)
+    real-to-complex and complex-to-real 3-D transforms of three 256^3 planes,
+    the work of one vector transform of the solve, and the 42 scalar
+    transforms of a K = 4 solve at that rate, beside the library's own
+    passes (which also carry the fused pointwise steps and operators)."""
+    import torch
+
+    n = WL["n"] * WL["pad"]
+    x = torch.randn(3, n, n, n, device=dev)
+    X = torch.fft.rfftn(x, dim=(1, 2, 3))
+    for _ in range(3):
+        X = torch.fft.rfftn(x, dim=(1, 2, 3))
+        y = torch.fft.irfftn(X, s=(n, n, n), dim=(1, 2, 3))
+    res = {}
+    for name, fn in (("r2c", lambda: torch.fft.rfftn(x, dim=(1, 2, 3))),
+                     ("c2r", lambda: torch.fft.irfftn(X, s=(n, n, n), dim=(1, 2, 3)))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps / 3.0
+        res[name] = {"ms_per_scalar_transform": ms,
+                     "GBps_one_round_trip": (4 * n ** 3 + 8 * n * n * (n // 2 + 1)) / (ms / 1e3) / 1e9}
+    del x, X, y
+    res["ms_42_transforms"] = 21 * (res["r2c"]["ms_per_scalar_transform"] + res["c2r"]["ms_per_scalar_transform"])
+    res["library_passes_ms_per_solve"] = transforms_ms_per_solve
+    res["note"] = ("cuFFT through torch.fft on the bench's stream, unfused: the 42 transforms alone, without the "
+                   "pointwise nu/mu steps and spectral operators the library's passes fuse into them")
+    return res
+
+
 def run_configs(dev):
     """The other configurations as side lines (not the headline): the two-body
     test (64^3 in a zero-padded 128^3 domain, simple mu, sigma 2 px, K = 4,
@@ -616,7 +651,9 @@ def run_configs(dev):
         h.bind_particles(*t)
         h.deposit()
         h.solve_field(4)
-        g = h.gather().double().cpu().numpy()
+        gt = h.gather()
+        h.sync()  # the force tensor is read on another stream
+        g = gt.double().cpu().numpy()
         h.set_option(B.OPT_USE_GRAPH, 1)
         for _ in range(3):
             h.step(c["dt"], 4, B.WARM_NONE)
@@ -994,6 +1031,8 @@ def main():
     if rank == 0 and args.scan:
         scan = optional(run_scan, dev, args.steps)
     configs = optional(run_configs, dev) if rank == 0 and args.configs else None
+    passes_ms = sum(x["ms"] for x in stats if x["name"][:5] in ("xpass", "ypass", "zpass")) / args.steps
+    cufft = optional(run_cufft, dev, stream, args.steps, passes_ms) if rank == 0 else None
     if rank == 0 and args.learned_pairs > 0:
         learned = optional(run_learned, args, dev)
     if args.ensemble_systems > 0:
@@ -1101,6 +1140,7 @@ def main():
             line["scan"] = scan
         if configs is not None:
             line["configs"] = configs
+        line["cufft_comparator"] = cufft
         if cpu:
             line["cpu_baseline"] = {"value": 1.0 / cpu["step_s"], "unit": "solves/s", "cores": cpu["threads"],
                                     "kind": "oracle",
