@@ -557,49 +557,54 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
     const int ha = ((pa.c2 - oz - R) * hw + (pa.c1 - oy - R)) * px + (pa.c0 - ox - R);
     const int hb = two ? ((pb.c2 - oz - R) * hw + (pb.c1 - oy - R)) * px + (pb.c0 - ox - R) : ha;
     float gax = 0.f, gay = 0.f, gaz = 0.f, gbx = 0.f, gby = 0.f, gbz = 0.f;
+    // every lane walks the full x extent of its rows: taps outside the ball
+    // (and the slots of lanes without a k-th row, read at the centre row, a
+    // cell of the staged tile) get weight 0 by a select instead of a branch
+    const int rcen = (R * hw + R) * px + R;
 #pragma unroll
     for (int k = 0; k < RPL; k++) {
-      if (rinfo[k] != 0xFFFFFFFFu) {
-        const int L = (int)(rinfo[k] >> 16), dy = rinfo[k] & 0xFF, dz = (rinfo[k] >> 8) & 0xFF;
-        const float wyza = sw->W[0][1][dy] * sw->W[0][2][dz];
-        const float wyzb = sw->W[1][1][dy] * sw->W[1][2][dz];
-        float sax = 0.f, say = 0.f, saz = 0.f, sbx = 0.f, sby = 0.f, sbz = 0.f;
-        const float4* ra = sa + ha + roff[k];  // dx = 0
-        if (same) {
+      const bool row = rinfo[k] != 0xFFFFFFFFu;
+      const int L = row ? (int)(rinfo[k] >> 16) : -1;
+      const int dy = row ? (int)(rinfo[k] & 0xFF) : 0, dz = row ? (int)((rinfo[k] >> 8) & 0xFF) : 0;
+      const float wyza = sw->W[0][1][dy] * sw->W[0][2][dz];
+      const float wyzb = sw->W[1][1][dy] * sw->W[1][2][dz];
+      float sax = 0.f, say = 0.f, saz = 0.f, sbx = 0.f, sby = 0.f, sbz = 0.f;
+      const int ro = row ? roff[k] : rcen;
+      const float4* ra = sa + ha + ro;  // dx = 0
+      if (same) {
 #pragma unroll
-          for (int t = -R; t <= R; t++) {
-            if ((t < 0 ? -t : t) <= L) {
-              const float4 m = ra[t];
-              sax = fmaf(wxa[t + R], m.x, sax);
-              say = fmaf(wxa[t + R], m.y, say);
-              saz = fmaf(wxa[t + R], m.z, saz);
-              sbx = fmaf(wxb[t + R], m.x, sbx);
-              sby = fmaf(wxb[t + R], m.y, sby);
-              sbz = fmaf(wxb[t + R], m.z, sbz);
-            }
-          }
-        } else {
-          const float4* rb = sa + hb + roff[k];
-#pragma unroll
-          for (int t = -R; t <= R; t++) {
-            if ((t < 0 ? -t : t) <= L) {
-              const float4 m = ra[t], n = rb[t];
-              sax = fmaf(wxa[t + R], m.x, sax);
-              say = fmaf(wxa[t + R], m.y, say);
-              saz = fmaf(wxa[t + R], m.z, saz);
-              sbx = fmaf(wxb[t + R], n.x, sbx);
-              sby = fmaf(wxb[t + R], n.y, sby);
-              sbz = fmaf(wxb[t + R], n.z, sbz);
-            }
-          }
+        for (int t = -R; t <= R; t++) {
+          const bool in = (t < 0 ? -t : t) <= L;
+          const float wa = in ? wxa[t + R] : 0.f, wb = in ? wxb[t + R] : 0.f;
+          const float4 m = ra[t];
+          sax = fmaf(wa, m.x, sax);
+          say = fmaf(wa, m.y, say);
+          saz = fmaf(wa, m.z, saz);
+          sbx = fmaf(wb, m.x, sbx);
+          sby = fmaf(wb, m.y, sby);
+          sbz = fmaf(wb, m.z, sbz);
         }
-        gax = fmaf(wyza, sax, gax);
-        gay = fmaf(wyza, say, gay);
-        gaz = fmaf(wyza, saz, gaz);
-        gbx = fmaf(wyzb, sbx, gbx);
-        gby = fmaf(wyzb, sby, gby);
-        gbz = fmaf(wyzb, sbz, gbz);
+      } else {
+        const float4* rb = sa + hb + ro;
+#pragma unroll
+        for (int t = -R; t <= R; t++) {
+          const bool in = (t < 0 ? -t : t) <= L;
+          const float wa = in ? wxa[t + R] : 0.f, wb = in ? wxb[t + R] : 0.f;
+          const float4 m = ra[t], n = rb[t];
+          sax = fmaf(wa, m.x, sax);
+          say = fmaf(wa, m.y, say);
+          saz = fmaf(wa, m.z, saz);
+          sbx = fmaf(wb, n.x, sbx);
+          sby = fmaf(wb, n.y, sby);
+          sbz = fmaf(wb, n.z, sbz);
+        }
       }
+      gax = fmaf(wyza, sax, gax);
+      gay = fmaf(wyza, say, gay);
+      gaz = fmaf(wyza, saz, gaz);
+      gbx = fmaf(wyzb, sbx, gbx);
+      gby = fmaf(wyzb, sby, gby);
+      gbz = fmaf(wyzb, sbz, gbz);
     }
     for (int o = 16; o > 0; o >>= 1) {
       gax += __shfl_xor_sync(0xffffffffu, gax, o);

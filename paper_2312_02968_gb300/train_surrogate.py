@@ -42,10 +42,13 @@ def train(h, net, pairs: int, epochs: int, batch: int, lr: float, seed0: int = 1
             "s_train": t_train}
 
 
-def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_guess=(1, 2, 3), reps: int = 5):
+def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_guess=(1, 2, 3), ks_mean=(2, 3, 4),
+             ks_guess_mean=(2,), reps: int = 5):
     """Median particle-force error against the converged field and mean solve
     time (Newton solve included, each solve one CUDA graph replay) for plain
-    and surrogate-seeded solves."""
+    and surrogate-seeded solves, each also with the mean of the last two
+    iterations (MOND_OPT_CYCLE_MEAN). The converged field is the midpoint of
+    the period-2 cycle the iteration ends in: the mean of iterations 40 and 41."""
     import torch
 
     from . import binding as B
@@ -57,6 +60,8 @@ def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_gu
     st = h.stream
     errs = {f"plain{k}": [] for k in ks_plain}
     errs.update({f"guess{k}": [] for k in ks_guess})
+    errs.update({f"mean{k}": [] for k in ks_mean})
+    errs.update({f"guess_mean{k}": [] for k in ks_guess_mean})
     times = {k: [] for k in errs}
     stages = {}
     for sd in seeds:
@@ -65,11 +70,18 @@ def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_gu
         h.bind_particles(*t)
         with torch.cuda.stream(st):
             h.deposit()
-            h.solve_field(S.REF_ITERS, B.WARM_NONE)
-            ga = h.gather().double()
+            h.set_option(B.OPT_CYCLE_MEAN, 1)
             h.solve_field(S.REF_ITERS + 1, B.WARM_NONE)
-            ref = 0.5 * (ga + h.gather().double())
+            h.set_option(B.OPT_CYCLE_MEAN, 0)
+            ref = h.gather().double()
             nref = float(ref.norm())
+
+            def with_mean(fn):
+                h.set_option(B.OPT_CYCLE_MEAN, 1)
+                try:
+                    fn()
+                finally:
+                    h.set_option(B.OPT_CYCLE_MEAN, 0)
 
             def graph_of(fn):
                 # every solve is timed as one CUDA graph replay, so that host
@@ -106,6 +118,10 @@ def evaluate(h, net, seeds, n_particles: int, ks_plain=(1, 2, 3, 4, 5, 6), ks_gu
                 run(f"plain{k}", lambda k=k: h.solve_field(k, B.WARM_NONE))
             for k in ks_guess:
                 run(f"guess{k}", lambda k=k: gs.solve(k))
+            for k in ks_mean:
+                run(f"mean{k}", lambda k=k: with_mean(lambda: h.solve_field(k, B.WARM_NONE)))
+            for k in ks_guess_mean:
+                run(f"guess_mean{k}", lambda k=k: with_mean(lambda: gs.solve(k)))
             if not stages:
                 # where a seeded solve's time goes (first system): each stage one graph replay
                 newton = replay_ms(graph_of(lambda: (h.deposit(), h.solve_field(0, B.WARM_NONE)))) - dep_ms
