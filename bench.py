@@ -686,6 +686,37 @@ def run_configs(dev):
             res["radial_accel_over_eq_ringforce"] = float(np.mean(-(g[1:] * rhat).sum(1)) / (F2 / m))
             res["force_rel_err_vs_oracle_K4"] = float(np.linalg.norm(g - g_ora) / np.linalg.norm(g_ora))
         out[name] = res
+    # the learned-warm-start and ensemble configurations on the oracle (their
+    # GPU lines are the learned and ensemble sections): one whole oracle step
+    # of a 1e7-particle sphere mixture (256^3, standard mu, sigma 1 px, K = 4),
+    # and one step of one system of each side of the ensemble, scaled to its
+    # 64 systems by the cost model that deals them to ranks
+    from paper_2312_02968_gb300 import replicas as R
+
+    mix, _ = W.sphere_mixture(256, 10_000_000, 0)
+    t0 = time.perf_counter()
+    oracle.step(256, 1.0, 1.0, 1.0, B.MU_STANDARD, 1.0, 4, 0.25, mix["cell"], mix["offset"], mix["vel"],
+                mix["mass"])
+    out["learned_oracle_step_s"] = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    specs = []
+    for _ in range(64):
+        n = int(rng.choice([64, 96, 128, 192]))
+        N = int(round(math.exp(rng.uniform(math.log(1e4), math.log(1e6)))))
+        specs.append((n, N, int(rng.integers(0, 2)), int(rng.integers(1 << 30))))
+    per_side = {}
+    for n, N, kind, seed in specs:
+        if n in per_side:
+            continue
+        q = W.isothermal(n, 1.0, N, n / 32, 0.4 * n, seed=seed)
+        t0 = time.perf_counter()
+        oracle.step(n, 1.0, 1.0, 1.0, B.MU_DEEP, 1.0, 4, 0.25, q["cell"], q["offset"], q["vel"], q["mass"])
+        per_side[n] = (time.perf_counter() - t0, R.system_cost(n, N))
+    est = sum(per_side[n][0] * R.system_cost(n, N) / per_side[n][1] for n, N, _, _ in specs)
+    out["ensemble_oracle"] = {"one_system_step_s_per_side": {str(k): v[0] for k, v in per_side.items()},
+                              "est_64_system_steps_s": est,
+                              "system_steps_per_s_est": 64.0 / est}
+    out["oracle_cores"] = oracle.num_threads()
     return out
 
 
