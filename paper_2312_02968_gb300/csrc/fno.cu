@@ -165,6 +165,112 @@ __global__ void __launch_bounds__(256) k_pw(const float* __restrict__ in, int Ci
   }
 }
 
+// The same channel mixing on the tensor cores (mma.sync m16n8k16, bfloat16
+// operands, FP32 accumulation), for Cin, Cout <= 32: out[o][v] = sum_i W[o][i]
+// in[i][v] (+ b[o]); transpose uses W[i][o]. The weights are bfloat16 already;
+// each FP32 input is split into three bfloat16 parts x = h + m + l (the top,
+// middle and low eight bits of its significand), so the three products per
+// weight are exact and only the FP32 accumulation rounds, as in the FMA chain
+// of k_pw. A warp takes 8 PW_NT voxels (PW_NT 8-column tiles) per step, all
+// 32 output rows (two 16-row tiles) and all 32 input rows (two 16-deep
+// steps); one tile a step keeps enough warps in flight on the small grids of
+// the network.
+constexpr int PW_NT = 1;  // 8-voxel tiles per warp step
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_half, float hi_half) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_half));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_half));
+  return a | (b << 16);
+}
+__device__ __forceinline__ void split3(float x, float& h, float& m, float& l) {
+  h = __bfloat162float(__float2bfloat16_rn(x));
+  const float r = x - h;  // exact
+  m = __bfloat162float(__float2bfloat16_rn(r));
+  l = r - m;              // exact, and representable in bfloat16
+}
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) k_pw_mma(const float* __restrict__ in, int Cin,
+                                                const uint16_t* __restrict__ W, const uint16_t* __restrict__ b,
+                                                int Cout, float* __restrict__ out, int64_t V, int transpose) {
+  __shared__ uint16_t sW[32][32 + 8];  // [o][i], zero-padded; row pitch 80 bytes (conflict-free fragments)
+  __shared__ float sb[32];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int o = e / 32, i = e % 32;
+    uint16_t w = 0;
+    if (o < Cout && i < Cin) w = transpose ? W[(int64_t)i * Cout + o] : W[(int64_t)o * Cin + i];
+    sW[o][i] = w;
+  }
+  for (int o = threadIdx.x; o < 32; o += blockDim.x) sb[o] = (b && o < Cout) ? bf(b, o) : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  // A fragments: [M tile][K step][4 registers], row-major 16x16 tiles of sW
+  uint32_t A[2][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+    for (int ks = 0; ks < 2; ks++) {
+      const int r0 = 16 * mt + g, c0 = 16 * ks + 2 * q;
+      A[mt][ks][0] = *reinterpret_cast<const uint32_t*>(&sW[r0][c0]);
+      A[mt][ks][1] = *reinterpret_cast<const uint32_t*>(&sW[r0 + 8][c0]);
+      A[mt][ks][2] = *reinterpret_cast<const uint32_t*>(&sW[r0][c0 + 8]);
+      A[mt][ks][3] = *reinterpret_cast<const uint32_t*>(&sW[r0 + 8][c0 + 8]);
+    }
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (8 * PW_NT); v0 < V;
+       v0 += warps * (8 * PW_NT)) {
+#pragma unroll
+    for (int nt = 0; nt < PW_NT; nt++) {
+      const int64_t vc = v0 + 8 * nt + g;  // this lane's column of the B fragments
+      // B fragments: rows k = 2q, 2q + 1 (register 0) and + 8 (register 1) of each 16-deep step
+      uint32_t Bh[2][2], Bm[2][2], Bl[2][2];
+#pragma unroll
+      for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          float x[2];
+#pragma unroll
+          for (int j = 0; j < 2; j++) {
+            const int k = 16 * ks + 8 * rr + 2 * q + j;
+            x[j] = (k < Cin && vc < V) ? in[(int64_t)k * V + vc] : 0.f;
+          }
+          float h0, m0, l0, h1, m1, l1;
+          split3(x[0], h0, m0, l0);
+          split3(x[1], h1, m1, l1);
+          Bh[ks][rr] = pack_bf16(h0, h1);
+          Bm[ks][rr] = pack_bf16(m0, m1);
+          Bl[ks][rr] = pack_bf16(l0, l1);
+        }
+#pragma unroll
+      for (int mt = 0; mt < 2; mt++) {
+        // C fragment: rows g and g + 8 of the tile, columns 2q and 2q + 1
+        float d[4] = {sb[16 * mt + g], sb[16 * mt + g], sb[16 * mt + g + 8], sb[16 * mt + g + 8]};
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+          mma_bf16(d, A[mt][ks], Bl[ks][0], Bl[ks][1]);  // smallest parts first
+          mma_bf16(d, A[mt][ks], Bm[ks][0], Bm[ks][1]);
+          mma_bf16(d, A[mt][ks], Bh[ks][0], Bh[ks][1]);
+        }
+        const int64_t vo = v0 + 8 * nt + 2 * q;
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+          const int o = 16 * mt + g + 8 * half;
+          if (o >= Cout) continue;
+#pragma unroll
+          for (int j = 0; j < 2; j++)
+            if (vo + j < V) out[(int64_t)o * V + vo + j] = d[2 * half + j];
+        }
+      }
+    }
+  }
+}
+
 // dW[o][i] += sum_v dout[o][v] in[i][v]; db[o] += sum_v dout[o][v].
 __global__ void k_wgrad(const float* dout, int Cout, const float* in, int Cin, int64_t V, float* dW, float* db) {
   constexpr int CH = 64;
@@ -873,8 +979,14 @@ void tables(const Shape& s, const Work& w, cudaStream_t st) {
 void pw(const float* in, int Cin, const uint16_t* W, const uint16_t* b, int Cout, float* out, int64_t V,
         int transpose, cudaStream_t st) {
   const unsigned g = grid_stride(V);
-  if (Cin <= 4) k_pw<4><<<g, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
-  else k_pw<32><<<g, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
+  if (Cin <= 4) {
+    k_pw<4><<<g, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
+  } else {
+    // tensor cores: one warp per 8 PW_NT voxels a step
+    const int64_t steps = (V + 8 * PW_NT - 1) / (8 * PW_NT);
+    const unsigned gm = (unsigned)std::min<int64_t>((steps + 7) / 8, 4096);
+    k_pw_mma<<<gm, TB, 0, st>>>(in, Cin, W, b, Cout, out, V, transpose);
+  }
 }
 
 }  // namespace
