@@ -739,7 +739,8 @@ def run_learned(args, dev):
         shape = tuple(int(v) for v in args.learned_fno.split(","))
         net = S.FNO(*shape, seed=7, device=dev, stream=st)
         tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 7e-4, seed0=1000, log=None)
-        ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000)
+        ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000, ks_plain=(1, 2, 3, 4, 5, 6, 8, 10),
+                        ks_guess=(1, 2, 3, 4, 6), ks_mean=(3, 4, 6, 8, 10), ks_guess_mean=(2, 4, 6))
         h.close()
     finally:
         torch.cuda.synchronize()
@@ -763,6 +764,19 @@ def run_learned(args, dev):
             for k in ev if k.startswith("guess")}
     meets = [k for k in ev if ev[k]["force_err_median"] <= 1e-4]
     fastest_meeting = min(meets, key=lambda k: ev[k]["ms_per_solve"]) if meets else None
+
+    # the time a seeded solve needs to reach the plain K = 4 solve's error, against plain K = 4's time
+    # (log-linear between the seeded solves' points, without the mean)
+    e4 = math.log(plain4["force_err_median"])
+    gp = sorted((ev[k]["ms_per_solve"], math.log(ev[k]["force_err_median"])) for k in ev
+                if k.startswith("guess") and not k.startswith("guess_mean"))
+    t_at = None
+    for (t0, l0), (t1, l1) in zip(gp, gp[1:]):
+        if l0 >= e4 >= l1 and l0 != l1:
+            t_at = t0 + (t1 - t0) * (l0 - e4) / (l0 - l1)
+            break
+    if t_at is None and gp and gp[0][1] <= e4:
+        t_at = gp[0][0]
     return {"workload": "sphere mixtures (1-8 Plummer/Hernquist), 1e7 particles, 256^3, standard mu, sigma 1 px",
             "fno": {"grid": shape[0], "width": shape[1], "modes": shape[2], "layers": shape[3], "weights": "bf16",
                     "accumulate": "f32"},
@@ -774,7 +788,8 @@ def run_learned(args, dev):
             "guess_stages_ms": stages,
             "error_ratio_plain_over_guess_at_equal_time": gain,
             "guess1_vs_plain4_speed": plain4["ms_per_solve"] / ev["guess1"]["ms_per_solve"],
-            "best_guess": best, "fastest_at_1e-4": fastest_meeting}
+            "best_guess": best, "fastest_at_1e-4": fastest_meeting,
+            "guess_time_at_plain4_error_over_plain4_time": (t_at / plain4["ms_per_solve"]) if t_at else None}
 
 
 def run_ensemble(args, dev, dist=None):
@@ -845,19 +860,25 @@ def run_ensemble(args, dev, dist=None):
     serial_steps = 2
     torch.cuda.synchronize()
     s0.record()
+    per_sys_ms = []
     for h in hs:
+        t0 = time.perf_counter()
         for _ in range(serial_steps):
             h.step(dt, 4, B.WARM_NONE)
         # each handle runs on its own stream: wait before the next one starts
         h.sync()
+        per_sys_ms.append((time.perf_counter() - t0) * 1000.0 / serial_steps)
     s1.record()
     s1.synchronize()
     serial_sps = len(hs) * serial_steps / (s0.elapsed_time(s1) / 1000.0)
+    by_side = {}
+    for n, ms1 in zip(sides, per_sys_ms):
+        by_side[str(n)] = by_side.get(str(n), 0.0) + ms1
     batch.close()
     for h in hs:
         h.close()
     parts = R.gather_to_root({"tuned": tuned, "Ns": Ns, "sides": sides, "launches": launches,
-                              "serial_sps": serial_sps}, dist)
+                              "serial_sps": serial_sps, "by_side": by_side}, dist)
     if rank != 0:
         return None
     chunks, allN, allsides = {}, [], []
@@ -873,6 +894,8 @@ def run_ensemble(args, dev, dist=None):
             "system_steps_per_s": nsys * args.ensemble_steps / sec,
             "particle_steps_per_s": sum(allN) * args.ensemble_steps / sec,
             "one_by_one_system_steps_per_s": sum(p["serial_sps"] for p in parts), "graph_launches_per_step": 1,
+            "one_by_one_ms_per_step_by_side": {k: sum(p["by_side"].get(k, 0.0) for p in parts)
+                                               for k in sorted({k for p in parts for k in p["by_side"]}, key=int)},
             "kernel_launches": sum(p["launches"] for p in parts), "autotuned": chunks, "s_generate": t_gen,
             "s_autotune": t_tune}
 

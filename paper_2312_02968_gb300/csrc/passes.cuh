@@ -223,9 +223,11 @@ __device__ __forceinline__ void x_load_spec(float2* sm, const float2* __restrict
   constexpr int SPL = C::H + 1;  // complex values of a line that are used (kx = 0..N/2)
   const float2* src = g + line0 * C::SP;
   const uint64_t pol = tma::policy_evict_first();  // read once: keep L2 for the prefetched planes
-  for (int i = tid; i < C::L * SPL; i += NTX) {
-    const int l = i / SPL, kk = i % SPL;
-    tma::async_copy8_stream(sm + kk * C::LP + l, src + (int64_t)l * C::SP + kk, pol);
+  // a warp per line, lanes along it (no division of the element index)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int l = warp; l < C::L; l += NTX / 32) {
+    const float2* s = src + (int64_t)l * C::SP;
+    for (int kk = lane; kk < SPL; kk += 32) tma::async_copy8_stream(sm + kk * C::LP + l, s + kk, pol);
   }
 }
 
@@ -234,11 +236,15 @@ __device__ __forceinline__ void x_store_spec(const float2* sm, float2* __restric
   using C = XCfg<N>;
   constexpr int Q = C::SP / 2;
   float4* dst = reinterpret_cast<float4*>(g + line0 * C::SP);
-  for (int i = tid; i < C::L * Q; i += NTX) {
-    int l = i / Q, kk = (i % Q) * 2;
-    float2 a = sm[kk * C::LP + l];
-    float2 b = (kk + 1 <= C::H) ? sm[(kk + 1) * C::LP + l] : make_float2(0.f, 0.f);
-    __stcs(dst + i, make_float4(a.x, a.y, b.x, b.y));
+  // a warp per line, lanes along it (no division of the element index)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int l = warp; l < C::L; l += NTX / 32) {
+    for (int qq = lane; qq < Q; qq += 32) {
+      const int kk = 2 * qq;
+      float2 a = sm[kk * C::LP + l];
+      float2 b = (kk + 1 <= C::H) ? sm[(kk + 1) * C::LP + l] : make_float2(0.f, 0.f);
+      __stcs(dst + l * Q + qq, make_float4(a.x, a.y, b.x, b.y));
+    }
   }
 }
 
