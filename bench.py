@@ -740,7 +740,7 @@ def run_learned(args, dev):
         net = S.FNO(*shape, seed=7, device=dev, stream=st)
         tr = T.train(h, net, args.learned_pairs, args.learned_epochs, 8, 7e-4, seed0=1000, log=None)
         ev = T.evaluate(h, net, list(range(args.learned_eval)), 10_000_000, ks_plain=(1, 2, 3, 4, 5, 6, 8, 10),
-                        ks_guess=(1, 2, 3, 4, 6), ks_mean=(3, 4, 6, 8, 10), ks_guess_mean=(2, 4, 6))
+                        ks_guess=(1, 2, 3, 4, 6), ks_mean=(3, 4, 5, 6, 8, 10), ks_guess_mean=(2, 4, 5, 6))
         h.close()
     finally:
         torch.cuda.synchronize()

@@ -514,9 +514,13 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
   // the cell and offset of a particle are rewritten (drift) only by this warp,
   // after their last use, so reading them ahead is safe
   PartIn pa, pb, na, nb;
-  // lanes 0..2 kick the first particle of a pair, lanes 3..5 the second
-  const int kax_a = a.do_kick && lane < 3 ? lane : -1;
-  const int kax_b = a.do_kick && lane >= 3 && lane < 6 ? lane - 3 : -1;
+  // after the warp's reduce-scatter, lane 4 v holds sum v of (gax, gay, gaz,
+  // gbx, gby, gbz): lanes 0, 4, 8 kick the first particle of a pair (axes x,
+  // y, z), lanes 12, 16, 20 the second
+  const int vi = lane >> 2;
+  const bool klane = (lane & 3) == 0;
+  const int kax_a = a.do_kick && klane && vi < 3 ? vi : -1;
+  const int kax_b = a.do_kick && klane && vi >= 3 && vi < 6 ? vi - 3 : -1;
   pa.fetch(__ldg(a.perm + q0), a.cell, a.off, nullptr, ls);
   pa.fetch_kick(a.vel, a.off, kax_a);
   if (q0 + 1 < q1) {
@@ -606,20 +610,33 @@ __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, in
       gby = fmaf(wyzb, sby, gby);
       gbz = fmaf(wyzb, sbz, gbz);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      gax += __shfl_xor_sync(0xffffffffu, gax, o);
-      gay += __shfl_xor_sync(0xffffffffu, gay, o);
-      gaz += __shfl_xor_sync(0xffffffffu, gaz, o);
-      gbx += __shfl_xor_sync(0xffffffffu, gbx, o);
-      gby += __shfl_xor_sync(0xffffffffu, gby, o);
-      gbz += __shfl_xor_sync(0xffffffffu, gbz, o);
+    // reduce-scatter of the six sums over the warp, 9 shuffles instead of 30:
+    // each level halves the values a lane keeps, exchanging the other half
+    // with the lane across that bit; lane L ends with sum number L >> 2
+    float w4[4], w2[2];
+    {
+      const float v8[8] = {gax, gay, gaz, gbx, gby, gbz, 0.f, 0.f};
+      const bool hi = (lane & 16) != 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        w4[i] = (hi ? v8[i + 4] : v8[i]) + __shfl_xor_sync(0xffffffffu, hi ? v8[i] : v8[i + 4], 16);
     }
-    if (lane < 3 || (two && lane < 6)) {
-      const bool first = lane < 3;
-      const int ax = first ? lane : lane - 3;
+    {
+      const bool hi = (lane & 8) != 0;
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+        w2[i] = (hi ? w4[i + 2] : w4[i]) + __shfl_xor_sync(0xffffffffu, hi ? w4[i] : w4[i + 2], 8);
+    }
+    const bool hi4 = (lane & 4) != 0;
+    float gsum = (hi4 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, hi4 ? w2[0] : w2[1], 4);
+    gsum += __shfl_xor_sync(0xffffffffu, gsum, 2);
+    gsum += __shfl_xor_sync(0xffffffffu, gsum, 1);
+    if (klane && (vi < 3 || (two && vi < 6))) {
+      const bool first = vi < 3;
+      const int ax = first ? vi : vi - 3;
       const PartIn& q = first ? pa : pb;
       const uint32_t i = q.i;
-      const float g = first ? (ax == 0 ? gax : (ax == 1 ? gay : gaz)) : (ax == 0 ? gbx : (ax == 1 ? gby : gbz));
+      const float g = gsum;
       if (a.g_out) a.g_out[3 * i + ax] = g;
       if (!isfinite(g)) set_status(a.status, ST_NAN);
       if (a.do_kick) {
