@@ -413,6 +413,8 @@ cudaError_t xpass(mond_pm* h, int mode, passes::XArgs a) {
   a.status = h->w.status;
   a.mu_kind = h->mu_kind;
   a.a0 = (float)h->a0;
+  a.inv_a0 = (float)(1.0 / h->a0);
+  a.sqrt_a0 = (float)std::sqrt(h->a0);
   a.pstride = h->plane;
   const double S = spec_bytes(h), R = real_bytes(h);
   double bytes = 0;
@@ -744,6 +746,15 @@ int ensure_khat(mond_pm* h) {
   return MOND_OK;
 }
 
+// Whether the density scale is an exact power of two (then the x-pass applies
+// the density rule with integer roundings, see rho_rule).
+void set_rho_pow2(passes::XArgs& x) {
+  int e = 0;
+  const double m = std::frexp(x.rho_scale, &e);  // scale = m 2^e, m in [1/2, 1)
+  x.rho_pow2 = (m == 0.5) ? 1 : 0;
+  x.rho_exp2 = e - 1;
+}
+
 // Field solve: the pass sequence of the iteration (see mond_pm_solve_field).
 int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   const int nout = h->keep_phi ? 4 : 3;
@@ -765,6 +776,8 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     x.dep = h->w.dep;
     x.rho_out = h->keep_phi ? h->w.rho : nullptr;  // the density plane is read only by the potential energy
     x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
+  set_rho_pow2(x);
+    set_rho_pow2(x);
     x.ext_axis1 = h->ext_axis + 1;
     x.ext_rho = (float)(h->ext_mass / ((double)h->nf * h->nf * h->s * h->s * h->s));
     if (h->density_given) {

@@ -77,6 +77,8 @@ struct XArgs {
   uint64_t* dep;         // X_RHO: accumulator
   float* rho_out;        // X_RHO: density plane (may be null)
   double rho_scale;      // X_RHO: 2^-Kacc / s^3
+  int rho_pow2;          // X_RHO, X_DRHO: 1 when rho_scale is exactly 2^rho_exp2 (the integer path of rho_rule)
+  int rho_exp2;
   int ext_axis1;         // X_RHO, X_FWD of a density: 1 + axis of the external-field dipole layer, 0 none
   float ext_rho;         // its density: +ext_rho on the last plane along that axis, -ext_rho on the first
   double* red;           // dH reduction slots (2 doubles) or null
@@ -91,6 +93,7 @@ struct XArgs {
   uint32_t* status;
   int mu_kind;
   float a0;
+  float inv_a0, sqrt_a0;  // 1 / a0 and sqrt(a0) (the deep-MOND steps)
   int ncomp;
 };
 
@@ -192,6 +195,36 @@ __device__ __forceinline__ void linearised(int kind, float a0, const float* P, f
   const float ud = (P[0] * d[0] + P[1] * d[1] + P[2] * d[2]) * im;
   const float c = fp * ud * im;
   for (int a = 0; a < 3; a++) d[a] = f * d[a] + c * P[a];
+}
+
+// The deposit's density rule, float(double(v) * scale) for an int64 total v.
+// When scale is an exact power of two, 2^e, the product only shifts the
+// exponent, and the two roundings of the rule are done on the integer
+// instead (the int64 -> double rounding to 53 bits, then the double -> float
+// rounding to 24 bits, each to nearest, ties to even); this GPU's FP64 rate
+// is low. Results outside the range of normal floats take the FP64 route.
+__device__ __forceinline__ uint64_t round_to_bits(uint64_t a, int bits) {
+  const int len = 64 - __clzll((long long)a);
+  if (len <= bits) return a;
+  const int d = len - bits;
+  const uint64_t low = a & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+  uint64_t m = a >> d;
+  if (low > half || (low == half && (m & 1ull))) m += 1ull;
+  return m << d;  // exact (a < 2^63)
+}
+__device__ __forceinline__ float rho_rule(long long v, double scale, int pow2, int e) {
+  if (pow2 && v != 0) {
+    const uint64_t mag = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;  // |v|, also for the most negative v
+    const uint64_t a = round_to_bits(round_to_bits(mag, 53), 24);
+    const int len = 64 - __clzll((long long)a);
+    const int ex = len - 1 + e;  // unbiased exponent of the result
+    if (ex >= -126 && ex <= 127) {
+      const uint32_t mant = (uint32_t)((len > 24 ? a >> (len - 24) : a << (24 - len)) & 0x7FFFFFull);
+      const uint32_t bits = ((uint32_t)(v < 0) << 31) | ((uint32_t)(ex + 127) << 23) | mant;
+      return __uint_as_float(bits);
+    }
+  }
+  return __double2float_rn(__dmul_rn(__ll2double_rn(v), scale));
 }
 
 // ---------------------------------------------------------------------------
@@ -373,30 +406,44 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
   const int64_t rbase = line0 * N;  // real index of the first sample of the tile
   float sq_dh = 0.f, sq_gn = 0.f;
   bool bad = false;
-  for (int i = tid; i < C::L * C::H; i += NTX) {
-    int j = i % C::H, l = i / C::H;
-    int64_t ri = rbase + (int64_t)l * N + 2 * j;
-    float2* const p0 = buf + j * C::LP + l;  // component c at p0 + c * TILE
-    if constexpr (MODE == X_RHO) {
-      ulonglong2 u = *reinterpret_cast<const ulonglong2*>(a.dep + ri);
-      float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.x), a.rho_scale));
-      float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)u.y), a.rho_scale));
+  if constexpr (MODE == X_RHO) {
+    // the density: all of a thread's accumulator loads in flight at once, then the rule
+    constexpr int PER = (C::L * C::H + NTX - 1) / NTX;
+    ulonglong2 u[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+      const int i = tid + k * NTX, j = i % C::H, l = i / C::H;
+      if (i < C::L * C::H) u[k] = __ldcs(reinterpret_cast<const ulonglong2*>(a.dep + rbase + (int64_t)l * N + 2 * j));
+    }
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+      const int i = tid + k * NTX, j = i % C::H, l = i / C::H;
+      if (i >= C::L * C::H) break;
+      const int64_t ri = rbase + (int64_t)l * N + 2 * j;
+      float r0 = rho_rule((long long)u[k].x, a.rho_scale, a.rho_pow2, a.rho_exp2);
+      float r1 = rho_rule((long long)u[k].y, a.rho_scale, a.rho_pow2, a.rho_exp2);
       if (a.rho_out) *reinterpret_cast<float2*>(a.rho_out + ri) = make_float2(r0, r1);
       if (a.ext_axis1) {
         const float2 e = dipole2<N>(a, line0 + l, 2 * j);
         r0 += e.x;
         r1 += e.y;
       }
-      *p0 = make_float2(r0, r1);
-    } else if constexpr (MODE == X_DRHO) {
+      buf[j * C::LP + l] = make_float2(r0, r1);
+    }
+  }
+  for (int i = tid; MODE != X_RHO && i < C::L * C::H; i += NTX) {
+    int j = i % C::H, l = i / C::H;
+    int64_t ri = rbase + (int64_t)l * N + 2 * j;
+    float2* const p0 = buf + j * C::LP + l;  // component c at p0 + c * TILE
+    if constexpr (MODE == X_DRHO) {
       // increment of two deposits: the int64 difference first (exact), then the
       // density rule; the new deposit becomes the base
       ulonglong2 u = *reinterpret_cast<const ulonglong2*>(a.dep + ri);
       ulonglong2* bp = reinterpret_cast<ulonglong2*>(a.dep0 + ri);
       ulonglong2 u0 = *bp;
       *bp = u;
-      float r0 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)(u.x - u0.x)), a.rho_scale));
-      float r1 = __double2float_rn(__dmul_rn(__ll2double_rn((long long)(u.y - u0.y)), a.rho_scale));
+      float r0 = rho_rule((long long)(u.x - u0.x), a.rho_scale, a.rho_pow2, a.rho_exp2);
+      float r1 = rho_rule((long long)(u.y - u0.y), a.rho_scale, a.rho_pow2, a.rho_exp2);
       *p0 = make_float2(r0, r1);
     } else if constexpr (INC) {
       const int64_t P3 = (int64_t)N * N * N;
@@ -545,16 +592,25 @@ __global__ void __launch_bounds__(NTX) k_xpass(XArgs a, int64_t nlines) {
       }
       for (int e = 0; e < 2; e++) {
         float m2 = v[0][e] * v[0][e] + v[1][e] * v[1][e] + v[2][e] * v[2][e];
-        float mag = sqrtf(m2);
         float f;
-        if constexpr (MODE == X_MU) f = mu_factor(a.mu_kind, mag, a.a0);
-        else f = nu_factor(a.mu_kind, mag, a.a0);
+        if (a.mu_kind == 0) {
+          // deep MOND, from the hardware reciprocal square root (a few ulp, no
+          // IEEE divide or square root): nu = sqrt(a0 / |F|) = sqrt(a0) (m2)^-1/4,
+          // mu |g| / a0 with |g| = m2 / sqrt(m2); 0 at zero field
+          const float r = m2 > 0.f ? rsqrtf(m2) : 0.f;  // 1 / |v|
+          if constexpr (MODE == X_MU) f = m2 * r * a.inv_a0;
+          else f = a.sqrt_a0 * (r * rsqrtf(r > 0.f ? r : 1.f)) * (r > 0.f ? 1.f : 0.f);
+        } else {
+          const float mag = sqrtf(m2);
+          if constexpr (MODE == X_MU) f = mu_factor(a.mu_kind, mag, a.a0);
+          else f = nu_factor(a.mu_kind, mag, a.a0);
+        }
         for (int c = 0; c < 3; c++) {
           float o = f * v[c][e];
           if constexpr (MODE == X_MU) o -= gn[c][e];  // H = F - g_N
           v[c][e] = o;
         }
-        bad |= !isfinite(mag);
+        bad |= !isfinite(m2);
       }
       for (int c = 0; c < 3; c++) p0[c * TILE] = make_float2(v[c][0], v[c][1]);
     }

@@ -397,3 +397,34 @@ def test_cycle_mean_matches_oracle(B, n, mu, K, keep_phi, warm):
         h.set_option(B.OPT_CYCLE_MEAN, 0)
         h.solve_field(K)
         assert rel(h.get_field(B.FIELD_ACC).cpu().numpy(), plain["acc"]) < TOL
+
+
+@pytest.mark.parametrize("box_over_n", [1.0, 0.5, 0.7])
+def test_density_rule_bit_exact_at_extreme_totals(B, box_over_n):
+    """The deposit's FP32 density, float(double(acc) 2^-Kacc / s^3), bit for bit
+    against the oracle's, where the totals reach the ends of their range: one
+    pile of the largest masses in one cell (its total past the 53 bits of a
+    double), one lone particle, masses of both signs, and empty neighbours.
+    Pixel widths 1 and 0.5 make the scale a power of two (the x-pass rounds on
+    the integer), 0.7 does not (it takes the FP64 route)."""
+    n = 32
+    rng = np.random.default_rng(23)
+    pos = np.concatenate([np.zeros((1, 3)), rng.normal(0.0, 0.3, size=(3000, 3)) + 5.0,
+                          rng.uniform(-14, 14, size=(500, 3))])
+    cell, off = W.to_cells(pos, n)
+    mass = np.concatenate([[1.0], np.full(3000, 1.0), rng.choice([-1.0, 1.0], 500) * np.exp(rng.uniform(-12, 0, 500))])
+    p = {"cell": cell, "offset": off, "vel": np.zeros((len(mass), 3), np.float32), "mass": mass.astype(np.float32)}
+    dev = torch.device("cuda", 0)
+    t = [torch.from_numpy(np.ascontiguousarray(p[k])).to(dev) for k in ("cell", "offset", "vel", "mass")]
+    s = box_over_n
+    h = B.MondPM(n, 1, n * s, 1.0, 1.0, 0, 1.5, len(mass))
+    h.bind_particles(*t)
+    h.deposit()
+    acc, ka = h.get_deposit_acc()
+    ref, ka_ref, _ = oracle.deposit_fixed(n, 1.5, p["cell"], p["offset"], p["mass"])
+    assert ka == ka_ref and np.array_equal(acc.cpu().numpy().view(np.uint64), ref)
+    assert int(np.abs(ref.view(np.int64)).max()) > 2 ** 53  # the double rounding is exercised
+    rho = h.get_field(B.FIELD_RHO).cpu().numpy()
+    r32, _ = oracle.acc_to_rho(ref, ka_ref, s)
+    assert np.array_equal(rho.view(np.uint32), r32.view(np.uint32))
+    h.close()
