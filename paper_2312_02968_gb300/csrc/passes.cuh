@@ -1051,6 +1051,17 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
           v[P] = cscale(aK, kpy);
           v[2 * P] = cscale(aK, kp[row]);
           if constexpr (SC) *sc = cmul_i<1>(aS);
+        } else if (!(nx || ny || nz)) {
+          // away from the Nyquist planes (all but a few per cent of the points):
+          // P g = k (k.g) A, from one dot product
+          const float2 S = cadd(cadd(cscale(gg[0], kx), cscale(gg[1], ky)), cscale(gg[2], kz));
+          const float2 SA = cscale(S, A);
+          if (mean_out) *sc = cscale(SA, a.norm);  // the potential this step implies, as Z_FINAL forms it
+#pragma unroll
+          for (int aa = 0; aa < 3; aa++) {
+            const float2 acc = cscale(SA, k3[aa]);
+            v[aa * P] = cscale((MODE == Z_DIV) ? csub(gg[aa], acc) : acc, a.norm);
+          }
         } else {
           if (mean_out) {
             // the potential this curl-free step implies, as Z_FINAL forms it: A sum_b k'_b g_b
