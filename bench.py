@@ -620,14 +620,16 @@ def run_cufft(dev, stream, steps, transforms_ms_per_solve):
     return res
 
 
-def run_configs(dev):
+def run_configs(dev, oracle_steps: bool = False):
     """The other configurations as side lines (not the headline): the two-body
     test (64^3 in a zero-padded 128^3 domain, simple mu, sigma 2 px, K = 4,
     200 steps of T/100) and the central body plus ring (1e5 ring particles,
     512^3, deep mu, sigma 1 px, K = 4, 50 steps of T/400): graph-replayed
-    steps per second, the force error of the first step against the FP64
-    oracle's K = 4 (the two-body) or against Eq. ringforce (the ring), and one
-    whole oracle step of each on the host's cores."""
+    steps per second and the force error of the first step against the FP64
+    oracle's K = 4 (the two-body) or against Eq. ringforce (the ring). With
+    oracle_steps, also one whole oracle step of each (and of the learned and
+    ensemble configurations) on the host's cores, and the ring's error
+    against the oracle's K = 4 on 512^3 (minutes of CPU)."""
     import numpy as np
     import torch
 
@@ -668,24 +670,25 @@ def run_configs(dev):
         h.close()
         res = {"steps_per_s": 1000.0 / ms, "ms_per_step": ms, "steps": c["steps"], "particles": len(p["mass"]),
                "fft_domain": nf}
-        t0 = time.perf_counter()
-        acc, ka, _ = oracle.deposit_fixed(nf, c["sigma"], p["cell"], p["offset"], p["mass"])
-        rho = oracle.acc_to_rho(acc, ka, 1.0)[0].astype(np.float64)
-        f = oracle.solve(rho, 1.0, 1.0, 1.0, c["mu"], 4, want=("acc",))
-        g_ora = oracle.gather(c["sigma"], f["acc"], p["cell"], p["offset"])
-        oracle.push(nf, 1.0, c["dt"], g_ora, p["cell"], p["offset"], p["vel"])
-        res["oracle_step_s"] = time.perf_counter() - t0
-        res["oracle_cores"] = oracle.num_threads()
-        if name == "two_body":
-            res["force_rel_err_vs_oracle_K4"] = float(np.linalg.norm(g - g_ora) / np.linalg.norm(g_ora))
-        else:
+        if name == "ring":
             m, M, N, r2 = rmeta["m"], rmeta["M"], 100_000, 64.0
             F2 = 2.0 / (3 * N * r2) * (M ** 1.5 - 1.0 - N * m ** 1.5)
             pos = (p["cell"][1:] - nf / 2 + p["offset"][1:]).astype(np.float64)
             rhat = pos / np.linalg.norm(pos, axis=1, keepdims=True)
             res["radial_accel_over_eq_ringforce"] = float(np.mean(-(g[1:] * rhat).sum(1)) / (F2 / m))
+        if name == "two_body" or oracle_steps:
+            t0 = time.perf_counter()
+            acc, ka, _ = oracle.deposit_fixed(nf, c["sigma"], p["cell"], p["offset"], p["mass"])
+            rho = oracle.acc_to_rho(acc, ka, 1.0)[0].astype(np.float64)
+            f = oracle.solve(rho, 1.0, 1.0, 1.0, c["mu"], 4, want=("acc",))
+            g_ora = oracle.gather(c["sigma"], f["acc"], p["cell"], p["offset"])
+            oracle.push(nf, 1.0, c["dt"], g_ora, p["cell"], p["offset"], p["vel"])
+            res["oracle_step_s"] = time.perf_counter() - t0
+            res["oracle_cores"] = oracle.num_threads()
             res["force_rel_err_vs_oracle_K4"] = float(np.linalg.norm(g - g_ora) / np.linalg.norm(g_ora))
         out[name] = res
+    if not oracle_steps:
+        return out
     # the learned-warm-start and ensemble configurations on the oracle (their
     # GPU lines are the learned and ensemble sections): one whole oracle step
     # of a 1e7-particle sphere mixture (256^3, standard mu, sigma 1 px, K = 4),
@@ -917,8 +920,8 @@ def main():
     ap.add_argument("--ensemble-systems", type=int, default=64, help="systems of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--scan", action="store_true", help="also time steps against N on 128^3 and 256^3")
-    ap.add_argument("--configs", action="store_true", help="also the two-body (128^3) and ring (512^3) "
-                                                           "configurations, GPU and one oracle step each")
+    ap.add_argument("--configs", action="store_true", help="also one whole oracle step of every configuration "
+                                                           "(the two-body and ring GPU lines are always made)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -1086,7 +1089,7 @@ def main():
     learned = ensemble = scan = None
     if rank == 0 and args.scan:
         scan = optional(run_scan, dev, args.steps)
-    configs = optional(run_configs, dev) if rank == 0 and args.configs else None
+    configs = optional(run_configs, dev, args.configs) if rank == 0 else None
     passes_ms = sum(x["ms"] for x in stats if x["name"][:5] in ("xpass", "ypass", "zpass")) / args.steps
     cufft = optional(run_cufft, dev, stream, args.steps, passes_ms) if rank == 0 else None
     if rank == 0 and args.learned_pairs > 0:
