@@ -501,8 +501,9 @@ struct GatWarp {
 // build the axis weights (FP32 exp); a lane sums each of its rows with the x
 // weights in registers and scales the row sums by the y.z weights. When both
 // particles sit in the same cell (most of them, in dense regions) each staged
-// value is read once for both. Warp sums give Eq. gi; lanes 0..2 kick and
-// drift the first particle, lanes 3..5 the second.
+// value is read once for both. A reduce-scatter over the warp gives the six
+// components of Eq. gi; lanes 0, 4, 8 kick and drift the first particle of the
+// pair (axes x, y, z), lanes 12, 16, 20 the second.
 template <int R>
 __device__ __forceinline__ void gather_rows(const GatArgs& a, int q0, int q1, int ox, int oy, int oz, int hw, int px,
                                             const float4* sa, const LaneSlots& ls, const int* roff,
