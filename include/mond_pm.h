@@ -113,13 +113,19 @@ enum {
                              stops, and the next synchronising call returns MOND_ETIMEOUT (the fields of
                              that solve are invalid; the handle stays usable). One-shot: cleared by that
                              launch. 0: off. Needs MOND_OPT_PIPELINED 1 and no graph replay. */
-  MOND_OPT_CYCLE_MEAN = 9     /* value 1: a solve with n_iter >= 2 (plain or warm-started, not incremental)
+  MOND_OPT_CYCLE_MEAN = 9,    /* value 1: a solve with n_iter >= 2 (plain or warm-started, not incremental)
                              takes as its potential the mean of the potentials of its last two iterations'
                              curl-free steps, phi^ = (phi^_{K-1} + phi^_K)/2. Near zeros of the field the
                              iteration of Sect. 2.1 ends in a period-2 cycle (its iterates alternate about
                              the solution of the discretised equation); the mean is the cycle's midpoint.
                              Not in the paper. Costs one half-spectrum plane written and read. Needs
                              MOND_OPT_PIPELINED 1 (default 0) */
+  MOND_OPT_FOLD = 10          /* value 1 (default): where the pipelined passes run and the side allows it
+                             (every supported side but 16 and 48), the curl-free, final and Newton steps
+                             carry one scalar and its z-derivative between their y- and z-passes instead
+                             of three components (the gradient form of their operators, with the axes on a
+                             Nyquist plane kept apart); 0: three components throughout. Same results up to
+                             FP32 rounding order. */
 };
 
 /* Per kernel class: launches, device time between the events around each

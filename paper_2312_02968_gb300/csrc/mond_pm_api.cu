@@ -159,15 +159,15 @@ bool encode_spectral_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx
   return r == CUDA_SUCCESS;
 }
 
-// 4-D view (x: 2 SP floats, component: ncomp planes, y: N rows, z: N planes)
-// with box (bx, bc, 1, bz): z-pass tiles [z][component][column].
-bool encode_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx, int bc, int bz) {
+// 4-D view (x: 2 SP floats, component: ncomp planes cstep planes apart, y: N
+// rows, z: N planes) with box (bx, bc, 1, bz): z-pass tiles [z][component][column].
+bool encode_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx, int bc, int bz, int cstep = 1) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const int sp = n / 2 + 2;
   const cuuint64_t row = (cuuint64_t)2 * sp * 4, plane = row * n * n;
   cuuint64_t dims[4] = {(cuuint64_t)2 * sp, (cuuint64_t)ncomp, (cuuint64_t)n, (cuuint64_t)n};
-  cuuint64_t strides[3] = {plane, row, row * n};
+  cuuint64_t strides[3] = {plane * cstep, row, row * n};
   cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)bc, 1, (cuuint32_t)bz};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
@@ -253,14 +253,14 @@ void mond_pm_set_create_error(const char* msg) { g_create_error = msg ? msg : ""
 enum KClass {
   KC_X_RHO, KC_X_NU_FIRST, KC_X_NU, KC_X_MU, KC_X_INV, KC_X_FWD, KC_X_NU_REAL, KC_X_DRHO, KC_X_DNU_FIRST,
   KC_X_DNU, KC_X_DMU, KC_Y_FWD, KC_Y_INV, KC_Z_NEWTON, KC_Z_CURL, KC_Z_DIV, KC_Z_FINAL, KC_Z_SMOOTH, KC_BIN,
-  KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_COUNT
+  KC_DEPOSIT, KC_GATHER, KC_OTHER, KC_Y_FOLD, KC_Y_UNFOLD, KC_COUNT
 };
 const char* const kKName[KC_COUNT] = {"xpass_rho", "xpass_nu_first", "xpass_nu", "xpass_mu", "xpass_inv",
                                       "xpass_fwd", "xpass_nu_real", "xpass_drho", "xpass_dnu_first",
                                       "xpass_dnu", "xpass_dmu", "ypass_fwd", "ypass_inv", "zpass_newton",
                                       "zpass_curl",
                                       "zpass_div", "zpass_final", "zpass_smooth", "bin", "deposit",
-                                      "gather_push", "other"};
+                                      "gather_push", "other", "ypass_fold", "ypass_unfold"};
 
 struct TimedLaunch {
   int cls;
@@ -305,6 +305,7 @@ struct mond_pm {
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   int lost_tile = -1;  // MOND_OPT_TEST_LOST_LOAD: tile of the next pipelined y-pass whose copy is not issued
   int cycle_mean = 0;  // MOND_OPT_CYCLE_MEAN
+  int fold = 1;        // MOND_OPT_FOLD (used where the pipelined passes run and the size allows it)
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
   // mond_pm_step for the key below, replayed with one cudaGraphLaunch
@@ -316,12 +317,12 @@ struct mond_pm {
     int64_t N;
     const void* cell;
     const void* inc;
-    int cycle_mean;
+    int cycle_mean, fold;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
              track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
              gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
-             cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean;
+             cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean && fold == o.fold;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -329,6 +330,9 @@ struct mond_pm {
   // the component as a dimension (4-D; W with 1 or 3 components per box, A
   // with 3 or 4)
   tma::TensorMap map_wy, map_ay, map_wz1, map_wz3, map_az1, map_az3;
+  // the folded passes: y tiles of two components (narrower), z tiles of components 0 and 2
+  tma::TensorMap map_wyf, map_ayf, map_wz02, map_az02;
+  bool fold_maps = false;
   std::vector<TimedLaunch> tl;      // launches recorded since the last read
   std::vector<cudaEvent_t> evpool;  // recycled events
   int64_t st_launch[KC_COUNT] = {};
@@ -521,6 +525,95 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout, int m
   switch (h->nf) {
 #define MOND_CASE(k) \
   case k: return mond_zpass_##k(mode, a, h->st);
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Whether a solve takes the folded y/z passes around its curl-free, final and
+// Newton steps.
+bool use_fold(const mond_pm* h) { return h->fold && h->pipelined && h->fold_maps; }
+
+// Folded y-pass (passes::YF_*): forward before a curl-free or final z-pass,
+// inverse after a folded z-pass; nplain components from 2 on are transformed
+// as they are.
+cudaError_t yfold(mond_pm* h, int kind, float2* spec, int nplain) {
+  passes::PipeYFArgs p{};
+  p.nplain = nplain;
+  p.tw = h->w.tw;
+  p.kt = (kind == passes::YF_GRAD || kind == passes::YF_GRADN) ? h->w.kp : h->w.kv;
+  p.spec = spec;
+  p.pstride = h->plane;
+  p.status = h->w.status;
+  const tma::TensorMap& m = spec == h->w.W ? h->map_wyf : h->map_ayf;
+  const double S = spec_bytes(h);
+  // the folded pair: two components in and one out (fold), or one in and two
+  // out (unfold; the kx = N/2 block of the curl-free kind reads two); plain
+  // components one in, one out
+  const double bytes = 3.0 * S + 2.0 * nplain * S;
+  Timed tm(h, kind == passes::YF_FOLD ? KC_Y_FOLD : KC_Y_UNFOLD, bytes);
+  switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_ypass_fold_##k(kind, m, p, h->st);
+    MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Folded z-pass: Z_NEWTON (rho^ in component 0 of W), Z_CURL (in place on W)
+// or Z_FINAL (W to out). The tiles holding kx = N/2 or ky = N/2 of the last
+// two go through k_zpass_pipe first (three components, as unfolded), the
+// others through the folded kernel (components 0 and 2).
+cudaError_t zfold(mond_pm* h, int mode, float2* out, int nout, int mean = 0) {
+  passes::PipeZArgs p{};
+  p.nout = nout;
+  p.kv = h->w.kv;
+  p.kp = h->w.kp;
+  p.tw = h->w.tw;
+  p.khat = (mode == passes::Z_FINAL && h->gather_mode) ? h->w.khat : nullptr;
+  p.norm = (float)(1.0 / ((double)h->nf * h->nf * h->nf));
+  p.coef = (float)(4.0 * M_PI * h->G);
+  p.status = h->w.status;
+  p.mean = mean;
+  const bool toA = out == h->w.A;
+  const int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : KC_Z_FINAL;
+  const double S = spec_bytes(h);
+  const double extra = ((mode != passes::Z_CURL && nout > 3) ? S : 0.0) + (mean ? S : 0.0) +
+                       (p.khat ? 0.5 * real_bytes(h) : 0.0);  // potential out, kept potential, smoothing spectrum
+  if (mode != passes::Z_NEWTON) {
+    const int pz = passes::pipe_pz(h->nf);
+    const double nblk = (h->nf / 2 + pz) / pz, ffull = (nblk + h->nf - 1) / (nblk * h->nf);
+    p.nyq_only = 1;
+    {
+      Timed tm(h, zc, (6.0 * S + extra) * ffull);
+      switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: {                                                                                                      \
+    cudaError_t e = mond_zpass_pipe_##k(mode, h->map_wz3, toA ? h->map_az3 : h->map_wz3, h->map_az1, p, h->st); \
+    if (e != cudaSuccess) return e;                                                                              \
+    break;                                                                                                       \
+  }
+        MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    p.nyq_only = 0;
+    Timed tm(h, zc, (4.0 * S + extra) * (1.0 - ffull));
+    switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_zpass_fold_##k(mode, h->map_wz02, toA ? h->map_az02 : h->map_wz02, h->map_az1, p, h->st);
+      MOND_SIZES(MOND_CASE)
+#undef MOND_CASE
+    }
+    return cudaErrorInvalidValue;
+  }
+  Timed tm(h, zc, 3.0 * S + extra);
+  switch (h->nf) {
+#define MOND_CASE(k) \
+  case k: return mond_zpass_fold_##k(mode, h->map_wz1, toA ? h->map_az02 : h->map_wz02, h->map_az1, p, h->st);
     MOND_SIZES(MOND_CASE)
 #undef MOND_CASE
   }
@@ -761,6 +854,7 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   // MOND_OPT_CYCLE_MEAN: the final potential is the mean of the last two iterations'
   const bool mean2 = h->cycle_mean && K >= 2;
   if (mean2 && !h->pipelined) return fail(h, MOND_ESTATE, "MOND_OPT_CYCLE_MEAN needs MOND_OPT_PIPELINED 1");
+  const bool fold = use_fold(h);
   float2* W = h->w.W;
   float2* A = h->w.A;
   // with an increment workspace, a solve also leaves the base of the next
@@ -776,7 +870,6 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     x.dep = h->w.dep;
     x.rho_out = h->keep_phi ? h->w.rho : nullptr;  // the density plane is read only by the potential energy
     x.rho_scale = ldexp(1.0, -h->kacc) / (h->s * h->s * h->s);
-  set_rho_pow2(x);
     set_rho_pow2(x);
     x.ext_axis1 = h->ext_axis + 1;
     x.ext_rho = (float)(h->ext_mass / ((double)h->nf * h->nf * h->s * h->s * h->s));
@@ -794,8 +887,13 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     }
     PK(ypass(h, -1, W, 1));
     if (K == 0) {
-      PK(zpass(h, passes::Z_NEWTON, W, A, nout));
-      PK(ypass(h, +1, A, nout));
+      if (fold) {
+        PK(zfold(h, passes::Z_NEWTON, A, nout));
+        PK(yfold(h, passes::YF_GRAD, A, nout - 2));
+      } else {
+        PK(zpass(h, passes::Z_NEWTON, W, A, nout));
+        PK(ypass(h, +1, A, nout));
+      }
       passes::XArgs xi{};
       xi.ncomp = nout;
       xi.spec = A;
@@ -813,8 +911,13 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
       h->gn_valid = true;
       return MOND_OK;
     }
-    PK(zpass(h, passes::Z_NEWTON, W, W, 3));
-    PK(ypass(h, +1, W, 3));
+    if (fold) {
+      PK(zfold(h, passes::Z_NEWTON, W, 3));
+      PK(yfold(h, passes::YF_GRAD, W, 1));
+    } else {
+      PK(zpass(h, passes::Z_NEWTON, W, W, 3));
+      PK(ypass(h, +1, W, 3));
+    }
   }
   const float* H0 = nullptr;
   if (warm == MOND_WARM_GUESS) {
@@ -850,15 +953,21 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
   PK(xpass(h, reuse ? passes::X_NU_REAL : passes::X_NU_FIRST, xn));
   h->gn_valid = true;
   for (int j = 1; j <= K; j++) {
-    PK(ypass(h, -1, W, 3));
+    if (fold) PK(yfold(h, passes::YF_FOLD, W, 1));
+    else PK(ypass(h, -1, W, 3));
     const bool last = (j == K);
     if (last) {
       if (h->gather_mode) {
         int rk = ensure_khat(h);
         if (rk) return rk;
       }
-      PK(zpass(h, passes::Z_FINAL, W, A, nout, mean2 ? 2 : 0));
-      PK(ypass(h, +1, A, nout));
+      if (fold) {
+        PK(zfold(h, passes::Z_FINAL, A, nout, mean2 ? 2 : 0));
+        PK(yfold(h, passes::YF_GRADN, A, nout - 2));
+      } else {
+        PK(zpass(h, passes::Z_FINAL, W, A, nout, mean2 ? 2 : 0));
+        PK(ypass(h, +1, A, nout));
+      }
       passes::XArgs xi{};
       xi.ncomp = nout;
       xi.spec = A;
@@ -869,8 +978,13 @@ int do_solve(mond_pm* h, int K, int warm, const float* Hguess) {
     }
     // with the mean of the last two iterations, the curl-free step before the
     // last keeps its potential in the scalar slot of A (unused until Z_FINAL)
-    PK(zpass(h, passes::Z_CURL, W, W, 3, (mean2 && j == K - 1) ? 1 : 0));
-    PK(ypass(h, +1, W, 3));
+    if (fold) {
+      PK(zfold(h, passes::Z_CURL, W, 3, (mean2 && j == K - 1) ? 1 : 0));
+      PK(yfold(h, passes::YF_CURL, W, 1));
+    } else {
+      PK(zpass(h, passes::Z_CURL, W, W, 3, (mean2 && j == K - 1) ? 1 : 0));
+      PK(ypass(h, +1, W, 3));
+    }
     passes::XArgs xm{};
     xm.ncomp = 3;
     xm.spec = W;
@@ -1169,6 +1283,11 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
               encode_component_map(&h->map_az1, h->w.A, n, 4, 2 * pz, 1, bx) &&
               encode_component_map(&h->map_az3, h->w.A, n, 4, 2 * pz, 3, bx);
     if (!ok) h->pipelined = 0;  // no driver entry point: the unpipelined passes
+    const int pyf = passes::pipe_pyf(n);
+    h->fold_maps = ok && passes::fold_ok(n) && encode_spectral_map(&h->map_wyf, h->w.W, n, 3, 2 * pyf, bx, 1) &&
+                   encode_spectral_map(&h->map_ayf, h->w.A, n, 4, 2 * pyf, bx, 1) &&
+                   encode_component_map(&h->map_wz02, h->w.W, n, 2, 2 * pz, 2, bx, 2) &&
+                   encode_component_map(&h->map_az02, h->w.A, n, 2, 2 * pz, 2, bx, 2);
   }
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemcpyAsync(h->w.lut, lut.data(), sizeof(uint32_t) * lut.size(), cudaMemcpyHostToDevice, h->st);
@@ -1218,6 +1337,9 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
       return MOND_OK;
     case MOND_OPT_CYCLE_MEAN:
       h->cycle_mean = value ? 1 : 0;
+      return MOND_OK;
+    case MOND_OPT_FOLD:
+      h->fold = value ? 1 : 0;
       return MOND_OK;
     case MOND_OPT_TEST_LOST_LOAD:
       if (value < 0 || value > (1 << 30)) return fail(h, MOND_EINVAL, "lost-load tile out of range");
@@ -1429,7 +1551,7 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   if (rc) return rc;
   const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
                               h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell,
-                              h->inc.dep0, h->cycle_mean};
+                              h->inc.dep0, h->cycle_mean, use_fold(h) ? 1 : 0};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);

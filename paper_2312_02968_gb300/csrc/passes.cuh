@@ -838,6 +838,8 @@ struct PipeZArgs {
   // transform) to the scalar slot of the final spectra; 2 = this Z_FINAL
   // reads it back and takes the mean with its own. Needs the scalar region.
   int mean;
+  // 1: only the tiles holding kx = N/2 or ky = N/2 (the rest is the folded z-pass's)
+  int nyq_only;
   const float* kv;
   const float* kp;
   const float2* tw;
@@ -969,11 +971,26 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
     kv[i] = a.kv[i];
     kp[i] = a.kp[i];
   }
-  const int ntiles = C::NBLKZ * N;
+  const int ntiles = a.nyq_only ? C::NBLKZ + N - 1 : C::NBLKZ * N;
+  // nyq_only: the row ky = N/2 of every block, then the block of kx = N/2 at every other row
+  auto tile_at = [&](int t, int& blk, int& y) {
+    if (!a.nyq_only) {
+      blk = t % C::NBLKZ;
+      y = t / C::NBLKZ;
+    } else if (t < C::NBLKZ) {
+      blk = t;
+      y = N / 2;
+    } else {
+      blk = C::NBLKZ - 1;
+      y = t - C::NBLKZ;
+      if (y >= N / 2) y++;
+    }
+  };
   const bool mean_in = SC && MODE == Z_FINAL && a.mean == 2;   // previous potential read back
   const bool mean_out = SC && MODE == Z_CURL && a.mean == 1;   // this iteration's potential kept
   auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
-    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    int blk, y;
+    tile_at(t, blk, y);
     if constexpr (MODE == Z_NEWTON) {
       tma::mbar_expect_tx(bar, N * P * 8);
       for (int b = 0; b < C::NBOX; b++)
@@ -990,7 +1007,8 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
     }
   };
   auto compute = [&](int t, float2* st) {
-    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    int blk, y;
+    tile_at(t, blk, y);
     float2* sv = st;            // vector region
     float2* ss = st + SOFF;     // scalar region
     if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(ss, P, 1, tw, 1, tid);
@@ -1085,12 +1103,284 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
     if (phi) fftk::fft<N, +1, P, NTZ>(ss, P, 1, tw, 1, tid);
   };
   auto store = [&](int t, const float2* src) {
-    const int blk = t % C::NBLKZ, y = t / C::NBLKZ;
+    int blk, y;
+    tile_at(t, blk, y);
     const tma::TensorMap* m = SCALAR ? &out_map : &in_map;
     for (int b = 0; b < C::NBOX; b++) tma::store_4d(m, blk * 2 * P, 0, y, b * C::BOX, src + b * C::BOX * VP);
     if (phi || mean_out)
       for (int b = 0; b < C::NBOX; b++)
         tma::store_4d(&phi_map, blk * 2 * P, 3, y, b * C::BOX, src + N * VP + b * C::BOX * P);
+  };
+  pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
+}
+
+// ---------------------------------------------------------------------------
+// Folded passes around the curl-free, final and Newton z-passes.
+//
+// Away from the Nyquist planes the curl-free projection is the gradient of one
+// scalar, k (k.g) A, and the final and Newton operators are gradients too
+// (-i kappa phi^). So the y-pass before such a z-pass folds the x and y
+// components into s = kx gx^ + ky gy^ (component 0; component 2 keeps gz^),
+// the z-pass reads two components instead of three and writes the scalar u
+// and its z-derivative (components 0 and 2), and the y-pass after it unfolds
+// them into the three components again: kx u and ky u before its inverse
+// transform, the z one as it is.
+//
+// Where the Nyquist rule of the projection splits the axes into two sets (a
+// point on the kx = N/2 column or the ky = N/2 row) nothing is folded: the
+// fold stores gx^ and gy^ apart (the whole y-block holding kx = N/2; for the
+// other blocks the row ky = N/2, gy^ written to component 1 of that row
+// alone), k_zpass_pipe transforms the z-tiles holding kx = N/2 or ky = N/2
+// as it always does (nyq_only), and the unfold takes those values as they
+// are. The Newton step has no Nyquist rule (kappa vanishes there), so all its
+// tiles are folded. The z-block and the y-block holding kx = N/2 start at the
+// same column (fold_ok) so that the passes agree on which columns are apart.
+// ---------------------------------------------------------------------------
+// kx columns per tile of the folded y-passes: two components per stage of
+// 2 N pyf complex values, 32 KB at N = 256 as in the plain y-pass (a variant
+// with 16 columns and one CTA of 512 threads per SM measured slower)
+constexpr int pipe_pyf(int n) { return n >= 384 ? 4 : 8; }
+constexpr int yf_threads(int) { return NT; }
+static_assert(NT % 16 == 0, "the folded y-pass keeps one column per thread");
+
+constexpr bool fold_ok(int n) {
+  return n >= 32 && ((n / 2) / pipe_pyf(n)) * pipe_pyf(n) == ((n / 2) / pipe_pz(n)) * pipe_pz(n);
+}
+
+enum YFoldKind {
+  YF_FOLD = 0,   // forward: s = kx gx^ + ky gy^ into component 0
+  YF_CURL = 1,   // inverse after the curl-free z-pass: k_x u, k_y u (spectral k)
+  YF_GRADN = 2,  // inverse after the final z-pass: kappa_x u, kappa_y u
+  YF_GRAD = 3    // inverse after the Newton z-pass: as YF_GRADN, every row and block folded
+};
+
+struct PipeYFArgs {
+  int nplain;        // components transformed as they are: 2 .. 1 + nplain
+  const float2* tw;
+  const float* kt;   // per index: k (fold, curl) or kappa (gradients)
+  float2* spec;      // the spectral planes (component 1's row ky = N/2: plain loads and stores)
+  int64_t pstride;   // complex elements between components
+  uint32_t* status;
+};
+
+// Every tile holds two regions of N x P (two components, or two (component,
+// z) lines of the plain components), transformed together.
+template <int N, int KIND, int NTY = yf_threads(N)>
+__global__ void __launch_bounds__(NTY) k_ypass_fold(const __grid_constant__ tma::TensorMap map, PipeYFArgs a) {
+  constexpr int P = pipe_pyf(N);
+  constexpr int H = N / 2;
+  constexpr int NB = (H + 1 + P - 1) / P;  // the last block holds kx = N/2
+  constexpr int SP = N / 2 + 2;
+  constexpr int BOX = pipe_box(N), NBOX = N / BOX;
+  constexpr int DIR = KIND == YF_FOLD ? -1 : +1;
+  constexpr int R = N * P;  // elements of one region
+  extern __shared__ __align__(128) float2 psm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  float2* tw = psm;
+  float* kt = reinterpret_cast<float*>(psm + N);
+  float2* stage0 = psm + 2 * N;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NTY) {
+    tw[i] = a.tw[i];
+    kt[i] = a.kt[i];
+  }
+  const int nxy = NB * N;
+  const int ntiles = nxy + NB * (a.nplain * N / 2);
+  // tile -> block and the (component, z) of its two regions; c0 = -1: the folded pair at z0
+  auto decode = [&](int t, int& blk, int& c0, int& z0, int& c1, int& z1) {
+    if (t < nxy) {
+      blk = t % NB;
+      z0 = z1 = t / NB;
+      c0 = -1;
+      c1 = 1;
+    } else {
+      const int u = t - nxy, m = 2 * (u / NB);
+      blk = u % NB;
+      c0 = 2 + m / N;
+      z0 = m % N;
+      c1 = 2 + (m + 1) / N;
+      z1 = (m + 1) % N;
+    }
+  };
+  auto load_comp = [&](float2* dst, int blk, int c, int z, uint64_t* bar) {
+    for (int b = 0; b < NBOX; b++) tma::load_3d(dst + b * BOX * P, &map, blk * 2 * P, b * BOX, c * N + z, bar);
+  };
+  auto store_comp = [&](const float2* src, int blk, int c, int z) {
+    for (int b = 0; b < NBOX; b++) tma::store_3d(&map, blk * 2 * P, b * BOX, c * N + z, src + b * BOX * P);
+  };
+  auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
+    int blk, c0, z0, c1, z1;
+    decode(t, blk, c0, z0, c1, z1);
+    const bool full = blk == NB - 1;
+    const bool two = c0 >= 0 || KIND == YF_FOLD || (KIND != YF_GRAD && full);
+    tma::mbar_expect_tx(bar, (two ? 2 : 1) * R * 8);
+    load_comp(dst, blk, c0 >= 0 ? c0 : 0, z0, bar);
+    if (two) load_comp(dst + R, blk, c1, z1, bar);
+    return (two ? 2 : 1) * R * 8;
+  };
+  auto compute = [&](int t, float2* st) {
+    int blk, c0, z0, c1, z1;
+    decode(t, blk, c0, z0, c1, z1);
+    const bool full = blk == NB - 1;
+    float2* row1 = a.spec + a.pstride + ((int64_t)z0 * N + H) * SP;  // component 1, row ky = N/2
+    // per-element steps: a thread keeps one column (NTY is a multiple of P)
+    const int cc = tid % P, col = blk * P + cc;
+    if (c0 < 0 && KIND == YF_FOLD) {
+      fftk::fft_c<N, -1, P, 2, NTY>(st, P, 1, R, tw, 1, tid);
+      if (!full) {
+        const float kx = kt[col];
+#pragma unroll 4
+        for (int row = tid / P; row < N; row += NTY / P) {
+          const int i = row * P + cc;
+          if (row == H) row1[col] = st[R + i];  // gy^ of the Nyquist row, kept apart
+          else st[i] = cadd(cscale(st[i], kx), cscale(st[R + i], kt[row]));
+        }
+      }
+      return;
+    }
+    if (c0 < 0 && !(KIND != YF_GRAD && full)) {
+      const float kx = kt[col];
+#pragma unroll 4
+      for (int row = tid / P; row < N; row += NTY / P) {
+        const int i = row * P + cc;
+        const float2 u = st[i];
+        if (KIND != YF_GRAD && row == H) {
+          st[R + i] = row1[col];  // the y output of the Nyquist row, as the z-pass left it
+        } else {
+          st[R + i] = cscale(u, kt[row]);
+          st[i] = cscale(u, kx);
+        }
+      }
+      __syncthreads();
+    }
+    fftk::fft_c<N, DIR, P, 2, NTY>(st, P, 1, R, tw, 1, tid);
+  };
+  auto store = [&](int t, const float2* src) {
+    int blk, c0, z0, c1, z1;
+    decode(t, blk, c0, z0, c1, z1);
+    store_comp(src, blk, c0 >= 0 ? c0 : 0, z0);
+    if (c0 >= 0 || KIND != YF_FOLD || blk == NB - 1) store_comp(src + R, blk, c1, z1);
+  };
+  pipe_run(ntiles, stage0, 2 * R, bars, a.status, load, compute, store);
+}
+
+// Folded z-pass (MODE Z_NEWTON, Z_CURL or Z_FINAL) over the tiles away from
+// the Nyquist planes of x and y (all tiles for Newton): it reads the folded
+// pair (s, gz^) through a map of components 0 and 2 ([z row][2][column] in
+// shared memory) and writes (u, z output) the same way; Newton reads rho^
+// (component 0) into a region of its own. The arithmetic per point is that of
+// k_zpass_pipe, with the x and y factors (k, or kappa for the gradients) left
+// to the unfolding y-pass. SCK: 1 = a scalar region for the mean of the last
+// two iterations, 2 = also the potential (its inverse z transform).
+template <int N, int MODE, int SCK>
+__global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ tma::TensorMap in2,
+                                                       const __grid_constant__ tma::TensorMap out2,
+                                                       const __grid_constant__ tma::TensorMap phi_map, PipeZArgs a) {
+  constexpr int NTZ = 128;
+  using C = PipeCfg<N>;
+  constexpr int P = C::PZ;
+  constexpr int H = N / 2;
+  constexpr int R = N * P;
+  constexpr int IOFF = 2 * R;                                 // Newton: rho^
+  constexpr int SOFF = 2 * R + (MODE == Z_NEWTON ? R : 0);    // scalar region
+  constexpr int SE = SOFF + (SCK ? R : 0);
+  constexpr int NBR = MODE == Z_NEWTON ? C::NBLKZ : C::NBLKZ - 1;  // column blocks visited
+  extern __shared__ __align__(128) float2 psm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  float2* tw = psm;
+  float* kv = reinterpret_cast<float*>(psm + N);
+  float* kp = kv + N;
+  float2* stage0 = psm + 2 * N;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NTZ) {
+    tw[i] = a.tw[i];
+    kv[i] = a.kv[i];
+    kp[i] = a.kp[i];
+  }
+  const int ntiles = MODE == Z_NEWTON ? NBR * N : NBR * (N - 1);
+  auto tile_at = [&](int t, int& blk, int& y) {
+    blk = t % NBR;
+    y = t / NBR;
+    if (MODE != Z_NEWTON && y >= H) y++;  // the row ky = N/2 is k_zpass_pipe's
+  };
+  const bool mean_in = SCK && MODE == Z_FINAL && a.mean == 2;
+  const bool mean_out = SCK && MODE == Z_CURL && a.mean == 1;
+  auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
+    int blk, y;
+    tile_at(t, blk, y);
+    const uint32_t bytes = ((MODE == Z_NEWTON ? 1 : 2) + (mean_in ? 1 : 0)) * R * 8;
+    tma::mbar_expect_tx(bar, bytes);
+    for (int b = 0; b < C::NBOX; b++)
+      tma::load_4d(dst + (MODE == Z_NEWTON ? IOFF + b * C::BOX * P : b * C::BOX * 2 * P), &in2, blk * 2 * P, 0, y,
+                   b * C::BOX, bar);
+    if (mean_in)
+      for (int b = 0; b < C::NBOX; b++)
+        tma::load_4d(dst + SOFF + b * C::BOX * P, &phi_map, blk * 2 * P, 3, y, b * C::BOX, bar);
+    return bytes;
+  };
+  auto compute = [&](int t, float2* st) {
+    int blk, y;
+    tile_at(t, blk, y);
+    float2* ss = st + SOFF;
+    const float ky = kv[y];
+    constexpr int PPT = (R + NTZ - 1) / NTZ;
+    if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(st + IOFF, P, 1, tw, 1, tid);
+    else fftk::fft<N, -1, 2 * P, NTZ>(st, 2 * P, 1, tw, 1, tid);
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int i = tid + k * NTZ;
+      if (i >= R) break;
+      const int row = i / P, cc = i % P, col = blk * P + cc;
+      if (col > H) continue;
+      const float kx = kv[col], kz = kv[row];
+      const float kk = kx * kx + ky * ky + kz * kz;
+      const float A = kk > 0.f ? __frcp_rn(kk) : 0.f;  // correctly rounded, as 1.0f / kk
+      float2* v = st + row * 2 * P + cc;  // u (in: s) at v[0], z output (in: gz^) at v[P]
+      if constexpr (MODE == Z_NEWTON) {
+        const float2 r = st[IOFF + i];
+        const float f = a.coef * A * a.norm;  // 4 pi G A / N^3
+        const float2 ir = cmul_i<1>(r);
+        v[0] = cscale(ir, f);
+        v[P] = cscale(ir, f * kp[row]);
+        if constexpr (SCK) ss[i] = cscale(r, -f);  // phi_N^ = -4 pi G A rho^
+      } else {
+        const bool nz = (row == H);
+        const float2 s = v[0], gz = v[P];
+        if constexpr (MODE == Z_CURL) {
+          if (!nz) {
+            const float2 SA = cscale(cadd(s, cscale(gz, kz)), A);
+            if (mean_out) ss[i] = cscale(SA, a.norm);
+            v[0] = cscale(SA, a.norm);
+            v[P] = cscale(cscale(SA, kz), a.norm);
+          } else {
+            // kz on its Nyquist plane: z is a set of its own
+            if (mean_out) ss[i] = cscale(s, A * a.norm);
+            v[0] = cscale(cscale(s, A), a.norm);
+            v[P] = cscale(cscale(gz, kz * kz * A), a.norm);
+          }
+        } else {  // Z_FINAL: phi^ = i A sum_b k'_b g_b (k'_z = 0 on its Nyquist plane), a^ = -i kappa phi^
+          const float2 S = nz ? s : cadd(s, cscale(gz, kz));
+          float2 aS = cscale(S, A * a.norm);
+          if (mean_in) aS = cscale(cadd(aS, ss[i]), 0.5f);  // the midpoint of the last two iterations
+          const float fk = a.khat ? a.khat[((int64_t)row * N + y) * (N / 2 + 1) + col] : 1.0f;
+          const float2 aK = cscale(aS, fk);
+          v[0] = aK;
+          v[P] = cscale(aK, kp[row]);
+          if constexpr (SCK == 2) ss[i] = cmul_i<1>(aS);
+        }
+      }
+    }
+    __syncthreads();
+    fftk::fft<N, +1, 2 * P, NTZ>(st, 2 * P, 1, tw, 1, tid);
+    if constexpr (SCK == 2) fftk::fft<N, +1, P, NTZ>(ss, P, 1, tw, 1, tid);
+  };
+  auto store = [&](int t, const float2* src) {
+    int blk, y;
+    tile_at(t, blk, y);
+    for (int b = 0; b < C::NBOX; b++) tma::store_4d(&out2, blk * 2 * P, 0, y, b * C::BOX, src + b * C::BOX * 2 * P);
+    if (SCK == 2 || mean_out)
+      for (int b = 0; b < C::NBOX; b++)
+        tma::store_4d(&phi_map, blk * 2 * P, 3, y, b * C::BOX, src + SOFF + b * C::BOX * P);
   };
   pipe_run(ntiles, stage0, SE, bars, a.status, load, compute, store);
 }

@@ -109,7 +109,7 @@ cudaError_t launch_zpipe_sc(const tma::TensorMap& in, const tma::TensorMap& out,
   static int grid = 0;
   constexpr int nt = zthreads<N, MODE>();
   if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE, SC>, sm, nt);
-  const int ntiles = PipeCfg<N>::NBLKZ * N;
+  const int ntiles = a.nyq_only ? PipeCfg<N>::NBLKZ + N - 1 : PipeCfg<N>::NBLKZ * N;
   k_zpass_pipe<N, MODE, SC><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
   return cudaGetLastError();
 }
@@ -139,6 +139,76 @@ cudaError_t CAT(mond_zpass_pipe_, MOND_N)(int mode, const tma::TensorMap& in, co
     case Z_DIV: return launch_zpipe<Z_DIV>(in, out, phi, a, st);
     case Z_FINAL: return launch_zpipe<Z_FINAL>(in, out, phi, a, st);
     case Z_SMOOTH: return launch_zpipe<Z_SMOOTH>(in, out, phi, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+namespace {
+template <int KIND>
+cudaError_t launch_yfold(const tma::TensorMap& map, const PipeYFArgs& a, cudaStream_t st) {
+  if constexpr (!fold_ok(N)) {
+    return cudaErrorInvalidValue;
+  } else {
+    const size_t sm = sizeof(float2) * (2 * N + 2 * 2 * (size_t)N * pipe_pyf(N));
+    cudaError_t e = set_smem(k_ypass_fold<N, KIND>, sm);
+    if (e != cudaSuccess) return e;
+    static int grid = 0;
+    if (!grid) grid = pipe_grid(k_ypass_fold<N, KIND>, sm, yf_threads(N));
+    const int nb = (N / 2 + pipe_pyf(N)) / pipe_pyf(N);
+    const int ntiles = nb * N + nb * (a.nplain * N / 2);
+    k_ypass_fold<N, KIND><<<grid < ntiles ? grid : ntiles, yf_threads(N), sm, st>>>(map, a);
+    return cudaGetLastError();
+  }
+}
+
+template <int MODE, int SCK>
+cudaError_t launch_zfold_sc(const tma::TensorMap& in2, const tma::TensorMap& out2, const tma::TensorMap& phi,
+                            const PipeZArgs& a, cudaStream_t st) {
+  if constexpr (!fold_ok(N)) {
+    return cudaErrorInvalidValue;
+  } else {
+    const size_t R = (size_t)N * PipeCfg<N>::PZ;
+    const size_t stage = 2 * R + (MODE == Z_NEWTON ? R : 0) + (SCK ? R : 0);
+    const size_t sm = sizeof(float2) * (2 * N + 2 * stage);
+    cudaError_t e = set_smem(k_zpass_fold<N, MODE, SCK>, sm);
+    if (e != cudaSuccess) return e;
+    static int grid = 0;
+    if (!grid) grid = pipe_grid(k_zpass_fold<N, MODE, SCK>, sm, 128);
+    const int nbr = MODE == Z_NEWTON ? PipeCfg<N>::NBLKZ : PipeCfg<N>::NBLKZ - 1;
+    const int ntiles = MODE == Z_NEWTON ? nbr * N : nbr * (N - 1);
+    k_zpass_fold<N, MODE, SCK><<<grid < ntiles ? grid : ntiles, 128, sm, st>>>(in2, out2, phi, a);
+    return cudaGetLastError();
+  }
+}
+
+template <int MODE>
+cudaError_t launch_zfold(const tma::TensorMap& in2, const tma::TensorMap& out2, const tma::TensorMap& phi,
+                         const PipeZArgs& a, cudaStream_t st) {
+  // a scalar region for the mean of the last two iterations; its inverse z
+  // transform too when the potential is stored
+  if (MODE != Z_CURL && a.nout > 3) return launch_zfold_sc<MODE, 2>(in2, out2, phi, a, st);
+  if (a.mean) return launch_zfold_sc<MODE, 1>(in2, out2, phi, a, st);
+  return launch_zfold_sc<MODE, 0>(in2, out2, phi, a, st);
+}
+}  // namespace
+
+cudaError_t CAT(mond_ypass_fold_, MOND_N)(int kind, const tma::TensorMap& map, const passes::PipeYFArgs& a,
+                                          cudaStream_t st) {
+  switch (kind) {
+    case YF_FOLD: return launch_yfold<YF_FOLD>(map, a, st);
+    case YF_CURL: return launch_yfold<YF_CURL>(map, a, st);
+    case YF_GRADN: return launch_yfold<YF_GRADN>(map, a, st);
+    case YF_GRAD: return launch_yfold<YF_GRAD>(map, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t CAT(mond_zpass_fold_, MOND_N)(int mode, const tma::TensorMap& in2, const tma::TensorMap& out2,
+                                          const tma::TensorMap& phi, const passes::PipeZArgs& a, cudaStream_t st) {
+  switch (mode) {
+    case Z_NEWTON: return launch_zfold<Z_NEWTON>(in2, out2, phi, a, st);
+    case Z_CURL: return launch_zfold<Z_CURL>(in2, out2, phi, a, st);
+    case Z_FINAL: return launch_zfold<Z_FINAL>(in2, out2, phi, a, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -428,3 +428,49 @@ def test_density_rule_bit_exact_at_extreme_totals(B, box_over_n):
     r32, _ = oracle.acc_to_rho(ref, ka_ref, s)
     assert np.array_equal(rho.view(np.uint32), r32.view(np.uint32))
     h.close()
+
+
+@pytest.mark.parametrize("n,mu,K,keep_phi,mean,gather", [(32, 0, 0, 1, 0, 0), (64, 0, 4, 1, 1, 0), (96, 2, 3, 0, 0, 0),
+                                                         (128, 0, 4, 0, 1, 0), (64, 1, 2, 1, 0, 3),
+                                                         (192, 0, 2, 0, 1, 0)])
+def test_folded_passes_match_oracle(B, n, mu, K, keep_phi, mean, gather):
+    """MOND_OPT_FOLD (the default): the curl-free, final and Newton steps carry
+    one scalar and its z-derivative between their y- and z-passes, the tiles on
+    the Nyquist planes of x and y three components as before. Against the
+    oracle at the parity bar, and against the three-component passes to FP32
+    rounding, for the Newton-only solve, the mean of the last two iterations,
+    the potential plane and the smoothing spectrum of the interpolating gather;
+    192^3 spans many tiles of both passes and a ragged last z-block."""
+    p = W.isothermal(n, 1.0, 5000, n / 11, 0.4 * n, seed=n + K + 17)
+    sigma = 1.5
+    a0 = 1.0 if mu == 0 else 0.05
+    fields = []
+    for fold in (1, 0):
+        h, _ = make(B, n, 1, p, sigma, mu=mu, a0=a0)
+        h.set_option(B.OPT_FOLD, fold)
+        h.set_option(B.OPT_KEEP_PHI, keep_phi)
+        h.set_option(B.OPT_CYCLE_MEAN, mean)
+        h.set_option(B.OPT_GATHER, gather)
+        h.deposit()
+        h.solve_field(K)
+        f = [h.get_field(B.FIELD_ACC).cpu().numpy(), h.get_field(B.FIELD_GN).cpu().numpy()]
+        if keep_phi:
+            f.append(h.get_field(B.FIELD_PHI).cpu().numpy())
+        if K >= 2:
+            f.append(h.get_field(B.FIELD_H).cpu().numpy())
+        fields.append(f)
+    nh = 1 if K >= 2 else 0  # H last: its rounding scales with g_N
+    for a, b in zip(fields[0][:len(fields[0]) - nh], fields[1]):
+        assert rel(a, b) < TOL / 4
+    if nh:
+        assert rel(fields[0][-1], fields[1][-1], scale=fields[1][1]) < TOL / 4
+    acc, ka, _ = oracle.deposit_fixed(n, sigma, p["cell"], p["offset"], p["mass"])
+    rho = oracle.acc_to_rho(acc, ka, 1.0)[0].astype(np.float64)
+    ref = oracle.solve(rho, 1.0, 1.0, a0, mu, K, mean_last2=bool(mean) and K >= 2, want=("acc", "gN", "phi", "H"))
+    acc_ref = oracle.node_smoothed(sigma, ref["acc"]) if gather else ref["acc"]
+    assert rel(fields[0][0], acc_ref) < TOL
+    assert rel(fields[0][1], ref["gN"]) < TOL
+    if keep_phi:
+        assert rel(fields[0][2], ref["phi"]) < TOL
+    if nh:
+        assert rel(fields[0][-1], ref["H"], scale=ref["gN"]) < TOL
