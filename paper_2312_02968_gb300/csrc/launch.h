@@ -14,8 +14,8 @@
                                   cudaStream_t st);                                                          \
   cudaError_t mond_zpass_pipe_##n(int mode, const tma::TensorMap& in, const tma::TensorMap& out,           \
                                   const tma::TensorMap& phi, const passes::PipeZArgs& a, cudaStream_t st); \
-  cudaError_t mond_ypass_fold_##n(int kind, const tma::TensorMap& map, const passes::PipeYFArgs& a,        \
-                                  cudaStream_t st);                                                          \
+  cudaError_t mond_ypass_fold_##n(int kind, const tma::TensorMap& map4, const tma::TensorMap& mapc,        \
+                                  const tma::TensorMap& mapp, const passes::PipeYFArgs& a, cudaStream_t st); \
   cudaError_t mond_zpass_fold_##n(int mode, const tma::TensorMap& in2, const tma::TensorMap& out2,          \
                                   const tma::TensorMap& phi, const passes::PipeZArgs& a, cudaStream_t st);
 MOND_SIZES(MOND_DECL_LAUNCHERS)

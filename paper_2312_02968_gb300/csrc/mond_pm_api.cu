@@ -176,6 +176,24 @@ bool encode_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int b
   return r == CUDA_SUCCESS;
 }
 
+// 4-D view (x: 2 SP floats, component: ncomp planes, y: N rows, z: N planes)
+// with box (bx, 2, by, 1): folded y-pass tiles [row][component][column] of
+// components 0 and 1.
+bool encode_row_component_map(tma::TensorMap* m, void* base, int n, int ncomp, int bx, int by) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int sp = n / 2 + 2;
+  const cuuint64_t row = (cuuint64_t)2 * sp * 4, plane = row * n * n;
+  cuuint64_t dims[4] = {(cuuint64_t)2 * sp, (cuuint64_t)ncomp, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[3] = {plane, row, row * n};
+  cuuint32_t box[4] = {(cuuint32_t)bx, 2, (cuuint32_t)by, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // Gaussian of Eq. smooth along one axis, width sigma pixels.
 double g1(double u, double sigma) { return exp(-(u * u) / (2.0 * sigma * sigma)) / (sigma * sqrt(2.0 * M_PI)); }
 
@@ -331,7 +349,7 @@ struct mond_pm {
   // with 3 or 4)
   tma::TensorMap map_wy, map_ay, map_wz1, map_wz3, map_az1, map_az3;
   // the folded passes: y tiles of two components (narrower), z tiles of components 0 and 2
-  tma::TensorMap map_wyf, map_ayf, map_wz02, map_az02;
+  tma::TensorMap map_wyf, map_ayf, map_wy4, map_ay4, map_wz02, map_az02;
   bool fold_maps = false;
   std::vector<TimedLaunch> tl;      // launches recorded since the last read
   std::vector<cudaEvent_t> evpool;  // recycled events
@@ -546,7 +564,7 @@ cudaError_t yfold(mond_pm* h, int kind, float2* spec, int nplain) {
   p.spec = spec;
   p.pstride = h->plane;
   p.status = h->w.status;
-  const tma::TensorMap& m = spec == h->w.W ? h->map_wyf : h->map_ayf;
+  const bool w = spec == h->w.W;
   const double S = spec_bytes(h);
   // the folded pair: two components in and one out (fold), or one in and two
   // out (unfold; the kx = N/2 block of the curl-free kind reads two); plain
@@ -555,7 +573,9 @@ cudaError_t yfold(mond_pm* h, int kind, float2* spec, int nplain) {
   Timed tm(h, kind == passes::YF_FOLD ? KC_Y_FOLD : KC_Y_UNFOLD, bytes);
   switch (h->nf) {
 #define MOND_CASE(k) \
-  case k: return mond_ypass_fold_##k(kind, m, p, h->st);
+  case k:                                                                                               \
+    return mond_ypass_fold_##k(kind, w ? h->map_wy4 : h->map_ay4, w ? h->map_wyf : h->map_ayf,           \
+                               w ? h->map_wy : h->map_ay, p, h->st);
     MOND_SIZES(MOND_CASE)
 #undef MOND_CASE
   }
@@ -1286,6 +1306,8 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
     const int pyf = passes::pipe_pyf(n);
     h->fold_maps = ok && passes::fold_ok(n) && encode_spectral_map(&h->map_wyf, h->w.W, n, 3, 2 * pyf, bx, 1) &&
                    encode_spectral_map(&h->map_ayf, h->w.A, n, 4, 2 * pyf, bx, 1) &&
+                   encode_row_component_map(&h->map_wy4, h->w.W, n, 3, 2 * pyf, bx) &&
+                   encode_row_component_map(&h->map_ay4, h->w.A, n, 4, 2 * pyf, bx) &&
                    encode_component_map(&h->map_wz02, h->w.W, n, 2, 2 * pz, 2, bx, 2) &&
                    encode_component_map(&h->map_az02, h->w.A, n, 2, 2 * pz, 2, bx, 2);
   }

@@ -1136,12 +1136,10 @@ __global__ void __launch_bounds__(NTZ, 768 / NTZ) k_zpass_pipe(const __grid_cons
 // tiles are folded. The z-block and the y-block holding kx = N/2 start at the
 // same column (fold_ok) so that the passes agree on which columns are apart.
 // ---------------------------------------------------------------------------
-// kx columns per tile of the folded y-passes: two components per stage of
-// 2 N pyf complex values, 32 KB at N = 256 as in the plain y-pass (a variant
-// with 16 columns and one CTA of 512 threads per SM measured slower)
-constexpr int pipe_pyf(int n) { return n >= 384 ? 4 : 8; }
+// kx columns per folded tile of the folded y-passes: two components of
+// pyf columns, as many values as a plain tile of pipe_py(n) = 2 pyf columns
+constexpr int pipe_pyf(int n) { return pipe_py(n) / 2; }
 constexpr int yf_threads(int) { return NT; }
-static_assert(NT % 16 == 0, "the folded y-pass keeps one column per thread");
 
 constexpr bool fold_ok(int n) {
   return n >= 32 && ((n / 2) / pipe_pyf(n)) * pipe_pyf(n) == ((n / 2) / pipe_pz(n)) * pipe_pz(n);
@@ -1163,17 +1161,28 @@ struct PipeYFArgs {
   uint32_t* status;
 };
 
-// Every tile holds two regions of N x P (two components, or two (component,
-// z) lines of the plain components), transformed together.
+// Tiles of N x PP complex values (PP = pipe_py(N) = 2 pyf, 32 KB at N = 256,
+// the plain y-pass's tile): a plain tile holds PP columns of one component;
+// a folded tile holds pyf columns of components 0 and 1 interleaved per row,
+// [row][component][pyf], loaded and stored through a 4-D view with the
+// component as a dimension, so that all tiles take the same conflict-free
+// transform. The folded value s (fold) or u (unfold) travels as a compact
+// [row][pyf] block of component 0, packed and unpacked in place in two halves.
 template <int N, int KIND, int NTY = yf_threads(N)>
-__global__ void __launch_bounds__(NTY) k_ypass_fold(const __grid_constant__ tma::TensorMap map, PipeYFArgs a) {
-  constexpr int P = pipe_pyf(N);
+__global__ void __launch_bounds__(NTY, 3) k_ypass_fold(const __grid_constant__ tma::TensorMap map4,
+                                                    const __grid_constant__ tma::TensorMap mapc,
+                                                    const __grid_constant__ tma::TensorMap mapp, PipeYFArgs a) {
+  constexpr int PF = pipe_pyf(N), PP = 2 * PF;
   constexpr int H = N / 2;
-  constexpr int NB = (H + 1 + P - 1) / P;  // the last block holds kx = N/2
+  constexpr int NBF = (H + 1 + PF - 1) / PF;  // folded blocks; the last holds kx = N/2
+  constexpr int NBP = (H + 1 + PP - 1) / PP;  // plain blocks
   constexpr int SP = N / 2 + 2;
   constexpr int BOX = pipe_box(N), NBOX = N / BOX;
   constexpr int DIR = KIND == YF_FOLD ? -1 : +1;
-  constexpr int R = N * P;  // elements of one region
+  constexpr int R = N * PP;   // elements of a stage
+  constexpr int RC = N * PF;  // elements of a compact block
+  constexpr int PER = R / 2 / NTY;  // slots per thread in each half of the tile
+  static_assert(R % (2 * NTY) == 0 && NTY % PP == 0 && PP <= 32, "slots split evenly, a warp on whole rows");
   extern __shared__ __align__(128) float2 psm[];
   __shared__ __align__(8) uint64_t bars[2];
   float2* tw = psm;
@@ -1184,84 +1193,114 @@ __global__ void __launch_bounds__(NTY) k_ypass_fold(const __grid_constant__ tma:
     tw[i] = a.tw[i];
     kt[i] = a.kt[i];
   }
-  const int nxy = NB * N;
-  const int ntiles = nxy + NB * (a.nplain * N / 2);
-  // tile -> block and the (component, z) of its two regions; c0 = -1: the folded pair at z0
-  auto decode = [&](int t, int& blk, int& c0, int& z0, int& c1, int& z1) {
+  const int nxy = NBF * N;
+  const int ntiles = nxy + NBP * N * a.nplain;
+  // tile -> block, z and component (-1: the folded pair)
+  auto decode = [&](int t, int& blk, int& z, int& comp) {
     if (t < nxy) {
-      blk = t % NB;
-      z0 = z1 = t / NB;
-      c0 = -1;
-      c1 = 1;
+      blk = t % NBF;
+      z = t / NBF;
+      comp = -1;
     } else {
-      const int u = t - nxy, m = 2 * (u / NB);
-      blk = u % NB;
-      c0 = 2 + m / N;
-      z0 = m % N;
-      c1 = 2 + (m + 1) / N;
-      z1 = (m + 1) % N;
+      const int u = t - nxy, rest = u / NBP;
+      blk = u % NBP;
+      comp = 2 + rest / N;
+      z = rest % N;
     }
   };
-  auto load_comp = [&](float2* dst, int blk, int c, int z, uint64_t* bar) {
-    for (int b = 0; b < NBOX; b++) tma::load_3d(dst + b * BOX * P, &map, blk * 2 * P, b * BOX, c * N + z, bar);
-  };
-  auto store_comp = [&](const float2* src, int blk, int c, int z) {
-    for (int b = 0; b < NBOX; b++) tma::store_3d(&map, blk * 2 * P, b * BOX, c * N + z, src + b * BOX * P);
-  };
+  // whether a folded tile moves both components whole (else the compact block)
+  auto whole = [&](int blk) { return KIND == YF_FOLD ? false : (KIND != YF_GRAD && blk == NBF - 1); };
   auto load = [&](int t, float2* dst, uint64_t* bar) -> uint32_t {
-    int blk, c0, z0, c1, z1;
-    decode(t, blk, c0, z0, c1, z1);
-    const bool full = blk == NB - 1;
-    const bool two = c0 >= 0 || KIND == YF_FOLD || (KIND != YF_GRAD && full);
-    tma::mbar_expect_tx(bar, (two ? 2 : 1) * R * 8);
-    load_comp(dst, blk, c0 >= 0 ? c0 : 0, z0, bar);
-    if (two) load_comp(dst + R, blk, c1, z1, bar);
-    return (two ? 2 : 1) * R * 8;
+    int blk, z, comp;
+    decode(t, blk, z, comp);
+    if (comp >= 0) {
+      tma::mbar_expect_tx(bar, R * 8);
+      for (int b = 0; b < NBOX; b++) tma::load_3d(dst + b * BOX * PP, &mapp, blk * 2 * PP, b * BOX, comp * N + z, bar);
+      return R * 8;
+    }
+    if (KIND == YF_FOLD || whole(blk)) {
+      tma::mbar_expect_tx(bar, R * 8);
+      for (int b = 0; b < NBOX; b++) tma::load_4d(dst + b * BOX * PP, &map4, blk * 2 * PF, 0, b * BOX, z, bar);
+      return R * 8;
+    }
+    tma::mbar_expect_tx(bar, RC * 8);
+    for (int b = 0; b < NBOX; b++) tma::load_3d(dst + b * BOX * PF, &mapc, blk * 2 * PF, b * BOX, z, bar);
+    return RC * 8;
   };
   auto compute = [&](int t, float2* st) {
-    int blk, c0, z0, c1, z1;
-    decode(t, blk, c0, z0, c1, z1);
-    const bool full = blk == NB - 1;
-    float2* row1 = a.spec + a.pstride + ((int64_t)z0 * N + H) * SP;  // component 1, row ky = N/2
-    // per-element steps: a thread keeps one column (NTY is a multiple of P)
-    const int cc = tid % P, col = blk * P + cc;
-    if (c0 < 0 && KIND == YF_FOLD) {
-      fftk::fft_c<N, -1, P, 2, NTY>(st, P, 1, R, tw, 1, tid);
-      if (!full) {
-        const float kx = kt[col];
-#pragma unroll 4
-        for (int row = tid / P; row < N; row += NTY / P) {
-          const int i = row * P + cc;
-          if (row == H) row1[col] = st[R + i];  // gy^ of the Nyquist row, kept apart
-          else st[i] = cadd(cscale(st[i], kx), cscale(st[R + i], kt[row]));
+    int blk, z, comp;
+    decode(t, blk, z, comp);
+    float2* row1 = a.spec + a.pstride + ((int64_t)z * N + H) * SP;  // component 1, row ky = N/2
+    // per-element steps over the slots of the tile, a warp on two whole rows
+    // (lane q of a row: component q / PF, column q % PF)
+    const int q = tid % PP, c = q % PF;
+    const bool xs = q < PF;  // the x component's slot
+    const float kxc = kt[blk * PF + c];
+    if (comp < 0 && KIND != YF_FOLD && !whole(blk)) {
+      // unpack u: rows N/2.. first (their slots lie above every packed value),
+      // then rows ..N/2 - 1 (read all, then write)
+#pragma unroll
+      for (int half = 1; half >= 0; half--) {
+        float2 u[PER];
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+          const int row = (half * (R / 2) + tid + k * NTY) / PP;
+          u[k] = st[row * PF + c];
         }
-      }
-      return;
-    }
-    if (c0 < 0 && !(KIND != YF_GRAD && full)) {
-      const float kx = kt[col];
-#pragma unroll 4
-      for (int row = tid / P; row < N; row += NTY / P) {
-        const int i = row * P + cc;
-        const float2 u = st[i];
-        if (KIND != YF_GRAD && row == H) {
-          st[R + i] = row1[col];  // the y output of the Nyquist row, as the z-pass left it
-        } else {
-          st[R + i] = cscale(u, kt[row]);
-          st[i] = cscale(u, kx);
+        if (half == 0) __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+          const int j = half * (R / 2) + tid + k * NTY, row = j / PP;
+          if (KIND != YF_GRAD && row == H)  // the Nyquist row: both outputs as the z-pass left them
+            st[j] = xs ? u[k] : row1[blk * PF + c];
+          else
+            st[j] = cscale(u[k], xs ? kxc : kt[row]);
         }
       }
       __syncthreads();
     }
-    fftk::fft_c<N, DIR, P, 2, NTY>(st, P, 1, R, tw, 1, tid);
+    fftk::fft<N, DIR, PP, NTY>(st, PP, 1, tw, 1, tid);
+    if (comp < 0 && KIND == YF_FOLD && blk != NBF - 1) {
+      // s = kx gx^ + ky gy^, packed: rows ..N/2 - 1 first (their packed places
+      // lie below every unread slot of the second half), then the rest; the
+      // y value reaches the x slot's lane by a shuffle
+#pragma unroll
+      for (int half = 0; half < 2; half++) {
+        float2 v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+          const int j = half * (R / 2) + tid + k * NTY, row = j / PP;
+          const float2 mine = st[j];
+          const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, PF),
+                                           __shfl_xor_sync(0xffffffffu, mine.y, PF));
+          if (row == H) {
+            if (!xs) row1[blk * PF + c] = mine;  // gy^ of the Nyquist row, kept apart
+            v[k] = mine;
+          } else {
+            v[k] = cadd(cscale(mine, kxc), cscale(other, kt[row]));
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+          const int row = (half * (R / 2) + tid + k * NTY) / PP;
+          if (xs) st[row * PF + c] = v[k];
+        }
+      }
+    }
   };
   auto store = [&](int t, const float2* src) {
-    int blk, c0, z0, c1, z1;
-    decode(t, blk, c0, z0, c1, z1);
-    store_comp(src, blk, c0 >= 0 ? c0 : 0, z0);
-    if (c0 >= 0 || KIND != YF_FOLD || blk == NB - 1) store_comp(src + R, blk, c1, z1);
+    int blk, z, comp;
+    decode(t, blk, z, comp);
+    if (comp >= 0) {
+      for (int b = 0; b < NBOX; b++) tma::store_3d(&mapp, blk * 2 * PP, b * BOX, comp * N + z, src + b * BOX * PP);
+    } else if (KIND == YF_FOLD && blk != NBF - 1) {
+      for (int b = 0; b < NBOX; b++) tma::store_3d(&mapc, blk * 2 * PF, b * BOX, z, src + b * BOX * PF);
+    } else {
+      for (int b = 0; b < NBOX; b++) tma::store_4d(&map4, blk * 2 * PF, 0, b * BOX, z, src + b * BOX * PP);
+    }
   };
-  pipe_run(ntiles, stage0, 2 * R, bars, a.status, load, compute, store);
+  pipe_run(ntiles, stage0, R, bars, a.status, load, compute, store);
 }
 
 // Folded z-pass (MODE Z_NEWTON, Z_CURL or Z_FINAL) over the tiles away from

@@ -145,18 +145,19 @@ cudaError_t CAT(mond_zpass_pipe_, MOND_N)(int mode, const tma::TensorMap& in, co
 
 namespace {
 template <int KIND>
-cudaError_t launch_yfold(const tma::TensorMap& map, const PipeYFArgs& a, cudaStream_t st) {
+cudaError_t launch_yfold(const tma::TensorMap& map4, const tma::TensorMap& mapc, const tma::TensorMap& mapp,
+                         const PipeYFArgs& a, cudaStream_t st) {
   if constexpr (!fold_ok(N)) {
     return cudaErrorInvalidValue;
   } else {
-    const size_t sm = sizeof(float2) * (2 * N + 2 * 2 * (size_t)N * pipe_pyf(N));
+    const size_t sm = sizeof(float2) * (2 * N + 2 * (size_t)N * pipe_py(N));
     cudaError_t e = set_smem(k_ypass_fold<N, KIND>, sm);
     if (e != cudaSuccess) return e;
     static int grid = 0;
     if (!grid) grid = pipe_grid(k_ypass_fold<N, KIND>, sm, yf_threads(N));
-    const int nb = (N / 2 + pipe_pyf(N)) / pipe_pyf(N);
-    const int ntiles = nb * N + nb * (a.nplain * N / 2);
-    k_ypass_fold<N, KIND><<<grid < ntiles ? grid : ntiles, yf_threads(N), sm, st>>>(map, a);
+    const int nbf = (N / 2 + pipe_pyf(N)) / pipe_pyf(N), nbp = (N / 2 + pipe_py(N)) / pipe_py(N);
+    const int ntiles = nbf * N + nbp * N * a.nplain;
+    k_ypass_fold<N, KIND><<<grid < ntiles ? grid : ntiles, yf_threads(N), sm, st>>>(map4, mapc, mapp, a);
     return cudaGetLastError();
   }
 }
@@ -192,13 +193,13 @@ cudaError_t launch_zfold(const tma::TensorMap& in2, const tma::TensorMap& out2, 
 }
 }  // namespace
 
-cudaError_t CAT(mond_ypass_fold_, MOND_N)(int kind, const tma::TensorMap& map, const passes::PipeYFArgs& a,
-                                          cudaStream_t st) {
+cudaError_t CAT(mond_ypass_fold_, MOND_N)(int kind, const tma::TensorMap& map4, const tma::TensorMap& mapc,
+                                          const tma::TensorMap& mapp, const passes::PipeYFArgs& a, cudaStream_t st) {
   switch (kind) {
-    case YF_FOLD: return launch_yfold<YF_FOLD>(map, a, st);
-    case YF_CURL: return launch_yfold<YF_CURL>(map, a, st);
-    case YF_GRADN: return launch_yfold<YF_GRADN>(map, a, st);
-    case YF_GRAD: return launch_yfold<YF_GRAD>(map, a, st);
+    case YF_FOLD: return launch_yfold<YF_FOLD>(map4, mapc, mapp, a, st);
+    case YF_CURL: return launch_yfold<YF_CURL>(map4, mapc, mapp, a, st);
+    case YF_GRADN: return launch_yfold<YF_GRADN>(map4, mapc, mapp, a, st);
+    case YF_GRAD: return launch_yfold<YF_GRAD>(map4, mapc, mapp, a, st);
   }
   return cudaErrorInvalidValue;
 }
