@@ -1364,7 +1364,7 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
     const float ky = kv[y];
     constexpr int PPT = (R + NTZ - 1) / NTZ;
     if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(st + IOFF, P, 1, tw, 1, tid);
-    else fftk::fft<N, -1, 2 * P, NTZ>(st, 2 * P, 1, tw, 1, tid);
+    else fftk::fft<N, -1, 2 * P, NTZ, true>(st, 2 * P, 1, tw, 1, tid);
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       const int i = tid + k * NTZ;
@@ -1410,7 +1410,7 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
       }
     }
     __syncthreads();
-    fftk::fft<N, +1, 2 * P, NTZ>(st, 2 * P, 1, tw, 1, tid);
+    fftk::fft<N, +1, 2 * P, NTZ, true>(st, 2 * P, 1, tw, 1, tid);
     if constexpr (SCK == 2) fftk::fft<N, +1, P, NTZ>(ss, P, 1, tw, 1, tid);
   };
   auto store = [&](int t, const float2* src) {
