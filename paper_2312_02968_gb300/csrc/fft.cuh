@@ -107,19 +107,21 @@ __device__ __forceinline__ void dftR(float2* v) {
 // transforms, and writes positions (j / Ns) Ns R + k + r Ns.
 // Threads are numbered tid < NT; butterfly g -> (q = g % NSEQ, j = g / NSEQ),
 // so neighbouring threads touch neighbouring sequences.
-// Row swizzle of the intermediate layout of a two-stage transform (SWZ): the
-// first stage stores position o in row o ^ ((o / B) & 1) with B its radix, the
-// second reads it back from there (its B = N / its radix, the same number).
-// Consecutive butterflies of the first stage then write rows of alternating
-// parity, so sequences of 64-byte rows (8 complex values) fall in both halves
-// of the shared-memory banks; the rows of each pair of positions only swap.
-template <int B>
+// Row swizzle of the intermediate layout of a two-stage transform (mask M):
+// the first stage stores position o in row o ^ ((o / B) & M) with B its
+// radix, the second reads it back from there (its B = N / its radix, the same
+// number). Consecutive butterflies of the first stage, whose rows lie B apart
+// and so start on the same bank, then write rows that start on different
+// banks: M = 1 spreads 64-byte rows (8 complex values) over both halves of the
+// banks (M = 1 and M = 3 on 96-byte rows measured slower). Rows only move
+// within aligned groups of M + 1.
+template <int B, int M>
 __device__ __forceinline__ int swz(int o) {
   if constexpr (B == 0) return o;
-  else return o ^ ((o / B) & 1);
+  else return o ^ ((o / B) & M);
 }
 
-template <int N, int R, int DIR, int NSEQ, int NT, int SWR = 0, int SWW = 0>
+template <int N, int R, int DIR, int NSEQ, int NT, int SWR = 0, int SWW = 0, int M = 1>
 __device__ __forceinline__ void stage(float2* s, int PS, int SS, int Ns, const float2* tw, int twstride, int tid) {
   constexpr int NB = N / R;
   constexpr int TOT = NB * NSEQ;
@@ -134,7 +136,7 @@ __device__ __forceinline__ void stage(float2* s, int PS, int SS, int Ns, const f
       int k = j % Ns;
       const float2* base = s + q * SS;
 #pragma unroll
-      for (int r = 0; r < R; r++) v[b][r] = base[swz<SWR>(j + r * NB) * PS];
+      for (int r = 0; r < R; r++) v[b][r] = base[swz<SWR, M>(j + r * NB) * PS];
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; r++) v[b][r] = cmul(v[b][r], twid<DIR>(tw[r * k * tstep]));
@@ -152,7 +154,7 @@ __device__ __forceinline__ void stage(float2* s, int PS, int SS, int Ns, const f
       int o = (j / Ns) * Ns * R + k;
       float2* base = s + q * SS;
 #pragma unroll
-      for (int r = 0; r < R; r++) base[swz<SWW>(o + r * Ns) * PS] = v[b][r];
+      for (int r = 0; r < R; r++) base[swz<SWW, M>(o + r * Ns) * PS] = v[b][r];
     }
   }
   __syncthreads();
@@ -225,13 +227,14 @@ MOND_PLAN(512, 8, 8, 8)
 
 // Full in-place transform of NSEQ sequences of length N. The twiddle table
 // has TN entries for angle 2 pi m / TN with TN = N * twstride.
-// SWZ: swizzle the intermediate rows of a two-stage plan (other plans ignore it).
-template <int N, int DIR, int NSEQ, int NT, bool SWZ = false>
+// SWZ: swizzle mask of the intermediate rows of a two-stage plan (0: none;
+// other plans ignore it).
+template <int N, int DIR, int NSEQ, int NT, int SWZ = 0>
 __device__ __forceinline__ void fft(float2* s, int PS, int SS, const float2* tw, int twstride, int tid) {
   constexpr int R0 = Plan<N>::r0, R1 = Plan<N>::r1, R2 = Plan<N>::r2;
-  constexpr int B = (SWZ && R1 > 1 && R2 == 1) ? R0 : 0;
-  stage<N, R0, DIR, NSEQ, NT, 0, B>(s, PS, SS, 1, tw, twstride, tid);
-  if constexpr (R1 > 1) stage<N, R1, DIR, NSEQ, NT, B, 0>(s, PS, SS, R0, tw, twstride, tid);
+  constexpr int B = (SWZ && R1 > 1 && R2 == 1 && R0 > SWZ) ? R0 : 0;
+  stage<N, R0, DIR, NSEQ, NT, 0, B, SWZ>(s, PS, SS, 1, tw, twstride, tid);
+  if constexpr (R1 > 1) stage<N, R1, DIR, NSEQ, NT, B, 0, SWZ>(s, PS, SS, R0, tw, twstride, tid);
   if constexpr (R2 > 1) stage<N, R2, DIR, NSEQ, NT>(s, PS, SS, R0 * R1, tw, twstride, tid);
 }
 

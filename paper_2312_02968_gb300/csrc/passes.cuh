@@ -1307,7 +1307,8 @@ __global__ void __launch_bounds__(NTY, 3) k_ypass_fold(const __grid_constant__ t
 // the Nyquist planes of x and y (all tiles for Newton): it reads the folded
 // pair (s, gz^) through a map of components 0 and 2 ([z row][2][column] in
 // shared memory) and writes (u, z output) the same way; Newton reads rho^
-// (component 0) into a region of its own. The arithmetic per point is that of
+// (component 0) into the upper half of that region and takes it into
+// registers before its outputs overwrite it. The arithmetic per point is that of
 // k_zpass_pipe, with the x and y factors (k, or kappa for the gradients) left
 // to the unfolding y-pass. SCK: 1 = a scalar region for the mean of the last
 // two iterations, 2 = also the potential (its inverse z transform).
@@ -1320,8 +1321,8 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
   constexpr int P = C::PZ;
   constexpr int H = N / 2;
   constexpr int R = N * P;
-  constexpr int IOFF = 2 * R;                                 // Newton: rho^
-  constexpr int SOFF = 2 * R + (MODE == Z_NEWTON ? R : 0);    // scalar region
+  constexpr int IOFF = R;       // Newton: rho^, in the upper half of the pair's region (read out first)
+  constexpr int SOFF = 2 * R;   // scalar region
   constexpr int SE = SOFF + (SCK ? R : 0);
   constexpr int NBR = MODE == Z_NEWTON ? C::NBLKZ : C::NBLKZ - 1;  // column blocks visited
   extern __shared__ __align__(128) float2 psm[];
@@ -1363,8 +1364,19 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
     float2* ss = st + SOFF;
     const float ky = kv[y];
     constexpr int PPT = (R + NTZ - 1) / NTZ;
-    if constexpr (MODE == Z_NEWTON) fftk::fft<N, -1, P, NTZ>(st + IOFF, P, 1, tw, 1, tid);
-    else fftk::fft<N, -1, 2 * P, NTZ, true>(st, 2 * P, 1, tw, 1, tid);
+    float2 rin[MODE == Z_NEWTON ? PPT : 1];
+    if constexpr (MODE == Z_NEWTON) {
+      fftk::fft<N, -1, P, NTZ>(st + IOFF, P, 1, tw, 1, tid);
+      // the outputs overwrite the input: take it all into registers first
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        const int i = tid + k * NTZ;
+        if (i < R) rin[k] = st[IOFF + i];
+      }
+      __syncthreads();
+    } else {
+      fftk::fft<N, -1, 2 * P, NTZ, 1>(st, 2 * P, 1, tw, 1, tid);
+    }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       const int i = tid + k * NTZ;
@@ -1376,7 +1388,7 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
       const float A = kk > 0.f ? __frcp_rn(kk) : 0.f;  // correctly rounded, as 1.0f / kk
       float2* v = st + row * 2 * P + cc;  // u (in: s) at v[0], z output (in: gz^) at v[P]
       if constexpr (MODE == Z_NEWTON) {
-        const float2 r = st[IOFF + i];
+        const float2 r = rin[k];
         const float f = a.coef * A * a.norm;  // 4 pi G A / N^3
         const float2 ir = cmul_i<1>(r);
         v[0] = cscale(ir, f);
@@ -1410,7 +1422,7 @@ __global__ void __launch_bounds__(128, 6) k_zpass_fold(const __grid_constant__ t
       }
     }
     __syncthreads();
-    fftk::fft<N, +1, 2 * P, NTZ, true>(st, 2 * P, 1, tw, 1, tid);
+    fftk::fft<N, +1, 2 * P, NTZ, 1>(st, 2 * P, 1, tw, 1, tid);
     if constexpr (SCK == 2) fftk::fft<N, +1, P, NTZ>(ss, P, 1, tw, 1, tid);
   };
   auto store = [&](int t, const float2* src) {

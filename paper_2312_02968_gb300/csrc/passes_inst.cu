@@ -169,7 +169,7 @@ cudaError_t launch_zfold_sc(const tma::TensorMap& in2, const tma::TensorMap& out
     return cudaErrorInvalidValue;
   } else {
     const size_t R = (size_t)N * PipeCfg<N>::PZ;
-    const size_t stage = 2 * R + (MODE == Z_NEWTON ? R : 0) + (SCK ? R : 0);
+    const size_t stage = 2 * R + (SCK ? R : 0);
     const size_t sm = sizeof(float2) * (2 * N + 2 * stage);
     cudaError_t e = set_smem(k_zpass_fold<N, MODE, SCK>, sm);
     if (e != cudaSuccess) return e;
