@@ -120,12 +120,16 @@ enum {
                              the solution of the discretised equation); the mean is the cycle's midpoint.
                              Not in the paper. Costs one half-spectrum plane written and read. Needs
                              MOND_OPT_PIPELINED 1 (default 0) */
-  MOND_OPT_FOLD = 10          /* value 1 (default): where the pipelined passes run and the side allows it
+  MOND_OPT_FOLD = 10,         /* value 1 (default): where the pipelined passes run and the side allows it
                              (every supported side but 16 and 48), the curl-free, final and Newton steps
                              carry one scalar and its z-derivative between their y- and z-passes instead
                              of three components (the gradient form of their operators, with the axes on a
                              Nyquist plane kept apart); 0: three components throughout. Same results up to
                              FP32 rounding order. */
+  MOND_OPT_GRID_CAP = 11      /* value c > 0: the persistent kernels of a step (pipelined y/z passes,
+                             deposit, gather) launch at most c CTAs, leaving the rest of the GPU to
+                             kernels that run beside them (independent systems on their own streams,
+                             a batch); 0 (default): as many as fit the GPU. Same results. */
 };
 
 /* Per kernel class: launches, device time between the events around each

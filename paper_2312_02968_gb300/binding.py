@@ -21,6 +21,7 @@ OPT_KEEP_PHI, OPT_TRACK_DH, OPT_USE_GRAPH, OPT_TIMING, OPT_PIPELINED, OPT_CHUNK,
 OPT_TEST_LOST_LOAD = 8  # tests of the bounded device waits only
 OPT_CYCLE_MEAN = 9
 OPT_FOLD = 10
+OPT_GRID_CAP = 11
 ERRORS = {0: "MOND_OK", -1: "MOND_EINVAL", -2: "MOND_ENOMEM", -3: "MOND_ECUDA", -4: "MOND_EOVERFLOW",
           -5: "MOND_EDOMAIN", -6: "MOND_ENAN", -7: "MOND_ETIMEOUT", -8: "MOND_ESTATE"}
 

@@ -323,7 +323,9 @@ struct mond_pm {
   int keep_phi = 0, track_dh = 0, use_graph = 0, timing = 0, pipelined = 1;
   int lost_tile = -1;  // MOND_OPT_TEST_LOST_LOAD: tile of the next pipelined y-pass whose copy is not issued
   int cycle_mean = 0;  // MOND_OPT_CYCLE_MEAN
+  bool count_dirty = true;  // the binning's cell counters may be nonzero
   int fold = 1;        // MOND_OPT_FOLD (used where the pipelined passes run and the size allows it)
+  int grid_cap = 0;    // MOND_OPT_GRID_CAP: CTAs of a persistent kernel at most (0: all that fit)
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
   // mond_pm_step for the key below, replayed with one cudaGraphLaunch
@@ -335,12 +337,13 @@ struct mond_pm {
     int64_t N;
     const void* cell;
     const void* inc;
-    int cycle_mean, fold;
+    int cycle_mean, fold, grid_cap;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
              track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
              gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
-             cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean && fold == o.fold;
+             cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean && fold == o.fold &&
+             grid_cap == o.grid_cap;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -470,6 +473,7 @@ cudaError_t ypass(mond_pm* h, int dir, float2* spec, int ncomp) {
     p.tw = h->w.tw;
     p.status = h->w.status;
     p.lost_tile = h->lost_tile;  // fault injection of the bounded-wait tests (one-shot)
+    p.max_ctas = h->grid_cap;
     h->lost_tile = -1;
     const tma::TensorMap& m = spec == h->w.W ? h->map_wy : h->map_ay;
     Timed tm(h, dir < 0 ? KC_Y_FWD : KC_Y_INV, 2.0 * ncomp * spec_bytes(h));
@@ -526,6 +530,7 @@ cudaError_t zpass(mond_pm* h, int mode, float2* in, float2* out, int nout, int m
     p.coef = a.coef;
     p.status = h->w.status;
     p.mean = mean;
+    p.max_ctas = h->grid_cap;
     // input: rho^ (component 0 of W) for Newton, else three components;
     // output: three components, phi^ separately as component 3 of A
     const tma::TensorMap& mi =
@@ -564,6 +569,7 @@ cudaError_t yfold(mond_pm* h, int kind, float2* spec, int nplain) {
   p.spec = spec;
   p.pstride = h->plane;
   p.status = h->w.status;
+  p.max_ctas = h->grid_cap;
   const bool w = spec == h->w.W;
   const double S = spec_bytes(h);
   // the folded pair: two components in and one out (fold), or one in and two
@@ -597,6 +603,7 @@ cudaError_t zfold(mond_pm* h, int mode, float2* out, int nout, int mean = 0) {
   p.coef = (float)(4.0 * M_PI * h->G);
   p.status = h->w.status;
   p.mean = mean;
+  p.max_ctas = h->grid_cap;
   const bool toA = out == h->w.A;
   const int zc = mode == passes::Z_NEWTON ? KC_Z_NEWTON : mode == passes::Z_CURL ? KC_Z_CURL : KC_Z_FINAL;
   const double S = spec_bytes(h);
@@ -663,6 +670,12 @@ int read_status(mond_pm* h) {
   return MOND_OK;
 }
 
+// CTAs of the persistent deposit and gather (work items from a counter).
+int persistent_ctas(const mond_pm* h) {
+  const int g = h->sms * 4;
+  return (h->grid_cap > 0 && h->grid_cap < g) ? h->grid_cap : g;
+}
+
 int do_bin(mond_pm* h) {
   parts::BinArgs b{};
   b.n = h->nf;
@@ -684,7 +697,10 @@ int do_bin(mond_pm* h) {
   b.status = h->w.status;
   const int64_t M = h->n3 + 1;
   const int nblk = (int)((M + parts::SCAN_B - 1) / parts::SCAN_B);
-  CK(cudaMemsetAsync(h->w.count, 0, sizeof(int) * M, h->st));
+  // the scatter takes every counter back to zero, so the counters are cleared
+  // only when the last binning did not get that far (and at creation)
+  if (h->count_dirty) CK(cudaMemsetAsync(h->w.count, 0, sizeof(int) * M, h->st));
+  h->count_dirty = true;
   unsigned nb = (unsigned)((h->N + 255) / 256);
   if (h->N > 0) {
     Timed tm(h, KC_BIN, 32.0 * h->N);
@@ -706,6 +722,8 @@ int do_bin(mond_pm* h) {
     Timed tm(h, KC_BIN, 16.0 * h->N);
     parts::k_bin_scatter<<<nb, 256, 0, h->st>>>(b);
   }
+  CK(cudaGetLastError());
+  h->count_dirty = false;
   {
     // work items per tile, then their exclusive scan in place (chunk_start[T] = total)
     Timed tm(h, KC_BIN, 16.0 * h->ntile);
@@ -773,7 +791,7 @@ int do_deposit(mond_pm* h) {
     Timed tm(h, KC_DEPOSIT, 32.0 * h->N + 8.0 * h->n3);
     switch (h->r) {
 #define DEPOSIT_R(R) \
-  case R: CK(launch_smem(parts::k_deposit<R>, h->sms * 4, parts::DEP_NT, sm, h->st, &d)); break;
+  case R: CK(launch_smem(parts::k_deposit<R>, persistent_ctas(h), parts::DEP_NT, sm, h->st, &d)); break;
       DEPOSIT_R(2) DEPOSIT_R(3) DEPOSIT_R(4) DEPOSIT_R(5) DEPOSIT_R(6) DEPOSIT_R(7)
 #undef DEPOSIT_R
       default: return fail(h, MOND_EINVAL, "no deposit for reach %d", h->r);
@@ -835,7 +853,7 @@ int do_gather(mond_pm* h, float* g_out, double dt, int kick, int drift) {
     Timed tm(h, KC_GATHER, 3.0 * real_bytes(h) + 64.0 * h->N);
     switch (h->r) {
 #define GATHER_R(R) \
-  case R: CK(launch_smem(parts::k_gather_push<R>, h->sms * 4, parts::GAT_NT, sm, h->st, &g)); break;
+  case R: CK(launch_smem(parts::k_gather_push<R>, persistent_ctas(h), parts::GAT_NT, sm, h->st, &g)); break;
       GATHER_R(2) GATHER_R(3) GATHER_R(4) GATHER_R(5) GATHER_R(6) GATHER_R(7)
 #undef GATHER_R
       default: return fail(h, MOND_EINVAL, "no gather for reach %d", h->r);
@@ -1363,6 +1381,10 @@ int mond_pm_set_option(mond_pm_t h, int option, int64_t value) {
     case MOND_OPT_FOLD:
       h->fold = value ? 1 : 0;
       return MOND_OK;
+    case MOND_OPT_GRID_CAP:
+      if (value < 0 || value > (1 << 20)) return fail(h, MOND_EINVAL, "grid cap out of range");
+      h->grid_cap = (int)value;
+      return MOND_OK;
     case MOND_OPT_TEST_LOST_LOAD:
       if (value < 0 || value > (1 << 30)) return fail(h, MOND_EINVAL, "lost-load tile out of range");
       if (value && (h->use_graph || !h->pipelined))
@@ -1573,7 +1595,7 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   if (rc) return rc;
   const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
                               h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell,
-                              h->inc.dep0, h->cycle_mean, use_fold(h) ? 1 : 0};
+                              h->inc.dep0, h->cycle_mean, use_fold(h) ? 1 : 0, h->grid_cap};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);

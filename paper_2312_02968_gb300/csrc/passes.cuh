@@ -289,23 +289,28 @@ __device__ __forceinline__ void x_pre_c2r(float2* sm0, int nc, const float2* tw,
   using C = XCfg<N>;
   constexpr int NP = N / 4 + 1;  // pairs (k, N/2 - k), k = 0..N/4
   constexpr int TILE = C::ROWS * C::LP;
-  for (int i = tid; i < NP * C::L * nc; i += NTX) {
-    float2* sm = sm0 + (i / (NP * C::L)) * TILE;  // component tile
-    int l = i % C::L, k = (i / C::L) % NP;
-    if (k == 0) {
-      float x0 = sm[0 * C::LP + l].x, xn = sm[C::H * C::LP + l].x;
-      sm[0 * C::LP + l] = make_float2(x0 + xn, x0 - xn);
-    } else {
-      int k2 = C::H - k;
-      float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
-      float2 w = tw[k];  // e^{+2 pi i k / N}
-      float2 ya = cadd(cadd(a, cconj(b)), cmul_i<1>(cmul(w, csub(a, cconj(b)))));
-      if (k2 != k) {
-        float2 w2 = make_float2(-w.x, w.y);  // e^{+2 pi i (N/2-k)/N} = -conj(w)
-        float2 yb = cadd(cadd(b, cconj(a)), cmul_i<1>(cmul(w2, csub(b, cconj(a)))));
-        sm[k2 * C::LP + l] = yb;
+  constexpr int KS = NTX / C::L;  // a thread keeps its line l and takes every KS-th pair
+  static_assert(NTX % C::L == 0, "lines divide the threads");
+  const int l = tid % C::L;
+  for (int c = 0; c < nc; c++) {
+    float2* sm = sm0 + c * TILE;  // component tile
+#pragma unroll
+    for (int k = tid / C::L; k < NP; k += KS) {
+      if (k == 0) {
+        float x0 = sm[0 * C::LP + l].x, xn = sm[C::H * C::LP + l].x;
+        sm[0 * C::LP + l] = make_float2(x0 + xn, x0 - xn);
+      } else {
+        int k2 = C::H - k;
+        float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
+        float2 w = tw[k];  // e^{+2 pi i k / N}
+        float2 ya = cadd(cadd(a, cconj(b)), cmul_i<1>(cmul(w, csub(a, cconj(b)))));
+        if (k2 != k) {
+          float2 w2 = make_float2(-w.x, w.y);  // e^{+2 pi i (N/2-k)/N} = -conj(w)
+          float2 yb = cadd(cadd(b, cconj(a)), cmul_i<1>(cmul(w2, csub(b, cconj(a)))));
+          sm[k2 * C::LP + l] = yb;
+        }
+        sm[k * C::LP + l] = ya;
       }
-      sm[k * C::LP + l] = ya;
     }
   }
   __syncthreads();
@@ -318,28 +323,32 @@ __device__ __forceinline__ void x_post_r2c(float2* sm0, int nc, const float2* tw
   using C = XCfg<N>;
   constexpr int NP = N / 4 + 1;
   constexpr int TILE = C::ROWS * C::LP;
-  for (int i = tid; i < NP * C::L * nc; i += NTX) {
-    float2* sm = sm0 + (i / (NP * C::L)) * TILE;  // component tile
-    int l = i % C::L, k = (i / C::L) % NP;
-    if (k == 0) {
-      float2 z = sm[0 * C::LP + l];
-      sm[0 * C::LP + l] = make_float2(z.x + z.y, 0.f);
-      sm[C::H * C::LP + l] = make_float2(z.x - z.y, 0.f);
-    } else {
-      int k2 = C::H - k;
-      float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
-      float2 w = tw[k];               // (cos, sin)(2 pi k/N)
-      float2 wc = cconj(w);           // e^{-2 pi i k/N}
-      float2 e = cscale(cadd(a, cconj(b)), 0.5f);
-      float2 d = cscale(csub(a, cconj(b)), 0.5f);
-      float2 xa = csub(e, cmul_i<1>(cmul(wc, d)));  // E - i W^k (a - conj b)/2
-      if (k2 != k) {
-        float2 e2 = cscale(cadd(b, cconj(a)), 0.5f);
-        float2 d2 = cscale(csub(b, cconj(a)), 0.5f);
-        float2 xb = cadd(e2, cmul_i<1>(cmul(w, d2)));  // X[N/2-k]
-        sm[k2 * C::LP + l] = xb;
+  constexpr int KS = NTX / C::L;  // a thread keeps its line l and takes every KS-th pair
+  const int l = tid % C::L;
+  for (int c = 0; c < nc; c++) {
+    float2* sm = sm0 + c * TILE;  // component tile
+#pragma unroll
+    for (int k = tid / C::L; k < NP; k += KS) {
+      if (k == 0) {
+        float2 z = sm[0 * C::LP + l];
+        sm[0 * C::LP + l] = make_float2(z.x + z.y, 0.f);
+        sm[C::H * C::LP + l] = make_float2(z.x - z.y, 0.f);
+      } else {
+        int k2 = C::H - k;
+        float2 a = sm[k * C::LP + l], b = sm[k2 * C::LP + l];
+        float2 w = tw[k];               // (cos, sin)(2 pi k/N)
+        float2 wc = cconj(w);           // e^{-2 pi i k/N}
+        float2 e = cscale(cadd(a, cconj(b)), 0.5f);
+        float2 d = cscale(csub(a, cconj(b)), 0.5f);
+        float2 xa = csub(e, cmul_i<1>(cmul(wc, d)));  // E - i W^k (a - conj b)/2
+        if (k2 != k) {
+          float2 e2 = cscale(cadd(b, cconj(a)), 0.5f);
+          float2 d2 = cscale(csub(b, cconj(a)), 0.5f);
+          float2 xb = cadd(e2, cmul_i<1>(cmul(w, d2)));  // X[N/2-k]
+          sm[k2 * C::LP + l] = xb;
+        }
+        sm[k * C::LP + l] = xa;
       }
-      sm[k * C::LP + l] = xa;
     }
   }
   __syncthreads();
@@ -829,6 +838,7 @@ struct PipeYArgs {
   // Fault injection for tests of the bounded waits: the load of this tile is
   // never issued, so its wait runs out (-1: none).
   int lost_tile = -1;
+  int max_ctas = 0;  // cap on the persistent grid (0: as many as fit the GPU)
 };
 
 struct PipeZArgs {
@@ -840,6 +850,7 @@ struct PipeZArgs {
   int mean;
   // 1: only the tiles holding kx = N/2 or ky = N/2 (the rest is the folded z-pass's)
   int nyq_only;
+  int max_ctas;  // cap on the persistent grid (0: as many as fit the GPU)
   const float* kv;
   const float* kp;
   const float2* tw;
@@ -1159,6 +1170,7 @@ struct PipeYFArgs {
   float2* spec;      // the spectral planes (component 1's row ky = N/2: plain loads and stores)
   int64_t pstride;   // complex elements between components
   uint32_t* status;
+  int max_ctas;      // cap on the persistent grid (0: as many as fit the GPU)
 };
 
 // Tiles of N x PP complex values (PP = pipe_py(N) = 2 pyf, 32 KB at N = 256,

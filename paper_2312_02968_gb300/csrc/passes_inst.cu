@@ -78,6 +78,12 @@ cudaError_t CAT(mond_ypass_, MOND_N)(int dir, const passes::YArgs& a, int ncomp,
 }
 
 namespace {
+// The persistent grid: min(every CTA that fits, tiles, the caller's cap).
+int capped(int grid, int ntiles, int cap) {
+  int g = grid < ntiles ? grid : ntiles;
+  return (cap > 0 && g > cap) ? cap : g;
+}
+
 template <typename K>
 int pipe_grid(K kern, size_t sm, int nt = NT) {
   int dev = 0, sms = 1, per = 1;
@@ -95,7 +101,7 @@ cudaError_t launch_ypipe(const tma::TensorMap& map, const PipeYArgs& a, cudaStre
   static int grid = 0;
   if (!grid) grid = pipe_grid(k_ypass_pipe<N, DIR>, sm);
   const int ntiles = PipeCfg<N>::NBLKY * N * a.ncomp;
-  k_ypass_pipe<N, DIR><<<grid < ntiles ? grid : ntiles, NT, sm, st>>>(map, a);
+  k_ypass_pipe<N, DIR><<<capped(grid, ntiles, a.max_ctas), NT, sm, st>>>(map, a);
   return cudaGetLastError();
 }
 
@@ -110,7 +116,7 @@ cudaError_t launch_zpipe_sc(const tma::TensorMap& in, const tma::TensorMap& out,
   constexpr int nt = zthreads<N, MODE>();
   if (!grid) grid = pipe_grid(k_zpass_pipe<N, MODE, SC>, sm, nt);
   const int ntiles = a.nyq_only ? PipeCfg<N>::NBLKZ + N - 1 : PipeCfg<N>::NBLKZ * N;
-  k_zpass_pipe<N, MODE, SC><<<grid < ntiles ? grid : ntiles, nt, sm, st>>>(in, out, phi, a);
+  k_zpass_pipe<N, MODE, SC><<<capped(grid, ntiles, a.max_ctas), nt, sm, st>>>(in, out, phi, a);
   return cudaGetLastError();
 }
 
@@ -157,7 +163,7 @@ cudaError_t launch_yfold(const tma::TensorMap& map4, const tma::TensorMap& mapc,
     if (!grid) grid = pipe_grid(k_ypass_fold<N, KIND>, sm, yf_threads(N));
     const int nbf = (N / 2 + pipe_pyf(N)) / pipe_pyf(N), nbp = (N / 2 + pipe_py(N)) / pipe_py(N);
     const int ntiles = nbf * N + nbp * N * a.nplain;
-    k_ypass_fold<N, KIND><<<grid < ntiles ? grid : ntiles, yf_threads(N), sm, st>>>(map4, mapc, mapp, a);
+    k_ypass_fold<N, KIND><<<capped(grid, ntiles, a.max_ctas), yf_threads(N), sm, st>>>(map4, mapc, mapp, a);
     return cudaGetLastError();
   }
 }
@@ -177,7 +183,7 @@ cudaError_t launch_zfold_sc(const tma::TensorMap& in2, const tma::TensorMap& out
     if (!grid) grid = pipe_grid(k_zpass_fold<N, MODE, SCK>, sm, 128);
     const int nbr = MODE == Z_NEWTON ? PipeCfg<N>::NBLKZ : PipeCfg<N>::NBLKZ - 1;
     const int ntiles = MODE == Z_NEWTON ? nbr * N : nbr * (N - 1);
-    k_zpass_fold<N, MODE, SCK><<<grid < ntiles ? grid : ntiles, 128, sm, st>>>(in2, out2, phi, a);
+    k_zpass_fold<N, MODE, SCK><<<capped(grid, ntiles, a.max_ctas), 128, sm, st>>>(in2, out2, phi, a);
     return cudaGetLastError();
   }
 }

@@ -474,3 +474,26 @@ def test_folded_passes_match_oracle(B, n, mu, K, keep_phi, mean, gather):
         assert rel(fields[0][2], ref["phi"]) < TOL
     if nh:
         assert rel(fields[0][-1], ref["H"], scale=ref["gN"]) < TOL
+
+
+@pytest.mark.parametrize("cap", [7, 152])
+def test_grid_cap_changes_nothing(B, cap):
+    """MOND_OPT_GRID_CAP: the persistent kernels with fewer CTAs take more
+    tiles or work items each; a step gives the same bits (each tile's
+    arithmetic and the integer deposit do not depend on which CTA runs them)."""
+    n = 64
+    p = W.isothermal(n, 1.0, 20000, n / 10, 0.4 * n, seed=41)
+    out = []
+    for c in (0, cap):
+        h, t = make(B, n, 1, p, 1.5)
+        h.set_option(B.OPT_GRID_CAP, c)
+        h.set_option(B.OPT_CYCLE_MEAN, 1)
+        h.deposit()
+        acc_dep = h.get_deposit_acc()[0].cpu().numpy()
+        h.solve_field(4)
+        h.gather_push(0.25)
+        h.sync()
+        out.append([acc_dep, h.get_field(B.FIELD_ACC).cpu().numpy(), t[0].cpu().numpy(), t[1].cpu().numpy(),
+                    t[2].cpu().numpy()])
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
