@@ -360,8 +360,10 @@ int mond_pm_autotune(mond_pm_t h, int n_iter, int trials, int64_t* chosen_chunk,
 /* One time step through host memory: copies cell/offset/vel of the N bound
  * particles from the host arrays (pinned memory recommended) to the bound
  * device arrays, runs mond_pm_step, copies cell/offset/vel back and
- * synchronises. Masses are not copied: they are constant and were scanned at
- * bind time. Returns any latched device error. */
+ * synchronises. The velocities go in on a copy stream of the handle while the
+ * deposit and the solve run (the gather waits for them); the other copies are
+ * on the handle's stream. Masses are not copied: they are constant and were
+ * scanned at bind time. Returns any latched device error. */
 int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cell_host, float* offset_host,
                       float* vel_host);
 

@@ -326,6 +326,12 @@ struct mond_pm {
   bool count_dirty = true;  // the binning's cell counters may be nonzero
   int fold = 1;        // MOND_OPT_FOLD (used where the pipelined passes run and the size allows it)
   int grid_cap = 0;    // MOND_OPT_GRID_CAP: CTAs of a persistent kernel at most (0: all that fit)
+  // mond_pm_step_host: the velocities go in on a copy stream of their own while
+  // the deposit and the solve run; the gather waits for them (vel_wait)
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_copy0 = nullptr, ev_vel = nullptr;
+  int vel_wait = 0;
+  bool capturing = false;
   int chunk = parts::CHUNK;  // particles per deposit/gather work item
   // captured step (MOND_OPT_USE_GRAPH): the launch sequence of one
   // mond_pm_step for the key below, replayed with one cudaGraphLaunch
@@ -337,13 +343,13 @@ struct mond_pm {
     int64_t N;
     const void* cell;
     const void* inc;
-    int cycle_mean, fold, grid_cap;
+    int cycle_mean, fold, grid_cap, vel_wait;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && n_iter == o.n_iter && warm == o.warm && keep_phi == o.keep_phi &&
              track_dh == o.track_dh && pipelined == o.pipelined && chunk == o.chunk &&
              gather_mode == o.gather_mode && ext_axis == o.ext_axis && ext_mass == o.ext_mass && N == o.N &&
              cell == o.cell && inc == o.inc && cycle_mean == o.cycle_mean && fold == o.fold &&
-             grid_cap == o.grid_cap;
+             grid_cap == o.grid_cap && vel_wait == o.vel_wait;
     }
   } gkey{};
   int64_t glaunches = 0;
@@ -1347,6 +1353,16 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
     delete h;
     return rc;
   }
+  // the copy stream of mond_pm_step_host (without it the copies stay on the handle's stream)
+  if (cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_copy0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_vel, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->ev_copy0) cudaEventDestroy(h->ev_copy0);
+    if (h->copy_st) cudaStreamDestroy(h->copy_st);
+    h->copy_st = nullptr;
+    h->ev_copy0 = h->ev_vel = nullptr;
+  }
   *out = h;
   return MOND_OK;
 }
@@ -1354,9 +1370,13 @@ int mond_pm_create(mond_pm_grid grid, double box, double a0, double G, int mu_ki
 int mond_pm_destroy(mond_pm_t h) {
   if (!h) return MOND_EINVAL;
   cudaStreamSynchronize(h->st);
+  if (h->copy_st) cudaStreamSynchronize(h->copy_st);
   collect_timing(h);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->ev_copy0) cudaEventDestroy(h->ev_copy0);
+  if (h->ev_vel) cudaEventDestroy(h->ev_vel);
+  if (h->copy_st) cudaStreamDestroy(h->copy_st);
   delete h;
   return MOND_OK;
 }
@@ -1568,6 +1588,8 @@ int step_direct(mond_pm_t h, double dt, int n_iter, int warm) {
   if (rc) return rc;
   rc = mond_pm_solve_field(h, n_iter, warm, nullptr);
   if (rc) return rc;
+  if (h->vel_wait)  // the velocities of mond_pm_step_host (an external wait inside a captured step)
+    CK(cudaStreamWaitEvent(h->st, h->ev_vel, h->capturing ? cudaEventWaitExternal : cudaEventWaitDefault));
   return mond_pm_gather_push(h, dt);
 }
 
@@ -1595,7 +1617,7 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
   if (rc) return rc;
   const mond_pm::GraphKey key{dt,       n_iter,          warm,        h->keep_phi, h->track_dh, h->pipelined,
                               h->chunk, h->gather_mode, h->ext_axis, h->ext_mass, h->N,         h->cell,
-                              h->inc.dep0, h->cycle_mean, use_fold(h) ? 1 : 0, h->grid_cap};
+                              h->inc.dep0, h->cycle_mean, use_fold(h) ? 1 : 0, h->grid_cap, h->vel_wait};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -1603,7 +1625,9 @@ int step_graph(mond_pm_t h, double dt, int n_iter, int warm) {
     }
     const int64_t l0 = h->launches;
     CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+    h->capturing = true;
     rc = capture_into(h, dt, n_iter, warm);
+    h->capturing = false;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->st, &g);  // always ends the capture
     h->glaunches = h->launches - l0;
@@ -1834,9 +1858,24 @@ int mond_pm_step_host(mond_pm_t h, double dt, int n_iter, int warm, int32_t* cel
   const size_t N = (size_t)h->N;
   CK(cudaMemcpyAsync(h->cell, cell_host, sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->off, offset_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->st));
-  CK(cudaMemcpyAsync(h->vel, vel_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->st));
+  // the velocities, needed first by the gather, go in on the copy stream
+  // after everything before them on h->st, beside the deposit and the solve
+  const bool overlap = h->copy_st && N > 0;
+  if (overlap) {
+    CK(cudaEventRecord(h->ev_copy0, h->st));
+    CK(cudaStreamWaitEvent(h->copy_st, h->ev_copy0, 0));
+    CK(cudaMemcpyAsync(h->vel, vel_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->copy_st));
+    CK(cudaEventRecord(h->ev_vel, h->copy_st));
+  } else {
+    CK(cudaMemcpyAsync(h->vel, vel_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->st));
+  }
+  h->vel_wait = overlap ? 1 : 0;
   int rc = mond_pm_step(h, dt, n_iter, warm);
-  if (rc) return rc;
+  h->vel_wait = 0;
+  if (rc) {
+    if (overlap) cudaStreamSynchronize(h->copy_st);  // no copy into the caller's velocities left in flight
+    return rc;
+  }
   CK(cudaMemcpyAsync(cell_host, h->cell, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(offset_host, h->off, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(vel_host, h->vel, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));

@@ -163,3 +163,27 @@ def test_autotune_cache(B, tmp_path):
     assert second == first and hs[1][0].kernel_launches() == l0  # nothing was timed
     for h, _ in hs:
         h.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_step_host_matches_device_steps(B, graph):
+    """mond_pm_step_host (the particle state in and out through pinned host
+    buffers, the velocities uploaded on a copy stream beside the deposit and
+    the solve, the gather waiting for them) gives the particle state of
+    mond_pm_step on device buffers, bit for bit, direct and captured."""
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    h1, t1 = system(B, 64, 20000, 5, B.MU_DEEP, s1)
+    h2, t2 = system(B, 64, 20000, 5, B.MU_DEEP, s2)
+    h2.set_option(B.OPT_USE_GRAPH, graph)
+    host = [x.cpu().pin_memory() for x in t2[:3]]
+    for _ in range(3):
+        h1.step(0.5, 4, B.WARM_NONE)
+        h2.step_host(0.5, 4, B.WARM_NONE, *host)
+    h1.sync()
+    assert same(state(t1), [x.numpy() for x in host])
+    # device steps on the same handle afterwards (a different captured step) continue from it
+    h1.step(0.5, 4, B.WARM_NONE)
+    h2.step(0.5, 4, B.WARM_NONE)
+    h1.sync()
+    h2.sync()
+    assert same(state(t1), state(t2))
