@@ -497,3 +497,24 @@ def test_grid_cap_changes_nothing(B, cap):
                     t[2].cpu().numpy()])
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [384, 512])
+def test_folded_passes_match_three_component_passes_at_large_sides(B, n):
+    """At the sides with 8-column y tiles and 4-column folded tiles (n >= 384)
+    the folded passes agree with the three-component ones to FP32 rounding
+    (the oracle at these sides is covered through the ring configuration)."""
+    p = W.isothermal(n, 1.0, 20000, n / 16, 0.4 * n, seed=n + 5)
+    fields = []
+    for fold in (1, 0):
+        h, _ = make(B, n, 1, p, 1.5)
+        h.set_option(B.OPT_FOLD, fold)
+        h.set_option(B.OPT_KEEP_PHI, 1)
+        h.set_option(B.OPT_CYCLE_MEAN, 1)
+        h.deposit()
+        h.solve_field(3)
+        fields.append([h.get_field(B.FIELD_ACC).cpu().numpy(), h.get_field(B.FIELD_PHI).cpu().numpy(),
+                       h.get_field(B.FIELD_GN).cpu().numpy()])
+        h.close()
+    for a, b in zip(fields[0], fields[1]):
+        assert rel(a, b) < TOL / 4
