@@ -83,16 +83,31 @@ __device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
   return r;
 }
 
-// Scan of the M = ncell + 1 counters in three launches.
+// Scan of the M = ncell + 1 counters in three launches. First the total of
+// each block of SCAN_B counters (16-byte loads, a warp reduction, the warps'
+// sums in shared memory).
 __global__ void __launch_bounds__(1024) k_scan_reduce(const int* cnt, int64_t M, int* bsum) {
   __shared__ int wsum[32];
-  int64_t b0 = (int64_t)blockIdx.x * SCAN_B;
+  const int64_t b0 = (int64_t)blockIdx.x * SCAN_B;
   int s = 0;
-  for (int k = threadIdx.x; k < SCAN_B; k += 1024)
-    if (b0 + k < M) s += cnt[b0 + k];
-  int tot;
-  block_excl_scan(s, wsum, &tot);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  if (b0 + SCAN_B <= M) {
+    const int4* c4 = reinterpret_cast<const int4*>(cnt + b0);
+    for (int k = threadIdx.x; k < SCAN_B / 4; k += 1024) {
+      const int4 v = c4[k];
+      s += (v.x + v.y) + (v.z + v.w);
+    }
+  } else {
+    for (int k = threadIdx.x; k < SCAN_B; k += 1024)
+      if (b0 + k < M) s += cnt[b0 + k];
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int t = threadIdx.x < (int)(blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+    t = __reduce_add_sync(0xffffffffu, t);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+  }
 }
 
 __global__ void __launch_bounds__(1024) k_scan_blocks(int* bsum, int nblk) {
