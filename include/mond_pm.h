@@ -98,7 +98,7 @@ enum {
   MOND_OPT_PIPELINED = 5, /* value 1 (default): y/z passes stream tiles with TMA through a two-stage ring;
                              0: one tile per CTA with plain loads (same results) */
   MOND_OPT_CHUNK = 6,     /* particles per deposit/gather work item: a power of two in 256..4096
-                             (default 2048; same results) */
+                             (default 1024; same results) */
   MOND_OPT_GATHER = 7,    /* force at the particles. 0 (default): Eq. gi, the ball sum at each particle.
                              1 or 3: the mesh-interpolating gather -- the final pass of a solve (n_iter >= 1)
                              also multiplies the acceleration spectrum by the smoothing spectrum, so that

@@ -11,7 +11,7 @@ namespace parts {
 constexpr int TILE = 8;       // mesh tile side: work items never span two tiles
 constexpr int DEP_NT = 256;   // threads per deposit CTA
 constexpr int GAT_NT = 256;   // threads per gather CTA
-constexpr int CHUNK = 2048;   // default particles per work item (runtime: the args' chunk)
+constexpr int CHUNK = 1024;   // default particles per work item (runtime: the args' chunk)
 constexpr int QHALF = 32768;  // offset quantisation: q = round(offset * 2^16) + 32768
 constexpr int SCAN_B = 8192;  // elements per block of the key scan
 
